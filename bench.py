@@ -1,0 +1,342 @@
+"""Throughput benchmark of GB300 mesh re-indexing (input elements re-indexed per second).
+
+Default workload: the 2048 x 2048-cell heightfield triangle soup (8,388,608 triangles, each
+emitting its own 3 float32 xyz vertices, plus 5% unreferenced vertices, vertex array randomly
+permuted; 26,424,115 vertices, int32 indices, 3 per element), seed 2.
+
+One step = one full pass of the pipeline (used flags, compaction + digit histograms, sort plan,
+onesweep radix passes, fused head scan / oldToNew scatter / unique gather, remap) on that mesh.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+Prints one JSON line.  `value` is device-resident throughput (inputs already in HBM, workspace
+preallocated); `e2e` is the same metric through the host-buffer C entry point with the copies
+inside the timed region.  Under torchrun each rank runs an independent replica of the workload
+(no collective on the data path); the time is the max over ranks.  `--impl reference` times the
+serial CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (description, builder args)
+    "heightfield2048": ("heightfield triangle soup 2048x2048 cells (8,388,608 tris, 25,165,824 soup vertices "
+                        "float32 xyz + 5% unused = 26,424,115 vertices, permuted), int32 idx x3, seed 2", 2),
+    "heightfield256": ("heightfield triangle soup 256x256 cells (131,072 tris, 393,216 soup vertices float32 xyz "
+                       "+ 10% unused = 432,538 vertices, permuted), int32 idx x3, seed 1", 1),
+    "tet128": ("tetrahedral soup 128^3 hex cells x 5 tets (10,485,760 tets, 41,943,040 soup vertices of 16 B "
+               "+ 3% unused = 43,201,331 vertices, permuted), int32 idx x4, seed 3", 3),
+}
+METRIC = "input elements re-indexed/sec"
+UNIT = "elements/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_digest(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+ONESWEEP_SOURCES = ["paper_2109_09812_gb300/csrc/k_onesweep.cu", "paper_2109_09812_gb300/csrc/common.cuh"]
+
+
+def ncu_traffic(workload):
+    """Per-launch DRAM bytes of the onesweep kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "onesweep_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("source_digest") != source_digest(ONESWEEP_SOURCES):
+            return None
+        return rec.get("per_launch_bytes_full", {}).get(workload)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def oracle_rate(mesh, repeats=1):
+    """Serial oracle (std::sort over (key, index) pairs) on the host: elements/s, seconds."""
+    import oracle
+
+    oracle.lib()
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        oracle.reindex_sort(mesh.vtx, mesh.idx)
+    dt = (time.perf_counter() - t0) / repeats
+    return mesh.n_elem / dt, dt
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the serial CPU oracle as it stands, on a bounded sample per step."""
+    if rank != 0:
+        return
+    from paper_2109_09812_gb300 import synth
+
+    cfg = WORKLOADS[args.workload][1]
+    if cfg == 3:
+        sample = synth.tet_soup(48, 0.03, 3)
+        sample_desc = "tetrahedral soup 48^3 cells x 5 tets, same construction (552,960 tets)"
+    else:
+        g = 1024 if cfg == 2 else 256
+        sample = synth.heightfield_soup(g, g, 0.05 if cfg == 2 else 0.10, cfg)
+        sample_desc = f"heightfield soup {g}x{g} cells, same construction ({2 * g * g:,} tris)"
+    import oracle
+
+    oracle.lib()
+    for _ in range(args.warmup):
+        oracle.reindex_sort(sample.vtx, sample.idx)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.reindex_sort(sample.vtx, sample.idx)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = sample.n_elem / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][0], "sample": sample_desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample_desc + ", serial std::sort oracle, one thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_2109_09812_gb300 as rx
+    from paper_2109_09812_gb300 import build as rxbuild
+    from paper_2109_09812_gb300 import synth
+
+    if rank == 0 or world == 1:
+        rxbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfg = WORKLOADS[args.workload][1]
+    mesh = synth.config_mesh(cfg)
+    S, k, n_vtx, n_elem = mesh.stride_bytes, mesh.idx_per_elem, mesh.n_vtx, mesh.n_elem
+    M = n_elem * k
+    U = M  # soups: every soup vertex is referenced exactly once
+    vtx = torch.from_numpy(mesh.vtx.view(np.int32)).to(dev)
+    idx = torch.from_numpy(mesh.idx).to(dev)
+    ws = torch.empty(rx.reindex_workspace_size(n_vtx, S, n_elem, k), dtype=torch.uint8, device=dev)
+    out_v = torch.empty((min(n_vtx, M), S // 4), dtype=torch.int32, device=dev)
+    out_n = torch.empty(1, dtype=torch.int64, device=dev)
+    out_i = torch.empty_like(idx)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(max(args.warmup, 1)):
+        rx.reindex_mesh_ws(vtx, idx, ws, out_v, out_n, out_i)
+    torch.cuda.synchronize(dev)
+    D = int(out_n.item())
+    if D != mesh.expected_unique:
+        raise SystemExit(f"unexpected unique count {D} (expected {mesh.expected_unique})")
+
+    # ---- timed region: device-resident inputs, per-launch events for the roofline
+    rx.profile_collect()
+    rx.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            rx.reindex_mesh_ws(vtx, idx, ws, out_v, out_n, out_i)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+    rx.profile_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    recs = rx.profile_collect()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_elem / (ms / 1e3)
+
+    # ---- per-kernel breakdown and the dominant kernel's roofline
+    per_kernel = {}
+    for r in recs:
+        key = r["name"] + (" (skipped)" if r["skipped"] else "")
+        a = per_kernel.setdefault(key, [0, 0.0])
+        a[0] += 1
+        a[1] += r["ms"]
+    sweeps = [r["ms"] for r in recs if r["name"] == "onesweep" and not r["skipped"]]
+    W = S + 4
+    alg_bytes = 2 * U * W  # one pass reads and writes every (key, index) item once
+    peak, peak_kind = load_peaks()
+    avg_ms = sum(sweeps) / len(sweeps) if sweeps else float("nan")
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    roofline = {"kernel": "onesweep", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                "traffic": ncu_traffic(args.workload), "algorithmic_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": avg_ms, "passes_per_step": len(sweeps) / args.steps}
+
+    # ---- end to end through the host-buffer entry point
+    hv = torch.from_numpy(mesh.vtx.view(np.int32)).pin_memory()
+    hi = torch.from_numpy(mesh.idx).pin_memory()
+    ho_v = torch.empty((min(n_vtx, M), S // 4), dtype=torch.int32).pin_memory()
+    ho_i = torch.empty_like(hi).pin_memory()
+    for _ in range(2):
+        rx.reindex_mesh_host(hv, hi, ho_v, ho_i)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(e2e_steps):
+        rv, _ = rx.reindex_mesh_host(hv, hi, ho_v, ho_i)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * n_elem / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n_vtx * S + M * 4,
+           "d2h_bytes_per_step": rv.shape[0] * S + M * 4 + 8, "ms_per_step": e2e_s * 1e3}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, secs = oracle_rate(mesh)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the full workload once ({secs:.1f} s), serial std::sort oracle, one thread"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][0], "n_vtx": n_vtx, "n_elem": n_elem, "stride_bytes": S,
+                   "idx_per_elem": k, "unique_out": D, "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2 ({(n_vtx * S + M * 4) / 1e6:.0f} MB read per step)"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": len(recs),
+        "kernels": {k_: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k_, v in sorted(per_kernel.items())},
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="heightfield2048")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_ours(args, world, rank, local)
+    finally:
+        if world > 1 and args.impl == "ours":
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * reindex.h -- C ABI of the GB300 (sm_103a) mesh re-indexing library.
+ *
+ * Method: Wald, "GPGPU-Parallel Re-indexing of Triangle Meshes with Duplicate-Vertex and
+ * Unused-Vertex Removal" (arXiv 2109.09812), Section 2.  Given a vertex array and an index
+ * array of fixed-arity elements, the library produces a new vertex array without unused or
+ * duplicate vertices and rewrites every index to point into it.
+ *
+ * Result definition (what every entry point computes, exactly):
+ *   - A vertex is S = vtxStrideBytes raw bytes, viewed as K = S/4 little-endian uint32 words
+ *     w[0..K-1].  Two vertices are equal iff all S bytes are equal (so +0.0 != -0.0 and NaNs
+ *     compare by payload; padding bytes inside the stride take part).  Section 2 asks for
+ *     "exact duplicates" and some total order without fixing either; this is the reading.
+ *   - Vertices are ordered lexicographically by (w[0], w[1], ...), each word compared as an
+ *     unsigned integer (raw-bit order: negative floats sort after non-negative ones).
+ *   - out_vtx holds the distinct values of the vertices referenced by at least one index, in
+ *     strictly ascending order; *out_nVtx is their number D.
+ *   - out_idx[j] is the position in out_vtx of the value of vtx[idx[j]].
+ *   This result is unique: it does not depend on any tie order inside the method.
+ *
+ * The pipeline (Sections 2.1-2.4, each step a CUDA kernel of this library):
+ *   1. used-vertex flags scattered from the index buffer (Section 2.1, isUsed);
+ *   2. stable compaction of the used vertices into (key, old index) items.  The paper instead
+ *      overwrites each unused vertex with a used one (Section 2.1); both give the same result;
+ *   3. LSD radix sort of the items by key, 8 bits per pass, onesweep style with decoupled
+ *      look-back (Section 2.2, key-value sort); passes whose digit is constant are skipped;
+ *   4. run-head flags where a key differs from its predecessor (Section 2.2, nodup);
+ *   5. exclusive prefix sum of the flags giving new indices (Section 2.2, newIdx; the
+ *      footnote there notes inclusive-minus-one equals exclusive);
+ *   6. oldToNew scatter: oldToNew[orgID[j]] = newIdx[j] (Section 2.4, perm composed with
+ *      newIdx);
+ *   7. gather of the unique vertices (Section 2.3, newVtx);
+ *   8. remap of every index: out_idx[j] = oldToNew[idx[j]] (Section 2.4).
+ *
+ * Conventions shared by all entry points:
+ *   - Pointers named vtx/idx/out_* are DEVICE pointers owned by the caller unless the entry
+ *     point says "host".  The library never frees caller memory.
+ *   - All calls are asynchronous on `stream` (0 = the legacy default stream) unless stated
+ *     otherwise; they never synchronise it.  The returned status covers host-side argument
+ *     checks, allocation and kernel launches only.
+ *   - Device-detected errors (an index outside [0, nVtx), a look-back wait that ran out) are
+ *     reported after the stream is synchronised in two ways: *out_nVtx holds the NEGATED
+ *     status code (e.g. -REINDEX_ERR_INDEX_RANGE), and reindex_stream_status() returns it.
+ *     When one occurs the contents of out_vtx and out_idx are unspecified.
+ *   - Supported strides: vtxStrideBytes in {4, 8, 12, 16}.  vtx and out_vtx must be aligned
+ *     to the stride's natural vector type: 4 bytes for S = 4 and 12, 8 bytes for S = 8,
+ *     16 bytes for S = 16.  idx and out_idx must be 4-byte aligned (16-byte alignment enables
+ *     128-bit vector loads and stores).
+ *   - nVtx <= 2^30 - 1 and nElem * idxPerElem <= 2^31 - 1 (int32 indices; the look-back
+ *     status words pack a 30-bit count).
+ *   - out_idx may alias idx (the remap reads and writes the same slot in one thread).  No
+ *     other output may overlap an input.
+ *   - Thread safety: calls may be issued concurrently from several host threads on different
+ *     streams; calls on one stream are ordered by that stream.
+ */
+#ifndef REINDEX_H
+#define REINDEX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque CUDA stream handle (binary-compatible with cudaStream_t / CUstream). */
+typedef struct CUstream_st* reindex_stream_t;
+
+typedef enum {
+  REINDEX_OK = 0,
+  REINDEX_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or workspace too small */
+  REINDEX_ERR_UNSUPPORTED = 2, /* stride not in {4,8,12,16}, or sizes beyond the limits above */
+  REINDEX_ERR_OOM = 3,         /* a library allocation failed */
+  REINDEX_ERR_INDEX_RANGE = 4, /* some index < 0 or >= nVtx (device-detected) */
+  REINDEX_ERR_TIMEOUT = 5,     /* a look-back wait exceeded its iteration limit (device-detected) */
+  REINDEX_ERR_CUDA = 6,        /* a CUDA runtime call failed */
+  REINDEX_ERR_INTERNAL = 7     /* a device-side consistency check failed (a library bug) */
+} reindex_status;
+
+/* Human-readable name of a status code.  Never returns NULL. */
+const char* reindex_status_string(reindex_status s);
+
+/* Bytes of device workspace reindex_mesh_ws needs for a mesh of this size (Section 3.6 notes
+ * the method needs temporary memory comparable to the data: here two copies of the (key,
+ * old index) items, one uint32 per input vertex, a bit per input vertex and small look-back
+ * and histogram tables).  Returns 0 for unsupported arguments. */
+size_t reindex_workspace_size(int64_t nVtx, int vtxStrideBytes, int64_t nElem, int idxPerElem);
+
+/* Re-index one mesh (Sections 2.1-2.4).
+ *   vtx         device, nVtx * vtxStrideBytes bytes (aligned as above)
+ *   nVtx        number of input vertices (>= 0)
+ *   idx         device int32[nElem * idxPerElem]; element e owns idx[e*idxPerElem ...]
+ *   nElem       number of elements (>= 0); idxPerElem >= 1 (3 = triangles, 4 = quads/tets)
+ *   out_vtx     device, room for min(nVtx, nElem*idxPerElem) * vtxStrideBytes bytes
+ *   out_nVtx    device int64 scalar: D, or -status after a device-detected error
+ *   out_idx     device int32[nElem * idxPerElem] (may alias idx)
+ * Workspace comes from the device's stream-ordered memory pool (cudaMallocAsync on `stream`),
+ * returned to the pool on the same stream.  nElem == 0 gives *out_nVtx = 0.  nVtx == 0 with
+ * nElem > 0 returns REINDEX_ERR_INDEX_RANGE at once (every index is out of range). */
+reindex_status reindex_mesh(const void* vtx, int64_t nVtx, int vtxStrideBytes,
+                            const int32_t* idx, int64_t nElem, int idxPerElem,
+                            void* out_vtx, int64_t* out_nVtx, int32_t* out_idx,
+                            reindex_stream_t stream);
+
+/* Same as reindex_mesh with a caller-supplied device workspace of wsBytes >=
+ * reindex_workspace_size(...) bytes, 256-byte aligned.  Performs no allocation and no host
+ * synchronisation, so it can be captured into a CUDA graph.  The workspace must not be used by
+ * any other call until this one has finished on the device. */
+reindex_status reindex_mesh_ws(const void* vtx, int64_t nVtx, int vtxStrideBytes,
+                               const int32_t* idx, int64_t nElem, int idxPerElem,
+                               void* out_vtx, int64_t* out_nVtx, int32_t* out_idx,
+                               void* ws, size_t wsBytes, reindex_stream_t stream);
+
+/* End-to-end variant on HOST buffers: copies vtx and idx to the device, runs the pipeline and
+ * copies the D unique vertices, the indices and D back.  host_vtx / host_idx should be pinned
+ * (page-locked) for full copy bandwidth; host_out_vtx needs room for min(nVtx, nElem *
+ * idxPerElem) vertices.  Device buffers come from the stream-ordered pool.  BLOCKING: returns
+ * after the results are in host memory; a device-detected error is returned as the status
+ * and written (negated) to *host_out_nVtx. */
+reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int vtxStrideBytes,
+                                 const int32_t* host_idx, int64_t nElem, int idxPerElem,
+                                 void* host_out_vtx, int64_t* host_out_nVtx, int32_t* host_out_idx,
+                                 reindex_stream_t stream);
+
+/* Synchronises `stream`, then returns and clears this device's sticky device-side error: the
+ * first INDEX_RANGE or TIMEOUT raised by any call on the current device since the last
+ * reindex_stream_status() (REINDEX_OK if none).  A CUDA error from the synchronisation is
+ * returned as REINDEX_ERR_CUDA. */
+reindex_status reindex_stream_status(reindex_stream_t stream);
+
+/* ---- per-kernel timing (measurement support) ------------------------------------------------
+ * While enabled, every pipeline kernel launch made by this process is bracketed by a pair of
+ * CUDA events recorded on its stream.  reindex_profile_collect() synchronises those events and
+ * returns one record per launch.  Off by default; not for use under stream capture. */
+typedef struct {
+  int kernel;      /* reindex_kernel_id */
+  int digit;       /* radix digit position of a sort pass (0 = least significant byte), else -1 */
+  int skipped;     /* 1 if a sort pass found its digit constant and moved no data */
+  float ms;        /* event-measured duration */
+} reindex_profile_record;
+
+typedef enum {
+  REINDEX_K_CLEAR = 0,      /* zero the workspace tables */
+  REINDEX_K_USED_FLAGS = 1, /* step 1 */
+  REINDEX_K_COMPACT = 2,    /* step 2 (+ upfront digit histograms) */
+  REINDEX_K_SORT_PLAN = 3,  /* digit offsets and pass skipping */
+  REINDEX_K_ONESWEEP = 4,   /* step 3, one launch per digit */
+  REINDEX_K_HEAD_SCAN = 5,  /* steps 4-7 fused */
+  REINDEX_K_REMAP = 6,      /* step 8 */
+  REINDEX_K_FINALIZE = 7,   /* error propagation */
+  REINDEX_K_COUNT = 8
+} reindex_kernel_id;
+
+void reindex_profile_enable(int on);
+/* Writes up to maxRecords records; returns the number of records pending (all of them are
+ * consumed), or -1 on a CUDA error. */
+int reindex_profile_collect(reindex_profile_record* out, int maxRecords);
+const char* reindex_kernel_name(int kernel);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REINDEX_H */

@@ -1,0 +1,218 @@
+"""GB300-native mesh re-indexing with duplicate- and unused-vertex removal.
+
+Thin Python binding (ctypes) of ``libreindex.so``, whose C ABI is ``include/reindex.h``.
+Every step of the method runs in the library's CUDA kernels; this module only checks that
+tensors are on the GPU, contiguous and of the right element size, and passes their pointers
+and the current CUDA stream.  PyTorch provides device memory and streams only.
+
+There is no CPU fallback: if ``libreindex.so`` is missing, every entry point raises.
+Build it with ``python -m paper_2109_09812_gb300.build``.
+
+Method: Wald, "GPGPU-Parallel Re-indexing of Triangle Meshes with Duplicate-Vertex and
+Unused-Vertex Removal" (arXiv 2109.09812), Sections 2.1-2.4.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libreindex.so")
+
+REINDEX_OK = 0
+REINDEX_ERR_INVALID_ARG = 1
+REINDEX_ERR_UNSUPPORTED = 2
+REINDEX_ERR_OOM = 3
+REINDEX_ERR_INDEX_RANGE = 4
+REINDEX_ERR_TIMEOUT = 5
+REINDEX_ERR_CUDA = 6
+REINDEX_ERR_INTERNAL = 7
+
+KERNEL_NAMES = ["clear", "used_flags", "compact_hist", "sort_plan", "onesweep", "head_scan", "remap", "finalize"]
+
+# Symbols declared in include/reindex.h (checked by the ABI test).
+EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "reindex_mesh_ws",
+            "reindex_mesh_host", "reindex_stream_status", "reindex_profile_enable", "reindex_profile_collect",
+            "reindex_kernel_name"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ReindexError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = int(code)
+        super().__init__(f"{where}: {reindex_status_string(self.code)}" if where else reindex_status_string(self.code))
+
+
+class _ProfileRecord(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("digit", ctypes.c_int), ("skipped", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
+def lib() -> ctypes.CDLL:
+    """Load libreindex.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2109_09812_gb300.build` "
+                                   "(there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            L.reindex_status_string.argtypes = [ci]
+            L.reindex_status_string.restype = ctypes.c_char_p
+            L.reindex_workspace_size.argtypes = [i64, ci, i64, ci]
+            L.reindex_workspace_size.restype = ctypes.c_size_t
+            mesh_args = [vp, i64, ci, vp, i64, ci, vp, vp, vp]
+            L.reindex_mesh.argtypes = mesh_args + [vp]
+            L.reindex_mesh.restype = ci
+            L.reindex_mesh_ws.argtypes = mesh_args + [vp, ctypes.c_size_t, vp]
+            L.reindex_mesh_ws.restype = ci
+            L.reindex_mesh_host.argtypes = mesh_args + [vp]
+            L.reindex_mesh_host.restype = ci
+            L.reindex_stream_status.argtypes = [vp]
+            L.reindex_stream_status.restype = ci
+            L.reindex_profile_enable.argtypes = [ci]
+            L.reindex_profile_enable.restype = None
+            L.reindex_profile_collect.argtypes = [ctypes.POINTER(_ProfileRecord), ci]
+            L.reindex_profile_collect.restype = ci
+            L.reindex_kernel_name.argtypes = [ci]
+            L.reindex_kernel_name.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def reindex_status_string(code: int) -> str:
+    try:
+        return lib().reindex_status_string(int(code)).decode()
+    except RuntimeError:
+        return f"status {code}"
+
+
+def reindex_workspace_size(n_vtx: int, stride_bytes: int, n_elem: int, idx_per_elem: int) -> int:
+    return int(lib().reindex_workspace_size(n_vtx, stride_bytes, n_elem, idx_per_elem))
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _mesh_geometry(vtx, idx):
+    """(nVtx, strideBytes, nElem, k) from a (nVtx, ...) tensor with one vertex per row and an
+    (nElem, k) int32 index tensor."""
+    torch = _torch()
+    if vtx.dim() < 1 or not vtx.is_contiguous():
+        raise ValueError("vtx must be a contiguous tensor with one vertex per row")
+    if idx.dtype != torch.int32 or idx.dim() != 2 or not idx.is_contiguous():
+        raise ValueError("idx must be a contiguous (nElem, idxPerElem) int32 tensor")
+    stride = math.prod(vtx.shape[1:]) * vtx.element_size()
+    return int(vtx.shape[0]), int(stride), int(idx.shape[0]), int(idx.shape[1])
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() else 0)
+
+
+def reindex_mesh(vtx, idx, out_vtx=None, out_nVtx=None, out_idx=None, stream=None):
+    """Asynchronously re-index one mesh on the GPU (workspace from the stream-ordered pool).
+
+    vtx: CUDA tensor (nVtx, ...) with one vertex of 4/8/12/16 bytes per row (any dtype; the
+    raw bits are the key).  idx: CUDA int32 tensor (nElem, k).  Returns (out_vtx, out_nVtx,
+    out_idx): out_vtx has min(nVtx, nElem*k) rows of which the first D = out_nVtx.item() are
+    valid; out_nVtx is a 1-element int64 CUDA tensor (negative status on a device error)."""
+    torch = _torch()
+    n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx)
+    if not (vtx.is_cuda and idx.is_cuda):
+        raise ValueError("vtx and idx must be CUDA tensors (use reindex_mesh_host for host buffers)")
+    cap = min(n_vtx, n_elem * k)
+    if out_vtx is None:
+        out_vtx = torch.empty((cap,) + tuple(vtx.shape[1:]), dtype=vtx.dtype, device=vtx.device)
+    if out_nVtx is None:
+        out_nVtx = torch.empty(1, dtype=torch.int64, device=vtx.device)
+    if out_idx is None:
+        out_idx = torch.empty_like(idx)
+    rc = lib().reindex_mesh(_ptr(vtx), n_vtx, S, _ptr(idx), n_elem, k, _ptr(out_vtx), _ptr(out_nVtx),
+                            _ptr(out_idx), _stream_handle(stream))
+    if rc:
+        raise ReindexError(rc, "reindex_mesh")
+    return out_vtx, out_nVtx, out_idx
+
+
+def reindex_mesh_ws(vtx, idx, ws, out_vtx=None, out_nVtx=None, out_idx=None, stream=None):
+    """Like reindex_mesh with a caller-supplied workspace (a CUDA uint8 tensor of at least
+    reindex_workspace_size(...) bytes); performs no allocation, so it can be graph-captured
+    when the outputs are preallocated."""
+    torch = _torch()
+    n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx)
+    cap = min(n_vtx, n_elem * k)
+    if out_vtx is None:
+        out_vtx = torch.empty((cap,) + tuple(vtx.shape[1:]), dtype=vtx.dtype, device=vtx.device)
+    if out_nVtx is None:
+        out_nVtx = torch.empty(1, dtype=torch.int64, device=vtx.device)
+    if out_idx is None:
+        out_idx = torch.empty_like(idx)
+    rc = lib().reindex_mesh_ws(_ptr(vtx), n_vtx, S, _ptr(idx), n_elem, k, _ptr(out_vtx), _ptr(out_nVtx),
+                               _ptr(out_idx), _ptr(ws), ws.numel() * ws.element_size(), _stream_handle(stream))
+    if rc:
+        raise ReindexError(rc, "reindex_mesh_ws")
+    return out_vtx, out_nVtx, out_idx
+
+
+def reindex_mesh_host(vtx, idx, out_vtx=None, out_idx=None, stream=None):
+    """Blocking end-to-end call on HOST tensors (pinned for full copy bandwidth): copies in,
+    re-indexes, copies the D unique vertices and the indices back.  Returns (out_vtx[:D], out_idx)."""
+    torch = _torch()
+    n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx)
+    if vtx.is_cuda or idx.is_cuda:
+        raise ValueError("reindex_mesh_host takes host tensors")
+    cap = min(n_vtx, n_elem * k)
+    if out_vtx is None:
+        out_vtx = torch.empty((cap,) + tuple(vtx.shape[1:]), dtype=vtx.dtype, pin_memory=True)
+    if out_idx is None:
+        out_idx = torch.empty_like(idx, pin_memory=True)
+    D = ctypes.c_int64(-1)
+    rc = lib().reindex_mesh_host(_ptr(vtx), n_vtx, S, _ptr(idx), n_elem, k, _ptr(out_vtx),
+                                 ctypes.cast(ctypes.pointer(D), ctypes.c_void_p), _ptr(out_idx),
+                                 _stream_handle(stream))
+    if rc:
+        raise ReindexError(rc, "reindex_mesh_host")
+    return out_vtx[: D.value], out_idx
+
+
+def reindex_stream_status(stream=None) -> int:
+    """Synchronise the stream; return and clear the device's sticky device-side error (0 = none)."""
+    return int(lib().reindex_stream_status(_stream_handle(stream)))
+
+
+def reindex(vtx, idx, stream=None):
+    """Convenience wrapper: re-index and return (new_vtx[:D], new_idx), synchronising to read D."""
+    out_vtx, out_n, out_idx = reindex_mesh(vtx, idx, stream=stream)
+    D = int(out_n.item())
+    if D < 0:
+        raise ReindexError(-D, "reindex (device)")
+    return out_vtx[:D], out_idx
+
+
+def profile_enable(on: bool = True) -> None:
+    lib().reindex_profile_enable(1 if on else 0)
+
+
+def profile_collect(max_records: int = 1 << 16):
+    """Per-launch records since the last collect: list of dicts(kernel, name, digit, skipped, ms)."""
+    buf = (_ProfileRecord * max_records)()
+    n = lib().reindex_profile_collect(buf, max_records)
+    if n < 0:
+        raise ReindexError(REINDEX_ERR_CUDA, "reindex_profile_collect")
+    return [dict(kernel=r.kernel, name=KERNEL_NAMES[r.kernel], digit=r.digit, skipped=bool(r.skipped), ms=r.ms)
+            for r in buf[: min(n, max_records)]]

@@ -1,0 +1,343 @@
+// C ABI of the re-indexing library (include/reindex.h): argument checks, workspace layout,
+// the launch sequence of the pipeline, the pool-allocating and host-buffer variants, the
+// sticky error query and the per-launch timing facility.
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "../../include/reindex.h"
+#include "internal.h"
+
+namespace reindex {
+
+// ---------------------------------------------------------------------------------------------
+// Per-device launch configuration.
+const LaunchCfg& launch_cfg(int S) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, LaunchCfg> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  auto it = cache.find({dev, S});
+  if (it != cache.end()) return it->second;
+  LaunchCfg c;
+  cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (c.sms < 1) c.sms = 1;
+  c.occ_compact = occupancy_compact(S);
+  c.occ_sort = occupancy_sort(S);
+  c.occ_head = occupancy_head(S);
+  return cache.emplace(std::make_pair(dev, S), c).first->second;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Per-launch timing (off by default).
+namespace prof {
+struct Pending {
+  int kernel, digit;
+  cudaEvent_t a, b;
+  const uint8_t* skip;  // pinned host copy of the plan's skip flags (sort passes only)
+};
+static std::mutex mu;
+static bool enabled = false;
+static std::vector<Pending> pending;
+static std::vector<uint8_t*> pinned;
+
+struct Scope {
+  bool on;
+  Pending p;
+  cudaStream_t st;
+  Scope(int kernel, int digit, cudaStream_t s, const uint8_t* skip = nullptr) : on(false), st(s) {
+    {
+      std::lock_guard<std::mutex> g(mu);
+      on = enabled;
+    }
+    if (!on) return;
+    p.kernel = kernel;
+    p.digit = digit;
+    p.skip = skip;
+    cudaEventCreate(&p.a);
+    cudaEventCreate(&p.b);
+    cudaEventRecord(p.a, st);
+  }
+  ~Scope() {
+    if (!on) return;
+    cudaEventRecord(p.b, st);
+    std::lock_guard<std::mutex> g(mu);
+    pending.push_back(p);
+  }
+};
+
+static uint8_t* skip_buffer(const Plan* plan, cudaStream_t st) {
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!enabled) return nullptr;
+  }
+  uint8_t* h = nullptr;
+  if (cudaMallocHost(&h, kMaxDigits) != cudaSuccess) return nullptr;
+  cudaMemcpyAsync(h, plan->skip, kMaxDigits, cudaMemcpyDeviceToHost, st);
+  std::lock_guard<std::mutex> g(mu);
+  pinned.push_back(h);
+  return h;
+}
+}  // namespace prof
+
+static reindex_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return REINDEX_OK;
+  if (e == cudaErrorMemoryAllocation) return REINDEX_ERR_OOM;
+  return REINDEX_ERR_CUDA;
+}
+
+#define REINDEX_TRY(expr)                          \
+  do {                                             \
+    cudaError_t e__ = (expr);                      \
+    if (e__ != cudaSuccess) return cuda_status(e__); \
+  } while (0)
+
+static bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+static uintptr_t vtx_alignment(int S) { return S == 8 ? 8 : (S == 16 ? 16 : 4); }
+
+// Host-side checks shared by every entry point.  Sets M.
+static reindex_status check_args(int64_t nVtx, int S, int64_t nElem, int k, int64_t* M) {
+  if (S != 4 && S != 8 && S != 12 && S != 16) return REINDEX_ERR_UNSUPPORTED;
+  if (nVtx < 0 || nElem < 0 || k < 1) return REINDEX_ERR_INVALID_ARG;
+  if (nVtx > kMaxCount) return REINDEX_ERR_UNSUPPORTED;
+  if (nElem > (int64_t)INT32_MAX / k) return REINDEX_ERR_UNSUPPORTED;
+  *M = nElem * (int64_t)k;
+  return REINDEX_OK;
+}
+
+static reindex_status check_ptrs(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t M,
+                                 const void* out_vtx, const int64_t* out_nVtx, const int32_t* out_idx) {
+  if (out_nVtx == nullptr || !aligned(out_nVtx, 8)) return REINDEX_ERR_INVALID_ARG;
+  if (M == 0) return REINDEX_OK;
+  if (!idx || !out_idx || !out_vtx || (nVtx > 0 && !vtx)) return REINDEX_ERR_INVALID_ARG;
+  if (!aligned(idx, 4) || !aligned(out_idx, 4)) return REINDEX_ERR_INVALID_ARG;
+  if ((nVtx > 0 && !aligned(vtx, vtx_alignment(S))) || !aligned(out_vtx, vtx_alignment(S)))
+    return REINDEX_ERR_INVALID_ARG;
+  return REINDEX_OK;
+}
+
+// The launch sequence (all on `st`, no host synchronisation).
+static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t M,
+                                   void* out_vtx, int64_t* out_nVtx, int32_t* out_idx, void* ws,
+                                   const WsLayout& L, cudaStream_t st) {
+  const LaunchCfg& c = launch_cfg(S);
+  const WsPtrs p = ws_ptrs(ws, L);
+  {
+    prof::Scope s(REINDEX_K_CLEAR, -1, st);
+    REINDEX_TRY(launch_clear(ws, L.zero_bytes, c, st));
+  }
+  {
+    prof::Scope s(REINDEX_K_USED_FLAGS, -1, st);
+    REINDEX_TRY(launch_used_flags(idx, M, nVtx, p, c, st));
+  }
+  {
+    prof::Scope s(REINDEX_K_COMPACT, -1, st);
+    REINDEX_TRY(launch_compact(S, vtx, nVtx, p, L.tilesV, c, st));
+  }
+  {
+    prof::Scope s(REINDEX_K_SORT_PLAN, -1, st);
+    REINDEX_TRY(launch_sort_plan(S, p, st));
+  }
+  const uint8_t* skip = prof::skip_buffer(p.plan, st);
+  for (int d = 0; d < L.P; ++d) {
+    prof::Scope s(REINDEX_K_ONESWEEP, d, st, skip);
+    REINDEX_TRY(launch_onesweep(S, d, p, c, st));
+  }
+  {
+    prof::Scope s(REINDEX_K_HEAD_SCAN, -1, st);
+    REINDEX_TRY(launch_head_scan(S, p, out_vtx, out_nVtx, (uint32_t)nVtx, c, st));
+  }
+  {
+    prof::Scope s(REINDEX_K_REMAP, -1, st);
+    REINDEX_TRY(launch_remap(idx, out_idx, M, p, c, st));
+  }
+  {
+    prof::Scope s(REINDEX_K_FINALIZE, -1, st);
+    REINDEX_TRY(launch_finalize(p, out_nVtx, st));
+  }
+  return REINDEX_OK;
+}
+
+static void set_pool_threshold() {
+  static std::mutex mu;
+  static std::map<int, bool> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;  // keep freed blocks cached in the pool between calls
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[dev] = true;
+}
+
+}  // namespace reindex
+
+using namespace reindex;
+
+extern "C" {
+
+const char* reindex_status_string(reindex_status s) {
+  switch (s) {
+    case REINDEX_OK: return "REINDEX_OK";
+    case REINDEX_ERR_INVALID_ARG: return "REINDEX_ERR_INVALID_ARG";
+    case REINDEX_ERR_UNSUPPORTED: return "REINDEX_ERR_UNSUPPORTED";
+    case REINDEX_ERR_OOM: return "REINDEX_ERR_OOM";
+    case REINDEX_ERR_INDEX_RANGE: return "REINDEX_ERR_INDEX_RANGE";
+    case REINDEX_ERR_TIMEOUT: return "REINDEX_ERR_TIMEOUT";
+    case REINDEX_ERR_CUDA: return "REINDEX_ERR_CUDA";
+    case REINDEX_ERR_INTERNAL: return "REINDEX_ERR_INTERNAL";
+  }
+  return "REINDEX_ERR_UNKNOWN";
+}
+
+size_t reindex_workspace_size(int64_t nVtx, int vtxStrideBytes, int64_t nElem, int idxPerElem) {
+  int64_t M = 0;
+  if (check_args(nVtx, vtxStrideBytes, nElem, idxPerElem, &M) != REINDEX_OK) return 0;
+  WsLayout L;
+  L.compute(nVtx, vtxStrideBytes, M);
+  return L.total;
+}
+
+reindex_status reindex_mesh_ws(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t nElem, int k,
+                               void* out_vtx, int64_t* out_nVtx, int32_t* out_idx, void* ws, size_t wsBytes,
+                               reindex_stream_t stream) {
+  int64_t M = 0;
+  reindex_status r = check_args(nVtx, S, nElem, k, &M);
+  if (r != REINDEX_OK) return r;
+  if ((r = check_ptrs(vtx, nVtx, S, idx, M, out_vtx, out_nVtx, out_idx)) != REINDEX_OK) return r;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (M == 0) return cuda_status(launch_set_count(out_nVtx, 0, st));
+  if (nVtx == 0) return REINDEX_ERR_INDEX_RANGE;
+  WsLayout L;
+  L.compute(nVtx, S, M);
+  if (ws == nullptr || !aligned(ws, 256) || wsBytes < L.total) return REINDEX_ERR_INVALID_ARG;
+  return run_pipeline(vtx, nVtx, S, idx, M, out_vtx, out_nVtx, out_idx, ws, L, st);
+}
+
+reindex_status reindex_mesh(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t nElem, int k,
+                            void* out_vtx, int64_t* out_nVtx, int32_t* out_idx, reindex_stream_t stream) {
+  int64_t M = 0;
+  reindex_status r = check_args(nVtx, S, nElem, k, &M);
+  if (r != REINDEX_OK) return r;
+  if ((r = check_ptrs(vtx, nVtx, S, idx, M, out_vtx, out_nVtx, out_idx)) != REINDEX_OK) return r;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (M == 0) return cuda_status(launch_set_count(out_nVtx, 0, st));
+  if (nVtx == 0) return REINDEX_ERR_INDEX_RANGE;
+  WsLayout L;
+  L.compute(nVtx, S, M);
+  set_pool_threshold();
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, L.total, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  r = run_pipeline(vtx, nVtx, S, idx, M, out_vtx, out_nVtx, out_idx, ws, L, st);
+  e = cudaFreeAsync(ws, st);
+  if (r == REINDEX_OK && e != cudaSuccess) r = cuda_status(e);
+  return r;
+}
+
+reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int S, const int32_t* host_idx,
+                                 int64_t nElem, int k, void* host_out_vtx, int64_t* host_out_nVtx,
+                                 int32_t* host_out_idx, reindex_stream_t stream) {
+  int64_t M = 0;
+  reindex_status r = check_args(nVtx, S, nElem, k, &M);
+  if (r != REINDEX_OK) return r;
+  if (host_out_nVtx == nullptr) return REINDEX_ERR_INVALID_ARG;
+  if (M == 0) {
+    *host_out_nVtx = 0;
+    return REINDEX_OK;
+  }
+  if (!host_idx || !host_out_idx || !host_out_vtx || !host_vtx) return REINDEX_ERR_INVALID_ARG;
+  if (nVtx == 0) return REINDEX_ERR_INDEX_RANGE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  WsLayout L;
+  L.compute(nVtx, S, M);
+  const size_t b_vtx = align_up((size_t)nVtx * S, 256), b_idx = align_up((size_t)M * 4, 256);
+  const size_t b_out = align_up((size_t)L.Umax * S, 256);
+  const size_t total = b_vtx + 2 * b_idx + b_out + 256 + L.total;
+  set_pool_threshold();
+  unsigned char* d = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), total, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  void* d_vtx = d;
+  int32_t* d_idx = reinterpret_cast<int32_t*>(d + b_vtx);
+  int32_t* d_oidx = reinterpret_cast<int32_t*>(d + b_vtx + b_idx);
+  void* d_ovtx = d + b_vtx + 2 * b_idx;
+  int64_t* d_n = reinterpret_cast<int64_t*>(d + b_vtx + 2 * b_idx + b_out);
+  void* d_ws = d + b_vtx + 2 * b_idx + b_out + 256;
+  int64_t D = -1;
+  do {
+    if ((e = cudaMemcpyAsync(d_vtx, host_vtx, (size_t)nVtx * S, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(d_idx, host_idx, (size_t)M * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    r = run_pipeline(d_vtx, nVtx, S, d_idx, M, d_ovtx, d_n, d_oidx, d_ws, L, st);
+    if (r != REINDEX_OK) break;
+    if ((e = cudaMemcpyAsync(host_out_idx, d_oidx, (size_t)M * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(&D, d_n, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+    if (D > 0 &&
+        (e = cudaMemcpyAsync(host_out_vtx, d_ovtx, (size_t)D * S, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      break;
+  } while (0);
+  cudaError_t ef = cudaFreeAsync(d, st);
+  cudaError_t es = cudaStreamSynchronize(st);
+  if (r != REINDEX_OK) return r;
+  if (e != cudaSuccess) return cuda_status(e);
+  if (ef != cudaSuccess) return cuda_status(ef);
+  if (es != cudaSuccess) return cuda_status(es);
+  *host_out_nVtx = D;
+  if (D < 0) return (reindex_status)(-D);
+  return REINDEX_OK;
+}
+
+reindex_status reindex_stream_status(reindex_stream_t stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return REINDEX_ERR_CUDA;
+  uint32_t v = 0;
+  if (read_and_clear_sticky(&v, st) != cudaSuccess) return REINDEX_ERR_CUDA;
+  return (reindex_status)v;
+}
+
+void reindex_profile_enable(int on) {
+  std::lock_guard<std::mutex> g(prof::mu);
+  prof::enabled = on != 0;
+}
+
+int reindex_profile_collect(reindex_profile_record* out, int maxRecords) {
+  std::vector<prof::Pending> recs;
+  std::vector<uint8_t*> pins;
+  {
+    std::lock_guard<std::mutex> g(prof::mu);
+    recs.swap(prof::pending);
+    pins.swap(prof::pinned);
+  }
+  int bad = 0;
+  for (size_t i = 0; i < recs.size(); ++i) {
+    const prof::Pending& p = recs[i];
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) != cudaSuccess || cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) bad = 1;
+    if (out && (int)i < maxRecords) {
+      out[i].kernel = p.kernel;
+      out[i].digit = p.digit;
+      out[i].skipped = (p.skip && p.digit >= 0) ? (int)p.skip[p.digit] : 0;
+      out[i].ms = ms;
+    }
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (uint8_t* h : pins) cudaFreeHost(h);
+  return bad ? -1 : (int)recs.size();
+}
+
+const char* reindex_kernel_name(int kernel) {
+  static const char* names[REINDEX_K_COUNT] = {"clear", "used_flags", "compact_hist", "sort_plan",
+                                               "onesweep", "head_scan", "remap", "finalize"};
+  return (kernel >= 0 && kernel < REINDEX_K_COUNT) ? names[kernel] : "unknown";
+}
+
+}  // extern "C"

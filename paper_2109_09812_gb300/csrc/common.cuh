@@ -1,0 +1,315 @@
+// Internal definitions shared by the kernels and the host orchestration of the re-indexing
+// library: workspace layout, item layouts of the sort, decoupled look-back primitives and
+// warp/block scans.  Nothing here is part of the public ABI (include/reindex.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace reindex {
+
+// ---------------------------------------------------------------------------------------------
+// Tunables (compile-time tile shapes; the look-back tables are sized from them).
+constexpr int kThreads = 256;              // threads per CTA for every tiled kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kCompactRows = 8;            // 32-vertex rows per warp in the compaction
+constexpr int kCompactTile = kWarps * kCompactRows * 32;   // 2048 vertices per tile
+constexpr int kSortIpt = 16;               // items per thread in a sort pass
+constexpr int kSortTile = kThreads * kSortIpt;             // 4096 items per tile
+constexpr int kHeadIpt = 16;               // items per thread in the head scan
+constexpr int kHeadTile = kThreads * kHeadIpt;             // 4096 items per tile
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;    // 256 digit values
+constexpr int kMaxDigits = 16;             // 16-byte keys -> 16 byte-digits
+
+// Look-back status word: 2-bit flag + 30-bit count.
+constexpr uint32_t kFlagAgg = 1u << 30;    // tile aggregate only
+constexpr uint32_t kFlagPre = 2u << 30;    // inclusive prefix through this tile
+constexpr uint32_t kFlagMask = 3u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr int64_t kMaxCount = (int64_t)kValMask;  // largest count a status word can carry
+
+// Bounded spin: every wait on another CTA gives up after this many polls, records
+// REINDEX_ERR_TIMEOUT and publishes a (meaningless) prefix so that no successor waits forever.
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// Device-side error codes (same numbers as reindex_status).
+constexpr uint32_t kErrIndexRange = 4;
+constexpr uint32_t kErrTimeout = 5;
+constexpr uint32_t kErrInternal = 7;
+
+// ---------------------------------------------------------------------------------------------
+// Workspace.
+struct Control {             // zeroed at the start of every call
+  uint32_t err;              // first device-detected error (0 = none)
+  uint32_t U;                // number of used vertices (written by the last compaction tile)
+  uint32_t ctr[32];          // atomic tile counters: [0] compaction, [1 + d] sort digit d,
+                             // [1 + kMaxDigits] head scan
+  uint32_t pad[30];
+};
+static_assert(sizeof(Control) == 256, "Control block is one 256-byte line");
+
+struct Plan {                // written by the sort-plan kernel
+  uint32_t U;
+  uint32_t final_sel;        // 0: sorted items end in buffer A, 1: in buffer B
+  uint8_t skip[kMaxDigits];  // 1: digit d is constant over all items; its pass moves nothing
+  uint8_t src[kMaxDigits];   // buffer the pass for digit d reads (0 = A, 1 = B)
+  uint8_t area[kMaxDigits];  // which of the two look-back areas the pass uses
+  uint8_t pad[16];
+  uint32_t base[kMaxDigits][kRadix];  // exclusive prefix of the digit histogram
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct WsLayout {
+  int S = 0, K = 0, P = 0;
+  int64_t nVtx = 0, M = 0, Umax = 0;
+  int64_t tilesV = 0, tilesS = 0, tilesH = 0;
+  size_t off_ctrl = 0, off_hist = 0, off_lb_compact = 0, off_lb_head = 0, off_lb_sort = 0,
+         off_bitmask = 0, zero_bytes = 0;
+  size_t off_plan = 0, off_itemsA = 0, off_itemsB = 0, items_bytes = 0, off_old2new = 0, total = 0;
+
+  void compute(int64_t n, int s, int64_t m) {
+    S = s; K = s / 4; P = s; nVtx = n; M = m;
+    Umax = n < m ? n : m;
+    tilesV = (n + kCompactTile - 1) / kCompactTile;
+    tilesS = (Umax + kSortTile - 1) / kSortTile;
+    tilesH = (Umax + kHeadTile - 1) / kHeadTile;
+    size_t o = 0;
+    off_ctrl = o;        o += sizeof(Control);
+    off_hist = o;        o = align_up(o + (size_t)P * kRadix * 4, 256);
+    off_lb_compact = o;  o = align_up(o + (size_t)tilesV * 4, 256);
+    off_lb_head = o;     o = align_up(o + (size_t)tilesH * 4, 256);
+    off_lb_sort = o;     o = align_up(o + (size_t)2 * tilesS * kRadix * 4, 256);
+    off_bitmask = o;     o = align_up(o + (size_t)((n + 31) / 32) * 4, 256);
+    zero_bytes = o;
+    off_plan = o;        o = align_up(o + sizeof(Plan), 256);
+    items_bytes = align_up((size_t)Umax * (size_t)(S + 4), 256);
+    off_itemsA = o;      o += items_bytes;
+    off_itemsB = o;      o += items_bytes;
+    off_old2new = o;     o = align_up(o + (size_t)n * 4, 256);
+    total = o;
+  }
+};
+
+// Device views of the workspace, passed by value to the kernels.
+struct WsPtrs {
+  Control* ctrl;
+  uint32_t* hist;        // [P][256]
+  uint32_t* lb_compact;  // [tilesV]
+  uint32_t* lb_head;     // [tilesH]
+  uint32_t* lb_sort;     // [2][tilesS][256]
+  uint32_t* bitmask;     // [ceil(nVtx/32)]
+  Plan* plan;
+  unsigned char* itemsA;
+  unsigned char* itemsB;
+  uint32_t* old2new;     // [nVtx]
+  int64_t tilesS;        // stride of one look-back area in tiles
+  int64_t Umax;          // capacity of each item buffer (SoA id plane offset)
+};
+
+inline WsPtrs ws_ptrs(void* ws, const WsLayout& L) {
+  unsigned char* b = static_cast<unsigned char*>(ws);
+  WsPtrs p;
+  p.ctrl = reinterpret_cast<Control*>(b + L.off_ctrl);
+  p.hist = reinterpret_cast<uint32_t*>(b + L.off_hist);
+  p.lb_compact = reinterpret_cast<uint32_t*>(b + L.off_lb_compact);
+  p.lb_head = reinterpret_cast<uint32_t*>(b + L.off_lb_head);
+  p.lb_sort = reinterpret_cast<uint32_t*>(b + L.off_lb_sort);
+  p.bitmask = reinterpret_cast<uint32_t*>(b + L.off_bitmask);
+  p.plan = reinterpret_cast<Plan*>(b + L.off_plan);
+  p.itemsA = b + L.off_itemsA;
+  p.itemsB = b + L.off_itemsB;
+  p.old2new = reinterpret_cast<uint32_t*>(b + L.off_old2new);
+  p.tilesS = L.tilesS;
+  p.Umax = L.Umax;
+  return p;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Sort items: K key words (word 0 most significant) plus the old vertex index.
+//   S = 4, 12: array of structures, one 8- or 16-byte vector per item {k..., id}
+//   S = 8, 16: structure of arrays, an 8- or 16-byte key vector per item, then an id plane
+template <int S>
+struct Item {
+  static constexpr int K = S / 4;
+  uint32_t k[K];
+  uint32_t id;
+};
+
+template <int S>
+struct ItemIO;
+
+template <>
+struct ItemIO<4> {
+  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t, int64_t i, Item<4>& it) {
+    uint2 v = reinterpret_cast<const uint2*>(buf)[i];
+    it.k[0] = v.x; it.id = v.y;
+  }
+  static __device__ __forceinline__ void store(unsigned char* buf, int64_t, int64_t i, const Item<4>& it) {
+    reinterpret_cast<uint2*>(buf)[i] = make_uint2(it.k[0], it.id);
+  }
+};
+
+template <>
+struct ItemIO<12> {
+  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t, int64_t i, Item<12>& it) {
+    uint4 v = reinterpret_cast<const uint4*>(buf)[i];
+    it.k[0] = v.x; it.k[1] = v.y; it.k[2] = v.z; it.id = v.w;
+  }
+  static __device__ __forceinline__ void store(unsigned char* buf, int64_t, int64_t i, const Item<12>& it) {
+    reinterpret_cast<uint4*>(buf)[i] = make_uint4(it.k[0], it.k[1], it.k[2], it.id);
+  }
+};
+
+template <>
+struct ItemIO<8> {
+  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t cap, int64_t i, Item<8>& it) {
+    uint2 v = reinterpret_cast<const uint2*>(buf)[i];
+    it.k[0] = v.x; it.k[1] = v.y;
+    it.id = reinterpret_cast<const uint32_t*>(buf + cap * 8)[i];
+  }
+  static __device__ __forceinline__ void store(unsigned char* buf, int64_t cap, int64_t i, const Item<8>& it) {
+    reinterpret_cast<uint2*>(buf)[i] = make_uint2(it.k[0], it.k[1]);
+    reinterpret_cast<uint32_t*>(buf + cap * 8)[i] = it.id;
+  }
+};
+
+template <>
+struct ItemIO<16> {
+  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t cap, int64_t i, Item<16>& it) {
+    uint4 v = reinterpret_cast<const uint4*>(buf)[i];
+    it.k[0] = v.x; it.k[1] = v.y; it.k[2] = v.z; it.k[3] = v.w;
+    it.id = reinterpret_cast<const uint32_t*>(buf + cap * 16)[i];
+  }
+  static __device__ __forceinline__ void store(unsigned char* buf, int64_t cap, int64_t i, const Item<16>& it) {
+    reinterpret_cast<uint4*>(buf)[i] = make_uint4(it.k[0], it.k[1], it.k[2], it.k[3]);
+    reinterpret_cast<uint32_t*>(buf + cap * 16)[i] = it.id;
+  }
+};
+
+// Vertex key loads from the caller's vertex array (stride S, natural alignment).
+template <int S>
+__device__ __forceinline__ void load_key(const void* vtx, int64_t i, uint32_t (&k)[S / 4]) {
+  if constexpr (S == 4) {
+    k[0] = reinterpret_cast<const uint32_t*>(vtx)[i];
+  } else if constexpr (S == 8) {
+    uint2 v = reinterpret_cast<const uint2*>(vtx)[i];
+    k[0] = v.x; k[1] = v.y;
+  } else if constexpr (S == 12) {
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(vtx) + i * 3;
+    k[0] = p[0]; k[1] = p[1]; k[2] = p[2];
+  } else {
+    uint4 v = reinterpret_cast<const uint4*>(vtx)[i];
+    k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void store_key(void* out, int64_t i, const uint32_t (&k)[S / 4]) {
+  if constexpr (S == 4) {
+    reinterpret_cast<uint32_t*>(out)[i] = k[0];
+  } else if constexpr (S == 8) {
+    reinterpret_cast<uint2*>(out)[i] = make_uint2(k[0], k[1]);
+  } else if constexpr (S == 12) {
+    uint32_t* p = reinterpret_cast<uint32_t*>(out) + i * 3;
+    p[0] = k[0]; p[1] = k[1]; p[2] = k[2];
+  } else {
+    reinterpret_cast<uint4*>(out)[i] = make_uint4(k[0], k[1], k[2], k[3]);
+  }
+}
+
+// Byte digit d of a key (d = 0 is the least significant byte of the least significant word).
+template <int K>
+__device__ __forceinline__ uint32_t key_digit(const uint32_t (&k)[K], int d) {
+  const int w = K - 1 - (d >> 2);
+  uint32_t word = k[0];
+#pragma unroll
+  for (int q = 1; q < K; ++q)
+    if (q == w) word = k[q];
+  return (word >> ((d & 3) * 8)) & 0xFFu;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Memory-model helpers for decoupled look-back.
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void record_error(Control* c, uint32_t code) { atomicCAS(&c->err, 0u, code); }
+
+// Block-uniform read of the error word (every thread of the CTA gets the same answer, so an
+// early return never leaves a barrier half-populated).
+__device__ __forceinline__ bool block_error(const Control* c) {
+  __shared__ uint32_t s_err;
+  if (threadIdx.x == 0) s_err = *(volatile const uint32_t*)&c->err;
+  __syncthreads();
+  const bool e = s_err != 0;
+  __syncthreads();
+  return e;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Wait until *p carries a flag; bounded.  Returns the status word (flag + value), or on
+// timeout records the error and returns a prefix flag with value 0.
+__device__ __forceinline__ uint32_t wait_status(const uint32_t* p, Control* c) {
+  uint32_t s = ld_relaxed(p);
+  uint32_t polls = 0;
+  while ((s & kFlagMask) == 0) {
+    ++polls;
+    if ((polls & 255u) == 0) {
+      if (polls >= kSpinLimit || ld_relaxed(&c->err) != 0) {
+        record_error(c, kErrTimeout);
+        return kFlagPre;
+      }
+      __nanosleep(64);
+    }
+    s = ld_relaxed(p);
+  }
+  return s;
+}
+
+// Decoupled look-back over one counter per tile, done by one full warp: returns the exclusive
+// prefix of tile `tile` (> 0) in every lane.  Each round inspects the 32 predecessors
+// tile-1 .. tile-32 at once, stops at the nearest one carrying an inclusive prefix.
+__device__ __forceinline__ uint32_t warp_lookback(const uint32_t* lb, int64_t tile, Control* c) {
+  const int lane = threadIdx.x & 31;
+  uint32_t excl = 0;
+  int64_t hi = tile - 1;  // newest predecessor not yet accumulated
+  while (true) {
+    const int64_t t = hi - lane;
+    uint32_t s = (t >= 0) ? wait_status(lb + t, c) : kFlagPre;  // before tile 0: prefix 0
+    const uint32_t pre_mask = __ballot_sync(0xffffffffu, (s & kFlagMask) == kFlagPre);
+    const int stop = __ffs(pre_mask) - 1;  // nearest predecessor with an inclusive prefix
+    uint32_t v = (pre_mask != 0 && lane > stop) ? 0u : (s & kValMask);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (pre_mask != 0) break;
+    hi -= 32;
+  }
+  return excl;
+}
+
+// Inclusive warp scan.
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+}  // namespace reindex

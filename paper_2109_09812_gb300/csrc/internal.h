@@ -1,0 +1,44 @@
+// Host-side launch wrappers of the re-indexing kernels (one translation unit per kernel
+// family so that they compile in parallel).  Internal; the public ABI is include/reindex.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace reindex {
+
+struct LaunchCfg {
+  int sms = 0;          // multiprocessors of the current device
+  int occ_compact = 0;  // resident CTAs per SM of each persistent kernel
+  int occ_sort = 0;
+  int occ_head = 0;
+};
+
+// Per-device launch configuration (computed once per device, thread-safe).
+const LaunchCfg& launch_cfg(int S);
+
+cudaError_t launch_clear(void* p, size_t bytes, const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_used_flags(const int32_t* idx, int64_t M, int64_t nVtx, WsPtrs ws, const LaunchCfg& c,
+                              cudaStream_t st);
+cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
+                           cudaStream_t st);
+cudaError_t launch_sort_plan(int S, WsPtrs ws, cudaStream_t st);
+cudaError_t launch_onesweep(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx,
+                             const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_remap(const int32_t* idx, int32_t* out_idx, int64_t M, WsPtrs ws, const LaunchCfg& c,
+                         cudaStream_t st);
+cudaError_t launch_finalize(WsPtrs ws, int64_t* out_nVtx, cudaStream_t st);
+cudaError_t launch_set_count(int64_t* out_nVtx, int64_t value, cudaStream_t st);
+
+// Occupancy queries for the persistent kernels (per template instantiation).
+int occupancy_compact(int S);
+int occupancy_sort(int S);
+int occupancy_head(int S);
+
+// Device-wide sticky error word (read and cleared by reindex_stream_status).
+cudaError_t read_and_clear_sticky(uint32_t* value, cudaStream_t st);
+
+}  // namespace reindex

@@ -1,0 +1,147 @@
+// Stable compaction of the used vertices into (key, old index) sort items, fused with the
+// upfront digit histograms of the radix sort.
+//
+// The paper (Section 2.1) instead overwrites every unused vertex with a used one and then sorts
+// all nVtx vertices.  An overwritten vertex is a copy of a used key, so the set of distinct keys
+// and every used vertex's new index are unchanged; dropping the unused vertices here gives the
+// same result while sorting U <= nVtx items instead of nVtx.
+//
+// Tiles of 2048 vertices (8 warps x 8 rows x 32 lanes); a tile's output offset comes from a
+// decoupled look-back over per-tile used counts, so items keep vertex order.  The same pass
+// counts, per byte digit d of the key, how many used vertices have each digit value.
+#include "internal.h"
+
+namespace reindex {
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ vtx, int64_t nVtx, WsPtrs ws,
+                                                       int64_t tilesV) {
+  constexpr int K = S / 4;
+  constexpr int P = S;  // byte digits per key
+  __shared__ uint32_t s_hist[P * kRadix];
+  __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint32_t s_tile, s_prefix;
+  Control* ctrl = ws.ctrl;
+  if (block_error(ctrl)) return;  // an invalid index was seen: nothing downstream is meaningful
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int i = t; i < P * kRadix; i += kThreads) s_hist[i] = 0;
+
+  for (;;) {
+    if (t == 0) s_tile = atomicAdd(&ctrl->ctr[0], 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= tilesV) break;
+    const int64_t vbase = tile * kCompactTile + (int64_t)w * kCompactRows * 32;
+
+    // Used bits of this warp's 8 rows of 32 vertices (bits past nVtx are never set).
+    uint32_t myword = 0;
+    if (lane < kCompactRows) {
+      const int64_t wi = (vbase >> 5) + lane;
+      if (wi * 32 < nVtx) myword = ws.bitmask[wi];
+    }
+    uint32_t k[kCompactRows][K];
+    uint32_t pos[kCompactRows];
+    uint32_t used = 0, cnt = 0;
+#pragma unroll
+    for (int r = 0; r < kCompactRows; ++r) {
+      const uint32_t word = __shfl_sync(0xffffffffu, myword, r);
+      const uint32_t u = (word >> lane) & 1u;
+      if (u) load_key<S>(vtx, vbase + r * 32 + lane, k[r]);
+      pos[r] = cnt + __popc(word & lanemask_lt());
+      cnt += __popc(word);
+      used |= u << r;
+    }
+    if (lane == 0) s_warp[w] = cnt;
+    __syncthreads();
+    uint32_t woff = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+      const uint32_t c = s_warp[q];
+      woff += (q < w) ? c : 0u;
+      total += c;
+    }
+    if (w == 0) {
+      uint32_t prefix = 0;
+      uint32_t* my = ws.lb_compact + tile;
+      if (tile == 0) {
+        if (lane == 0) st_relaxed(my, kFlagPre | total);
+      } else {
+        if (lane == 0) st_relaxed(my, kFlagAgg | total);
+        prefix = warp_lookback(ws.lb_compact, tile, ctrl);
+        if (lane == 0) st_relaxed(my, kFlagPre | ((prefix + total) & kValMask));
+      }
+      if (lane == 0) {
+        s_prefix = prefix;
+        if (tile == tilesV - 1) ctrl->U = prefix + total;
+      }
+    }
+    __syncthreads();
+    const int64_t obase = (int64_t)s_prefix + woff;
+
+#pragma unroll
+    for (int r = 0; r < kCompactRows; ++r) {
+      const uint32_t u = (used >> r) & 1u;
+      const uint32_t umask = __ballot_sync(0xffffffffu, u);
+      if (umask == 0) continue;  // warp-uniform
+      if (u) {
+        Item<S> it;
+#pragma unroll
+        for (int q = 0; q < K; ++q) it.k[q] = k[r][q];
+        it.id = (uint32_t)(vbase + r * 32 + lane);
+        ItemIO<S>::store(ws.itemsA, ws.Umax, obase + pos[r], it);
+      }
+      // Histograms: one shared-memory atomic per used item and digit, or a single one per warp
+      // when the digit is the same in every used lane (common for constant bytes).
+      const int leader = __ffs(umask) - 1;
+      const uint32_t n_used = __popc(umask);
+#pragma unroll
+      for (int d = 0; d < P; ++d) {
+        const uint32_t dig = u ? key_digit<K>(k[r], d) : 0u;
+        const uint32_t d0 = __shfl_sync(0xffffffffu, dig, leader);
+        if (__all_sync(0xffffffffu, !u || dig == d0)) {
+          if (lane == leader) atomicAdd(&s_hist[d * kRadix + d0], n_used);
+        } else if (u) {
+          atomicAdd(&s_hist[d * kRadix + dig], 1u);
+        }
+      }
+    }
+    __syncthreads();  // s_tile, s_warp and s_prefix are rewritten by the next tile
+  }
+  __syncthreads();
+  for (int i = t; i < P * kRadix; i += kThreads) {
+    const uint32_t c = s_hist[i];
+    if (c) atomicAdd(ws.hist + i, c);
+  }
+}
+
+template <int S>
+static int occ() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_compact<S>, kThreads, 0);
+  return n < 1 ? 1 : n;
+}
+
+int occupancy_compact(int S) {
+  switch (S) {
+    case 4: return occ<4>();
+    case 8: return occ<8>();
+    case 12: return occ<12>();
+    default: return occ<16>();
+  }
+}
+
+cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
+                           cudaStream_t st) {
+  if (tilesV == 0) return cudaSuccess;
+  int64_t g = (int64_t)c.sms * c.occ_compact;
+  if (g > tilesV) g = tilesV;
+  switch (S) {
+    case 4: k_compact<4><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV); break;
+    case 8: k_compact<8><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV); break;
+    case 12: k_compact<12><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV); break;
+    default: k_compact<16><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace reindex

@@ -1,0 +1,155 @@
+// Steps 4-7 of the pipeline fused into one pass over the sorted (key, old index) items:
+//   nodup[j]  = j == 0 || key[j] != key[j-1]                 (Section 2.2, run heads)
+//   newIdx[j] = number of run heads before j, minus one unless j is itself a head
+//             = inclusive prefix sum of nodup minus one      (Section 2.2 and its footnote)
+//   oldToNew[orgID[j]] = newIdx[j]                           (Section 2.4: perm composed with newIdx)
+//   newVtx[newIdx[j]] = key[j] for every head j              (Section 2.3)
+//   *out_nVtx = total number of heads                        (Section 2.3, newN)
+// The prefix sum is a decoupled look-back scan over tiles of 4096 items; neither nodup nor
+// newIdx is materialised.
+#include "internal.h"
+
+namespace reindex {
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_head_scan(WsPtrs ws, void* __restrict__ out_vtx,
+                                                         int64_t* __restrict__ out_nVtx, uint32_t nVtx) {
+  constexpr int K = S / 4;
+  __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint32_t s_tile, s_prefix;
+  Control* ctrl = ws.ctrl;
+  if (block_error(ctrl)) return;
+  const Plan* plan = ws.plan;
+  const uint32_t U = plan->U;
+  const int64_t ntiles = ((int64_t)U + kHeadTile - 1) / kHeadTile;
+  const unsigned char* buf = plan->final_sel ? ws.itemsB : ws.itemsA;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (U == 0) {
+    if (blockIdx.x == 0 && t == 0) *out_nVtx = 0;
+    return;
+  }
+
+  for (;;) {
+    if (t == 0) s_tile = atomicAdd(&ctrl->ctr[1 + kMaxDigits], 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= ntiles) break;
+    const int64_t wbase = tile * kHeadTile + (int64_t)w * 32 * kHeadIpt;
+
+    Item<S> it[kHeadIpt];
+#pragma unroll
+    for (int r = 0; r < kHeadIpt; ++r) {
+      const int64_t j = wbase + r * 32 + lane;
+      if (j < U) ItemIO<S>::load(buf, ws.Umax, j, it[r]);
+    }
+    uint32_t prevk[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) prevk[q] = 0;
+    if (lane == 0 && wbase > 0 && wbase < U) {
+      Item<S> p;
+      ItemIO<S>::load(buf, ws.Umax, wbase - 1, p);
+#pragma unroll
+      for (int q = 0; q < K; ++q) prevk[q] = p.k[q];
+    }
+
+    uint32_t within[kHeadIpt];
+    uint32_t heads = 0, cnt = 0;
+#pragma unroll
+    for (int r = 0; r < kHeadIpt; ++r) {
+      const int64_t j = wbase + r * 32 + lane;
+      bool diff = false;
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const uint32_t up = __shfl_up_sync(0xffffffffu, it[r].k[q], 1);
+        uint32_t pk;
+        if (r == 0) {
+          pk = lane ? up : prevk[q];
+        } else {
+          const uint32_t last = __shfl_sync(0xffffffffu, it[r - 1].k[q], 31);
+          pk = lane ? up : last;
+        }
+        diff |= it[r].k[q] != pk;
+      }
+      const bool head = (j < U) && (j == 0 || diff);
+      const uint32_t m = __ballot_sync(0xffffffffu, head);
+      within[r] = cnt + __popc(m & lanemask_lt());
+      heads |= (uint32_t)head << r;
+      cnt += __popc(m);
+    }
+    if (lane == 0) s_warp[w] = cnt;
+    __syncthreads();
+    uint32_t woff = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+      const uint32_t c = s_warp[q];
+      woff += (q < w) ? c : 0u;
+      total += c;
+    }
+    if (w == 0) {
+      uint32_t prefix = 0;
+      uint32_t* my = ws.lb_head + tile;
+      if (tile == 0) {
+        if (lane == 0) st_relaxed(my, kFlagPre | total);
+      } else {
+        if (lane == 0) st_relaxed(my, kFlagAgg | total);
+        prefix = warp_lookback(ws.lb_head, tile, ctrl);
+        if (lane == 0) st_relaxed(my, kFlagPre | ((prefix + total) & kValMask));
+      }
+      if (lane == 0) {
+        s_prefix = prefix;
+        if (tile == ntiles - 1) *out_nVtx = (int64_t)(prefix + total);
+      }
+    }
+    __syncthreads();
+    const uint32_t ebase = s_prefix + woff;
+#pragma unroll
+    for (int r = 0; r < kHeadIpt; ++r) {
+      const int64_t j = wbase + r * 32 + lane;
+      if (j < U) {
+        const bool head = (heads >> r) & 1u;
+        const uint32_t e = ebase + within[r];  // heads strictly before j
+        const uint32_t nid = head ? e : e - 1u;
+        if (it[r].id < nVtx) {
+          ws.old2new[it[r].id] = nid;
+          if (head) store_key<S>(out_vtx, nid, it[r].k);
+        } else {
+          record_error(ctrl, kErrInternal);  // corrupted item: never write out of range
+        }
+      }
+    }
+    __syncthreads();  // s_tile / s_warp / s_prefix reuse
+  }
+}
+
+template <int S>
+static int occ() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_head_scan<S>, kThreads, 0);
+  return n < 1 ? 1 : n;
+}
+
+int occupancy_head(int S) {
+  switch (S) {
+    case 4: return occ<4>();
+    case 8: return occ<8>();
+    case 12: return occ<12>();
+    default: return occ<16>();
+  }
+}
+
+cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx,
+                             const LaunchCfg& c, cudaStream_t st) {
+  int64_t tiles = (ws.Umax + kHeadTile - 1) / kHeadTile;
+  int64_t g = (int64_t)c.sms * c.occ_head;
+  if (g > tiles) g = tiles;
+  if (g < 1) g = 1;
+  switch (S) {
+    case 4: k_head_scan<4><<<(int)g, kThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
+    case 8: k_head_scan<8><<<(int)g, kThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
+    case 12: k_head_scan<12><<<(int)g, kThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
+    default: k_head_scan<16><<<(int)g, kThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace reindex

@@ -1,0 +1,191 @@
+// Streaming kernels of the re-indexing pipeline:
+//   k_clear       zero the workspace tables that must start at zero
+//   k_used_flags  Section 2.1: isUsed[idx[j]] = true, as one bit per vertex, with range check
+//   k_sort_plan   exclusive digit offsets of the upfront histograms; which radix passes are
+//                 trivial (digit constant over all items) and the buffer each pass reads
+//   k_remap       Section 2.4: out_idx[j] = oldToNew[idx[j]]
+//   k_finalize    propagate a device-detected error into *out_nVtx and the sticky word
+#include "internal.h"
+
+namespace reindex {
+
+// Device-wide sticky error (one per device context); see reindex_stream_status.
+__device__ uint32_t g_sticky_err;
+__device__ uint32_t g_sticky_out;
+
+__global__ void __launch_bounds__(kThreads) k_clear(uint4* p, int64_t n16) {
+  const uint4 z = make_uint4(0, 0, 0, 0);
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n16; i += (int64_t)gridDim.x * kThreads)
+    p[i] = z;
+}
+
+__device__ __forceinline__ void mark_used(int32_t v, uint32_t nVtx, uint32_t* bitmask, bool& bad) {
+  if ((uint32_t)v >= nVtx) {  // negative indices wrap to >= 2^31 > nVtx
+    bad = true;
+  } else {
+    atomicOr(bitmask + ((uint32_t)v >> 5), 1u << ((uint32_t)v & 31u));  // result unused -> RED.OR
+  }
+}
+
+// One bit per vertex, set by every index that references it (Section 2.1).  Indices are read
+// with 128-bit loads when the array is 16-byte aligned.
+template <bool kVec>
+__global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int64_t M, uint32_t nVtx,
+                                                          uint32_t* bitmask, Control* ctrl) {
+  bool bad = false;
+  const int64_t t0 = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  int64_t done = 0;
+  if (kVec) {
+    const int4* v4 = reinterpret_cast<const int4*>(idx);
+    const int64_t n4 = M >> 2;
+    for (int64_t i = t0; i < n4; i += stride) {
+      const int4 q = v4[i];
+      mark_used(q.x, nVtx, bitmask, bad);
+      mark_used(q.y, nVtx, bitmask, bad);
+      mark_used(q.z, nVtx, bitmask, bad);
+      mark_used(q.w, nVtx, bitmask, bad);
+    }
+    done = n4 << 2;
+  }
+  for (int64_t i = done + t0; i < M; i += stride) mark_used(idx[i], nVtx, bitmask, bad);
+  if (bad) record_error(ctrl, kErrIndexRange);
+}
+
+// Digit offsets and pass plan (one CTA of 256 threads; thread t owns digit value t).
+__global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P) {
+  __shared__ uint32_t s_warp[kRadix / 32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const uint32_t U = ws.ctrl->U;
+  Plan* plan = ws.plan;
+  uint32_t sel = 0, q = 0;  // identical in every thread
+  for (int d = 0; d < P; ++d) {
+    const uint32_t c = ws.hist[d * kRadix + t];
+    // A digit whose value is the same for all U items: that pass is the identity.
+    const int trivial = __syncthreads_or(c == U);
+    const uint32_t incl = warp_incl_scan(c);
+    if (lane == 31) s_warp[w] = incl;
+    __syncthreads();
+    uint32_t off = 0;
+    for (int k = 0; k < w; ++k) off += s_warp[k];
+    plan->base[d][t] = off + incl - c;
+    __syncthreads();
+    if (t == 0) {
+      plan->skip[d] = (uint8_t)trivial;
+      plan->src[d] = (uint8_t)sel;
+      plan->area[d] = (uint8_t)(q & 1u);
+    }
+    if (!trivial) {
+      sel ^= 1u;
+      ++q;
+    }
+  }
+  if (t == 0) {
+    for (int d = P; d < kMaxDigits; ++d) plan->skip[d] = 1;
+    plan->U = U;
+    plan->final_sel = sel;
+  }
+}
+
+// out_idx[j] = oldToNew[idx[j]] (Section 2.4).  Safe in place: each slot is read and written
+// by the same thread.
+template <bool kVec>
+__global__ void __launch_bounds__(kThreads) k_remap(const int32_t* idx, int32_t* out, int64_t M,
+                                                     const uint32_t* __restrict__ o2n, const Control* ctrl) {
+  if (ctrl->err) return;  // outputs are unspecified after a device-detected error
+  const int64_t t0 = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  int64_t done = 0;
+  if (kVec) {
+    const int4* in4 = reinterpret_cast<const int4*>(idx);
+    int4* out4 = reinterpret_cast<int4*>(out);
+    const int64_t n4 = M >> 2;
+    for (int64_t i = t0; i < n4; i += stride) {
+      const int4 q = in4[i];
+      int4 r;
+      r.x = (int32_t)__ldg(o2n + q.x);
+      r.y = (int32_t)__ldg(o2n + q.y);
+      r.z = (int32_t)__ldg(o2n + q.z);
+      r.w = (int32_t)__ldg(o2n + q.w);
+      out4[i] = r;
+    }
+    done = n4 << 2;
+  }
+  for (int64_t i = done + t0; i < M; i += stride) out[i] = (int32_t)__ldg(o2n + idx[i]);
+}
+
+__global__ void k_finalize(Control* ctrl, int64_t* out_nVtx) {
+  const uint32_t e = ctrl->err;
+  if (e) {
+    *out_nVtx = -(int64_t)e;
+    atomicCAS(&g_sticky_err, 0u, e);
+  }
+}
+
+__global__ void k_set_count(int64_t* out_nVtx, int64_t v) { *out_nVtx = v; }
+
+__global__ void k_take_sticky() { g_sticky_out = atomicExch(&g_sticky_err, 0u); }
+
+static int grid_for(int64_t work_items, const LaunchCfg& c, int per_sm) {
+  int64_t g = (work_items + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)c.sms * per_sm;
+  if (g > cap) g = cap;
+  return g < 1 ? 1 : (int)g;
+}
+
+cudaError_t launch_clear(void* p, size_t bytes, const LaunchCfg& c, cudaStream_t st) {
+  const int64_t n16 = (int64_t)(bytes / 16);
+  if (n16 == 0) return cudaSuccess;
+  k_clear<<<grid_for(n16, c, 8), kThreads, 0, st>>>(static_cast<uint4*>(p), n16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_used_flags(const int32_t* idx, int64_t M, int64_t nVtx, WsPtrs ws, const LaunchCfg& c,
+                              cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  const bool vec = (reinterpret_cast<uintptr_t>(idx) & 15) == 0;
+  const int g = grid_for(vec ? (M + 3) / 4 : M, c, 8);
+  if (vec)
+    k_used_flags<true><<<g, kThreads, 0, st>>>(idx, M, (uint32_t)nVtx, ws.bitmask, ws.ctrl);
+  else
+    k_used_flags<false><<<g, kThreads, 0, st>>>(idx, M, (uint32_t)nVtx, ws.bitmask, ws.ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_plan(int S, WsPtrs ws, cudaStream_t st) {
+  k_sort_plan<<<1, kRadix, 0, st>>>(ws, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_remap(const int32_t* idx, int32_t* out_idx, int64_t M, WsPtrs ws, const LaunchCfg& c,
+                         cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  const bool vec = ((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(out_idx)) & 15) == 0;
+  const int g = grid_for(vec ? (M + 3) / 4 : M, c, 8);
+  if (vec)
+    k_remap<true><<<g, kThreads, 0, st>>>(idx, out_idx, M, ws.old2new, ws.ctrl);
+  else
+    k_remap<false><<<g, kThreads, 0, st>>>(idx, out_idx, M, ws.old2new, ws.ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(WsPtrs ws, int64_t* out_nVtx, cudaStream_t st) {
+  k_finalize<<<1, 1, 0, st>>>(ws.ctrl, out_nVtx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_count(int64_t* out_nVtx, int64_t value, cudaStream_t st) {
+  k_set_count<<<1, 1, 0, st>>>(out_nVtx, value);
+  return cudaGetLastError();
+}
+
+cudaError_t read_and_clear_sticky(uint32_t* value, cudaStream_t st) {
+  k_take_sticky<<<1, 1, 0, st>>>();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyFromSymbolAsync(value, g_sticky_out, sizeof(uint32_t), 0, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+}  // namespace reindex

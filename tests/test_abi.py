@@ -1,0 +1,76 @@
+"""The C ABI library builds, loads on a machine without a GPU, exports every entry point that
+include/reindex.h declares, and rejects bad arguments on the host before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2109_09812_gb300 as rx
+from paper_2109_09812_gb300 import build as rxbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "reindex.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_][\w\s\*]*?\b(reindex_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    rxbuild.build()
+    return rx.lib()
+
+
+def test_library_exports_every_declared_function(L):
+    names = declared_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in include/reindex.h but not exported"
+    assert sorted(rx.EXPORTED) == sorted(names)
+
+
+def test_status_strings(L):
+    for code, name in [(0, "REINDEX_OK"), (1, "REINDEX_ERR_INVALID_ARG"), (2, "REINDEX_ERR_UNSUPPORTED"),
+                       (3, "REINDEX_ERR_OOM"), (4, "REINDEX_ERR_INDEX_RANGE"), (5, "REINDEX_ERR_TIMEOUT"),
+                       (6, "REINDEX_ERR_CUDA"), (7, "REINDEX_ERR_INTERNAL")]:
+        assert rx.reindex_status_string(code) == name
+    assert rx.reindex_status_string(99) == "REINDEX_ERR_UNKNOWN"
+    assert [L.reindex_kernel_name(i).decode() for i in range(8)] == rx.KERNEL_NAMES
+
+
+def test_workspace_size_model(L):
+    # two item buffers of (S+4) bytes per potentially used vertex + oldToNew + bitmask + tables
+    n, S, ne, k = 26_424_115, 12, 8_388_608, 3
+    b = rx.reindex_workspace_size(n, S, ne, k)
+    U = min(n, ne * k)
+    assert 2 * U * (S + 4) + 4 * n <= b <= 2 * U * (S + 4) + 4 * n + 64 * 2**20
+    assert rx.reindex_workspace_size(n, 5, ne, k) == 0  # unsupported stride
+    assert rx.reindex_workspace_size(-1, 12, ne, k) == 0
+    assert rx.reindex_workspace_size(10, 12, 0, 3) > 0
+
+
+def test_host_side_argument_checks(L):
+    z = ctypes.c_void_p(0)
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails its host checks
+    # unsupported stride
+    assert L.reindex_mesh(fake, 10, 6, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
+    # negative sizes, zero arity
+    assert L.reindex_mesh(fake, -1, 12, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_INVALID_ARG
+    assert L.reindex_mesh(fake, 10, 12, fake, 3, 0, fake, fake, fake, z) == rx.REINDEX_ERR_INVALID_ARG
+    # too many vertices for 30-bit look-back counts; too many indices for int32
+    assert L.reindex_mesh(fake, 1 << 30, 12, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
+    assert L.reindex_mesh(fake, 10, 12, fake, 1 << 30, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
+    # null output count, null idx
+    assert L.reindex_mesh(fake, 10, 12, fake, 3, 3, fake, z, fake, z) == rx.REINDEX_ERR_INVALID_ARG
+    assert L.reindex_mesh(fake, 10, 12, z, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_INVALID_ARG
+    # misaligned 16-byte vertices
+    assert L.reindex_mesh(ctypes.c_void_p((1 << 20) + 4), 10, 16, fake, 3, 3, fake, fake, fake, z) \
+        == rx.REINDEX_ERR_INVALID_ARG
+    # no vertices but some indices: every index is out of range
+    assert L.reindex_mesh(z, 0, 12, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_INDEX_RANGE
+    # workspace too small
+    assert L.reindex_mesh_ws(fake, 10, 12, fake, 3, 3, fake, fake, fake, fake, 16, z) == rx.REINDEX_ERR_INVALID_ARG

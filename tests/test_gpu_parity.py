@@ -1,0 +1,246 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the serial oracle.
+
+Every comparison is element by element on the same seeded inputs: the unique vertex array,
+its length D and every remapped index.  Sizes straddle the kernels' tiles (2048 vertices per
+compaction tile, 4096 items per sort and head-scan tile) and end in ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_09812_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2109_09812_gb300 import build
+
+    build.build()
+    import paper_2109_09812_gb300 as rx
+
+    return rx
+
+
+def to_dev(vtx_words: np.ndarray, idx: np.ndarray):
+    v = torch.from_numpy(np.ascontiguousarray(vtx_words).view(np.int32)).cuda()
+    i = torch.from_numpy(np.ascontiguousarray(idx, dtype=np.int32)).cuda()
+    return v, i
+
+
+def run_gpu(rx, vtx_words, idx, k=None):
+    idx2 = idx.reshape(-1, k) if k else (idx if idx.ndim == 2 else idx.reshape(-1, 1))
+    v, i = to_dev(vtx_words, idx2)
+    out_v, out_n, out_i = rx.reindex_mesh(v, i)
+    torch.cuda.synchronize()
+    D = int(out_n.item())
+    return D, out_v[: max(D, 0)].cpu().numpy().view(np.uint32), out_i.cpu().numpy().reshape(-1)
+
+
+def assert_parity(rx, vtx_words, idx, k=None):
+    ov, oi = oracle.reindex_sort(vtx_words, idx)
+    D, gv, gi = run_gpu(rx, vtx_words, idx, k)
+    assert D == ov.shape[0], f"D: gpu {D} vs oracle {ov.shape[0]}"
+    np.testing.assert_array_equal(gv, ov)
+    np.testing.assert_array_equal(gi, oi)
+    return D
+
+
+def random_mesh(rng, n, m, K, mode):
+    if mode == "random":
+        vtx = rng.integers(0, 2**32, size=(n, K), dtype=np.uint64).astype(np.uint32)
+    elif mode == "dups":  # few distinct values per word -> many duplicates, all digits vary
+        pool = rng.integers(0, 2**32, size=(7,), dtype=np.uint64).astype(np.uint32)
+        vtx = pool[rng.integers(0, 7, size=(n, K))]
+    elif mode == "floats":  # +-0, NaN payloads, negatives, integers
+        pool = np.array([0x00000000, 0x80000000, 0x7FC00000, 0x7FC00001, 0xBF800000, 0x3F800000, 0x40400000],
+                        dtype=np.uint32)
+        vtx = pool[rng.integers(0, len(pool), size=(n, K))]
+    else:  # "const": a few constant words -> trivial radix passes get skipped
+        vtx = np.zeros((n, K), dtype=np.uint32)
+        vtx[:, -1] = rng.integers(0, 300, size=n).astype(np.uint32)
+    idx = rng.integers(0, n, size=m).astype(np.int32)
+    return vtx, idx
+
+
+SIZES = [(1, 3), (2, 4), (33, 30), (2047, 2047), (2049, 6000), (4096, 4096), (4097, 4097), (12289, 9000),
+         (70001, 70001), (150_000, 40_000)]
+
+
+@pytest.mark.parametrize("S", [4, 8, 12, 16])
+@pytest.mark.parametrize("mode", ["random", "dups", "floats", "const"])
+def test_random_meshes(rx, S, mode):
+    rng = np.random.default_rng(1000 + S * 10 + ["random", "dups", "floats", "const"].index(mode))
+    for n, m in SIZES:
+        assert_parity(rx, *random_mesh(rng, n, m, S // 4, mode))
+
+
+def test_worked_example(rx):
+    from test_oracle import load_worked_example
+
+    rows, letters, ints, words = load_worked_example()
+    vtx, idx = words("vtx"), ints("idx").astype(np.int32)
+    D, gv, gi = run_gpu(rx, vtx, idx, 3)
+    assert D == 6
+    np.testing.assert_array_equal(gv, words("newVtx"))
+    np.testing.assert_array_equal(gi, ints("idxNew"))
+
+
+def test_config1_heightfield_256(rx):
+    m = synth.config_mesh(1)
+    assert assert_parity(rx, m.vtx, m.idx.reshape(-1), 3) == 66_049
+
+
+@pytest.mark.parametrize("n", [8, 64, 1024])
+def test_table1_quad_grid(rx, n):
+    m = synth.quad_grid(n)
+    assert assert_parity(rx, m.vtx, m.idx.reshape(-1), 4) == (n + 1) ** 2
+
+
+@pytest.mark.slow
+def test_config2_heightfield_2048_full(rx):
+    m = synth.config_mesh(2)
+    assert assert_parity(rx, m.vtx, m.idx.reshape(-1), 3) == 4_198_401
+
+
+@pytest.mark.slow
+def test_config3_tet_soup_128_full(rx):
+    m = synth.config_mesh(3)
+    assert assert_parity(rx, m.vtx, m.idx.reshape(-1), 4) == 2_146_689
+
+
+# ------------------------------------------------------------------------------- edge cases
+
+
+def test_no_elements(rx):
+    v, _ = to_dev(np.arange(12, dtype=np.uint32).reshape(4, 3), np.zeros((0, 3), np.int32))
+    i = torch.zeros((0, 3), dtype=torch.int32, device="cuda")
+    out_v, out_n, out_i = rx.reindex_mesh(v, i)
+    assert int(out_n.item()) == 0 and out_i.numel() == 0
+
+
+def test_single_vertex_all_indices(rx):
+    vtx = np.arange(3 * 5000, dtype=np.uint32).reshape(5000, 3)
+    idx = np.full(9999, 4321, np.int32)
+    assert assert_parity(rx, vtx, idx, 3) == 1
+
+
+def test_all_vertices_bitwise_equal(rx):
+    vtx = np.tile(np.array([[0xDEADBEEF, 7, 0x80000000, 1]], np.uint32), (20000, 1))
+    idx = np.random.default_rng(3).integers(0, 20000, size=(30000,)).astype(np.int32)
+    assert assert_parity(rx, vtx, idx, 3) == 1
+
+
+@pytest.mark.parametrize("bad", [-1, 1000, 2**31 - 1])
+def test_index_out_of_range_is_reported(rx, bad):
+    vtx = np.arange(3000, dtype=np.uint32).reshape(1000, 3)
+    idx = np.arange(999, dtype=np.int32)
+    idx[517] = bad
+    v, i = to_dev(vtx, idx.reshape(-1, 3))
+    rx.reindex_stream_status()  # clear anything left over
+    out_v, out_n, out_i = rx.reindex_mesh(v, i)
+    assert rx.reindex_stream_status() == rx.REINDEX_ERR_INDEX_RANGE
+    assert int(out_n.item()) == -rx.REINDEX_ERR_INDEX_RANGE
+    assert rx.reindex_stream_status() == rx.REINDEX_OK  # sticky word was cleared
+    # the context stays usable
+    idx[517] = 5
+    assert_parity(rx, vtx, idx, 3)
+
+
+def test_in_place_remap(rx):
+    rng = np.random.default_rng(8)
+    vtx, idx = random_mesh(rng, 30000, 45000, 3, "dups")
+    ov, oi = oracle.reindex_sort(vtx, idx)
+    v, i = to_dev(vtx, idx.reshape(-1, 3))
+    out_v, out_n, out_i = rx.reindex_mesh(v, i, out_idx=i)
+    assert int(out_n.item()) == ov.shape[0]
+    np.testing.assert_array_equal(i.cpu().numpy().reshape(-1), oi)
+
+
+def test_unaligned_index_buffers(rx):
+    """int32 index arrays that are only 4-byte aligned take the scalar load path."""
+    rng = np.random.default_rng(9)
+    vtx, idx = random_mesh(rng, 20000, 30003, 3, "dups")
+    ov, oi = oracle.reindex_sort(vtx, idx)
+    v = torch.from_numpy(vtx.view(np.int32)).cuda()
+    big = torch.zeros(30003 + 1, dtype=torch.int32, device="cuda")
+    big[1:] = torch.from_numpy(idx).cuda()
+    i = big[1:].view(-1, 3)
+    outbig = torch.zeros_like(big)
+    o = outbig[1:].view(-1, 3)
+    assert i.data_ptr() % 16 != 0 and o.data_ptr() % 16 != 0
+    out_v, out_n, _ = rx.reindex_mesh(v, i, out_idx=o)
+    assert int(out_n.item()) == ov.shape[0]
+    np.testing.assert_array_equal(o.cpu().numpy().reshape(-1), oi)
+    np.testing.assert_array_equal(out_v[: ov.shape[0]].cpu().numpy().view(np.uint32), ov)
+
+
+def test_workspace_variant_and_determinism(rx):
+    m = synth.heightfield_soup(300, 200, 0.07, seed=42)
+    v, i = to_dev(m.vtx, m.idx)
+    ws = torch.empty(rx.reindex_workspace_size(m.n_vtx, 12, m.n_elem, 3), dtype=torch.uint8, device="cuda")
+    a = rx.reindex_mesh(v, i)
+    b = rx.reindex_mesh_ws(v, i, ws)
+    c = rx.reindex_mesh_ws(v, i, ws)
+    torch.cuda.synchronize()
+    D = int(a[1].item())
+    assert D == 301 * 201 == int(b[1].item()) == int(c[1].item())
+    for x, y in ((a, b), (b, c)):
+        assert torch.equal(x[0][:D], y[0][:D]) and torch.equal(x[2], y[2])
+
+
+def test_cuda_graph_capture_of_workspace_variant(rx):
+    m = synth.heightfield_soup(120, 90, 0.1, seed=5)
+    ov, oi = oracle.reindex_sort(m.vtx, m.idx)
+    v, i = to_dev(m.vtx, m.idx)
+    ws = torch.empty(rx.reindex_workspace_size(m.n_vtx, 12, m.n_elem, 3), dtype=torch.uint8, device="cuda")
+    out_v = torch.empty((min(m.n_vtx, i.numel()), 3), dtype=torch.int32, device="cuda")
+    out_n = torch.empty(1, dtype=torch.int64, device="cuda")
+    out_i = torch.empty_like(i)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        rx.reindex_mesh_ws(v, i, ws, out_v, out_n, out_i)  # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rx.reindex_mesh_ws(v, i, ws, out_v, out_n, out_i, stream=s)
+    out_i.zero_()
+    out_n.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(out_n.item()) == ov.shape[0]
+    np.testing.assert_array_equal(out_v[: ov.shape[0]].cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+
+
+def test_host_buffer_variant(rx):
+    m = synth.heightfield_soup(200, 150, 0.05, seed=6)
+    ov, oi = oracle.reindex_sort(m.vtx, m.idx)
+    hv = torch.from_numpy(m.vtx.view(np.int32)).pin_memory()
+    hi = torch.from_numpy(m.idx).pin_memory()
+    out_v, out_i = rx.reindex_mesh_host(hv, hi)
+    np.testing.assert_array_equal(out_v.numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out_i.numpy().reshape(-1), oi)
+
+
+def test_profile_records_every_kernel(rx):
+    m = synth.config_mesh(1)
+    v, i = to_dev(m.vtx, m.idx)
+    rx.profile_collect()
+    rx.profile_enable(True)
+    try:
+        rx.reindex_mesh(v, i)
+        torch.cuda.synchronize()
+    finally:
+        rx.profile_enable(False)
+    recs = rx.profile_collect()
+    names = [r["name"] for r in recs]
+    assert names.count("onesweep") == 12
+    assert set(names) == set(rx.KERNEL_NAMES)
+    # x and y are integers 0..256 as float32: their lowest byte is always zero -> skipped passes
+    sk = {r["digit"]: r["skipped"] for r in recs if r["name"] == "onesweep"}
+    assert sk[8] and sk[4] and not sk[0]
