@@ -40,6 +40,9 @@ WORKLOADS = {
                        "+ 10% unused = 432,538 vertices, permuted), int32 idx x3, seed 1", 1),
     "tet128": ("tetrahedral soup 128^3 hex cells x 5 tets (10,485,760 tets, 41,943,040 soup vertices of 16 B "
                "+ 3% unused = 43,201,331 vertices, permuted), int32 idx x4, seed 3", 3),
+    # a half-size case of the 2048^2 workload, for profiler captures (still larger than L2)
+    "heightfield1448": ("heightfield triangle soup 1448x1448 cells (4,193,408 tris, 12,580,224 soup vertices "
+                        "float32 xyz + 5% unused, permuted), int32 idx x3, seed 2", (1448, 0.05, 2)),
 }
 METRIC = "input elements re-indexed/sec"
 UNIT = "elements/s"
@@ -80,7 +83,7 @@ def ncu_traffic(workload):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms around the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -97,7 +100,7 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
             time.sleep(0.3)
         except Exception:
@@ -212,7 +215,7 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     cfg = WORKLOADS[args.workload][1]
-    mesh = synth.config_mesh(cfg)
+    mesh = synth.heightfield_soup(cfg[0], cfg[0], cfg[1], cfg[2]) if isinstance(cfg, tuple) else synth.config_mesh(cfg)
     S, k, n_vtx, n_elem = mesh.stride_bytes, mesh.idx_per_elem, mesh.n_vtx, mesh.n_elem
     M = n_elem * k
     U = M  # soups: every soup vertex is referenced exactly once
@@ -274,26 +277,9 @@ def run_ours(args, world, rank, local):
                 "avg_launch_ms": avg_ms, "passes_per_step": len(sweeps) / args.steps}
 
     # ---- end to end through the host-buffer entry point
-    hv = torch.from_numpy(mesh.vtx.view(np.int32)).pin_memory()
-    hi = torch.from_numpy(mesh.idx).pin_memory()
-    ho_v = torch.empty((min(n_vtx, M), S // 4), dtype=torch.int32).pin_memory()
-    ho_i = torch.empty_like(hi).pin_memory()
-    for _ in range(2):
-        rx.reindex_mesh_host(hv, hi, ho_v, ho_i)
-    if world > 1:
-        torch.distributed.barrier()
-    t0 = time.perf_counter()
-    e2e_steps = max(3, min(args.steps, 10))
-    for _ in range(e2e_steps):
-        rv, _ = rx.reindex_mesh_host(hv, hi, ho_v, ho_i)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * n_elem / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n_vtx * S + M * 4,
-           "d2h_bytes_per_step": rv.shape[0] * S + M * 4 + 8, "ms_per_step": e2e_s * 1e3}
-
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(rx, torch, mesh, world, dev, args)
     if rank != 0:
         return
     cpu = None
@@ -316,6 +302,30 @@ def run_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_e2e(rx, torch, mesh, world, dev, args):
+    """Same metric through reindex_mesh_host: pinned host buffers in, results back in host memory."""
+    S, M, n_vtx, n_elem = mesh.stride_bytes, mesh.n_elem * mesh.idx_per_elem, mesh.n_vtx, mesh.n_elem
+    hv = torch.from_numpy(mesh.vtx.view(np.int32)).pin_memory()
+    hi = torch.from_numpy(mesh.idx).pin_memory()
+    ho_v = torch.empty((min(n_vtx, M), S // 4), dtype=torch.int32).pin_memory()
+    ho_i = torch.empty_like(hi).pin_memory()
+    for _ in range(2):
+        rx.reindex_mesh_host(hv, hi, ho_v, ho_i)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(e2e_steps):
+        rv, _ = rx.reindex_mesh_host(hv, hi, ho_v, ho_i)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    return {"value": world * n_elem / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n_vtx * S + M * 4,
+            "d2h_bytes_per_step": rv.shape[0] * S + M * 4 + 8, "ms_per_step": e2e_s * 1e3}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,6 +334,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="heightfield2048")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     try:
