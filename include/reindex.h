@@ -122,6 +122,29 @@ reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int vtxStri
                                  void* host_out_vtx, int64_t* host_out_nVtx, int32_t* host_out_idx,
                                  reindex_stream_t stream);
 
+/* Re-index one small mesh WITHOUT ALLOCATING ANYTHING.  The paper has no counterpart; this entry
+ * point exists for callers that cannot allocate device memory when they call us: a program that
+ * reserved its whole device-memory budget up front and accounts for every byte, a real-time
+ * loop in which cudaMalloc/cudaFree would synchronise the device and stall its other streams, or
+ * a plugin whose host application forbids allocations behind its back.
+ *   Arguments, result and error reporting are those of reindex_mesh (inputs and outputs are
+ *   still the caller's device buffers).
+ *   Limit: nVtx <= REINDEX_NOALLOC_MAX_VTX (262,144 vertices, any supported stride and any
+ *   number of elements); a larger mesh returns REINDEX_ERR_UNSUPPORTED and nothing is launched.
+ *   Scratch: one 16 MiB array of device memory inside the library, reserved on every device
+ *   that loads the library and held until the process exits.  The first call on a device looks
+ *   up that array's device address (cudaGetSymbolAddress, with the device current) and caches
+ *   it; make that first call before any stream capture on the device.
+ *   All calls share the array.  Each call zeroes the parts that must start at zero, but two
+ *   calls whose work overlaps on the GPU (e.g. on two streams with no ordering between them)
+ *   race on it and corrupt each other's results: order them on one stream or with events.
+ *   Keep per-launch timing (reindex_profile_enable) off: that facility allocates for itself. */
+#define REINDEX_NOALLOC_MAX_VTX 262144
+reindex_status reindex_mesh_noalloc(const void* vtx, int64_t nVtx, int vtxStrideBytes,
+                                    const int32_t* idx, int64_t nElem, int idxPerElem,
+                                    void* out_vtx, int64_t* out_nVtx, int32_t* out_idx,
+                                    reindex_stream_t stream);
+
 /* Synchronises `stream`, then returns and clears this device's sticky device-side error: the
  * first INDEX_RANGE or TIMEOUT raised by any call on the current device since the last
  * reindex_stream_status() (REINDEX_OK if none).  A CUDA error from the synchronisation is

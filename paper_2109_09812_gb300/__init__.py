@@ -35,7 +35,7 @@ KERNEL_NAMES = ["clear", "used_flags", "compact_hist", "sort_plan", "onesweep", 
 # Symbols declared in include/reindex.h (checked by the ABI test).
 EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "reindex_mesh_ws",
             "reindex_mesh_host", "reindex_stream_status", "reindex_profile_enable", "reindex_profile_collect",
-            "reindex_kernel_name"]
+            "reindex_kernel_name", "reindex_mesh_noalloc"]
 
 _lock = threading.Lock()
 _lib = None

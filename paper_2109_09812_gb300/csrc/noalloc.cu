@@ -1,0 +1,62 @@
+// reindex_mesh_noalloc: re-index one small mesh with scratch memory that the library reserved
+// when it was loaded, so that the call itself allocates nothing.
+//
+// Who needs this: callers that cannot (or must not) allocate device memory at call time -- a
+// host program that committed its whole device-memory budget up front and accounts for every
+// byte, a real-time loop in which cudaMalloc/cudaFree would synchronise the device and stall
+// its other streams, or a plugin whose host application forbids allocations behind its back.
+// They pass inputs and outputs as usual; the scratch is the static array below.
+//
+// The array is a file-scope __device__ variable, so every device that loads this library holds
+// it (16 MiB) until the process exits.  Host code only sees a stand-in for its name; the real
+// device address is looked up once per device with cudaGetSymbolAddress (with that device
+// current) and cached.  Every call shares the array: the pipeline's first kernel zeroes the
+// parts that must start at zero, and calls whose work overlaps on the GPU (for example two
+// calls on two streams without ordering between them) race on it.
+#include <mutex>
+
+#include "../../include/reindex.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = 16u << 20;  // 16 MiB, enough for nVtx <= REINDEX_NOALLOC_MAX_VTX
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+cudaError_t scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(g_mu);
+  if (g_addr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (p == nullptr) return cudaErrorInvalidSymbol;
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" reindex_status reindex_mesh_noalloc(const void* vtx, int64_t nVtx, int vtxStrideBytes,
+                                               const int32_t* idx, int64_t nElem, int idxPerElem,
+                                               void* out_vtx, int64_t* out_nVtx, int32_t* out_idx,
+                                               reindex_stream_t stream) {
+  if (nVtx > REINDEX_NOALLOC_MAX_VTX) return REINDEX_ERR_UNSUPPORTED;
+  const size_t need = reindex_workspace_size(nVtx, vtxStrideBytes, nElem, idxPerElem);
+  if (need == 0) return nVtx < 0 || nElem < 0 || idxPerElem < 1 ? REINDEX_ERR_INVALID_ARG : REINDEX_ERR_UNSUPPORTED;
+  if (need > kScratchBytes) return REINDEX_ERR_UNSUPPORTED;
+  void* ws = nullptr;
+  if (scratch_address(&ws) != cudaSuccess) return REINDEX_ERR_CUDA;
+  return reindex_mesh_ws(vtx, nVtx, vtxStrideBytes, idx, nElem, idxPerElem, out_vtx, out_nVtx, out_idx, ws,
+                         kScratchBytes, stream);
+}
