@@ -1,12 +1,14 @@
 // C ABI of the re-indexing library (include/reindex.h): argument checks, workspace layout,
 // the launch sequence of the pipeline, the pool-allocating and host-buffer variants, the
 // sticky error query and the per-launch timing facility.
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <utility>
 #include <vector>
 
-#include "../../include/reindex.h"
+#include "reindex.h"
 #include "internal.h"
 
 namespace reindex {
@@ -27,6 +29,19 @@ const LaunchCfg& launch_cfg(int S) {
   c.occ_compact = occupancy_compact(S);
   c.occ_sort = occupancy_sort(S);
   c.occ_head = occupancy_head(S);
+  c.occ_sort_pipe = occupancy_sort_pipe(S);
+  if (c.occ_sort_pipe < 1) c.sort_kernel = kSortRegs;  // shared memory too small on this device
+  // Kernel variants: defaults measured on GB300; REINDEX_TUNE="sort=regs|pipe,rank=ballot|match,hist=uniform|peel|match"
+  // overrides them (used to compare variants; every variant computes the same result).
+  if (const char* tune = std::getenv("REINDEX_TUNE")) {
+    if (std::strstr(tune, "sort=regs")) c.sort_kernel = kSortRegs;
+    if (std::strstr(tune, "sort=pipe") && c.occ_sort_pipe > 0) c.sort_kernel = kSortPipe;
+    if (std::strstr(tune, "rank=match")) c.rank_mode = kRankMatchAny;
+    if (std::strstr(tune, "rank=ballot")) c.rank_mode = kRankBallot;
+    if (std::strstr(tune, "hist=uniform")) c.hist_mode = kHistUniform;
+    if (std::strstr(tune, "hist=peel")) c.hist_mode = kHistPeel;
+    if (std::strstr(tune, "hist=match")) c.hist_mode = kHistMatchAny;
+  }
   return cache.emplace(std::make_pair(dev, S), c).first->second;
 }
 
@@ -144,7 +159,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
   const uint8_t* skip = prof::skip_buffer(p.plan, st);
   for (int d = 0; d < L.P; ++d) {
     prof::Scope s(REINDEX_K_ONESWEEP, d, st, skip);
-    REINDEX_TRY(launch_onesweep(S, d, p, c, st));
+    REINDEX_TRY(c.sort_kernel == kSortPipe ? launch_onesweep_pipe(S, d, p, c, st) : launch_onesweep(S, d, p, c, st));
   }
   {
     prof::Scope s(REINDEX_K_HEAD_SCAN, -1, st);

@@ -14,13 +14,25 @@ constexpr int kThreads = 256;              // threads per CTA for every tiled ke
 constexpr int kWarps = kThreads / 32;
 constexpr int kCompactRows = 8;            // 32-vertex rows per warp in the compaction
 constexpr int kCompactTile = kWarps * kCompactRows * 32;   // 2048 vertices per tile
-constexpr int kSortIpt = 16;               // items per thread in a sort pass
-constexpr int kSortTile = kThreads * kSortIpt;             // 4096 items per tile
-constexpr int kHeadIpt = 16;               // items per thread in the head scan
-constexpr int kHeadTile = kThreads * kHeadIpt;             // 4096 items per tile
+constexpr int kSortThreads = 512;          // threads per CTA of a sort pass
+constexpr int kSortIpt = 8;                // items per thread in a sort pass
+constexpr int kSortTile = kSortThreads * kSortIpt;         // 4096 items per tile
+constexpr int kSortTileMin = 2048;         // smallest sort tile of any variant (sizes the look-back)
+constexpr int kHeadThreads = 512;          // threads per CTA of the head scan
+constexpr int kHeadIpt = 8;                // items per thread in the head scan
+constexpr int kHeadTile = kHeadThreads * kHeadIpt;         // 4096 items per tile
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;    // 256 digit values
 constexpr int kMaxDigits = 16;             // 16-byte keys -> 16 byte-digits
+
+// Kernel variants (chosen per device by launch_cfg; see REINDEX_TUNE in api.cu).
+constexpr int kSortRegs = 0;      // radix pass with items in registers (k_onesweep)
+constexpr int kSortPipe = 1;      // radix pass pipelined through shared memory (k_onesweep_pipe)
+constexpr int kRankBallot = 0;    // digit peers from 8 ballots
+constexpr int kRankMatchAny = 1;  // digit peers from match.any
+constexpr int kHistUniform = 0;   // histogram: one atomic per warp when the digit is warp-uniform
+constexpr int kHistPeel = 1;      // histogram: the first lane's digit group counted with one atomic
+constexpr int kHistMatchAny = 2;  // histogram: one atomic per distinct digit (match.any)
 
 // Look-back status word: 2-bit flag + 30-bit count.
 constexpr uint32_t kFlagAgg = 1u << 30;    // tile aggregate only
@@ -32,6 +44,7 @@ constexpr int64_t kMaxCount = (int64_t)kValMask;  // largest count a status word
 // Bounded spin: every wait on another CTA gives up after this many polls, records
 // REINDEX_ERR_TIMEOUT and publishes a (meaningless) prefix so that no successor waits forever.
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kLookWindow = 16;  // predecessor status words fetched per look-back round (sort)
 
 // Device-side error codes (same numbers as reindex_status).
 constexpr uint32_t kErrIndexRange = 4;
@@ -67,13 +80,13 @@ struct WsLayout {
   int64_t tilesV = 0, tilesS = 0, tilesH = 0;
   size_t off_ctrl = 0, off_hist = 0, off_lb_compact = 0, off_lb_head = 0, off_lb_sort = 0,
          off_bitmask = 0, zero_bytes = 0;
-  size_t off_plan = 0, off_itemsA = 0, off_itemsB = 0, items_bytes = 0, off_old2new = 0, total = 0;
+  size_t off_plan = 0, off_itemsA = 0, off_itemsB = 0, items_bytes = 0, idoff = 0, off_old2new = 0, total = 0;
 
   void compute(int64_t n, int s, int64_t m) {
     S = s; K = s / 4; P = s; nVtx = n; M = m;
     Umax = n < m ? n : m;
     tilesV = (n + kCompactTile - 1) / kCompactTile;
-    tilesS = (Umax + kSortTile - 1) / kSortTile;
+    tilesS = (Umax + kSortTileMin - 1) / kSortTileMin;  // enough for every sort kernel variant
     tilesH = (Umax + kHeadTile - 1) / kHeadTile;
     size_t o = 0;
     off_ctrl = o;        o += sizeof(Control);
@@ -84,7 +97,11 @@ struct WsLayout {
     off_bitmask = o;     o = align_up(o + (size_t)((n + 31) / 32) * 4, 256);
     zero_bytes = o;
     off_plan = o;        o = align_up(o + sizeof(Plan), 256);
-    items_bytes = align_up((size_t)Umax * (size_t)(S + 4), 256);
+    // SoA layouts keep the id plane 256-byte aligned; 256 spare bytes let bulk copies of a
+    // ragged last tile round their size up to 16 bytes without leaving the buffer.
+    idoff = (S == 8 || S == 16) ? align_up((size_t)Umax * S, 256) : 0;
+    items_bytes = (S == 8 || S == 16) ? idoff + align_up((size_t)Umax * 4, 256) + 256
+                                      : align_up((size_t)Umax * (size_t)(S + 4), 256) + 256;
     off_itemsA = o;      o += items_bytes;
     off_itemsB = o;      o += items_bytes;
     off_old2new = o;     o = align_up(o + (size_t)n * 4, 256);
@@ -104,8 +121,9 @@ struct WsPtrs {
   unsigned char* itemsA;
   unsigned char* itemsB;
   uint32_t* old2new;     // [nVtx]
-  int64_t tilesS;        // stride of one look-back area in tiles
-  int64_t Umax;          // capacity of each item buffer (SoA id plane offset)
+  int64_t tilesS;        // capacity of the sort look-back table, in tiles
+  int64_t Umax;          // capacity of each item buffer, in items
+  int64_t idoff;         // byte offset of the id plane inside an item buffer (S = 8, 16)
 };
 
 inline WsPtrs ws_ptrs(void* ws, const WsLayout& L) {
@@ -123,6 +141,7 @@ inline WsPtrs ws_ptrs(void* ws, const WsLayout& L) {
   p.old2new = reinterpret_cast<uint32_t*>(b + L.off_old2new);
   p.tilesS = L.tilesS;
   p.Umax = L.Umax;
+  p.idoff = (int64_t)L.idoff;
   return p;
 }
 
@@ -130,6 +149,7 @@ inline WsPtrs ws_ptrs(void* ws, const WsLayout& L) {
 // Sort items: K key words (word 0 most significant) plus the old vertex index.
 //   S = 4, 12: array of structures, one 8- or 16-byte vector per item {k..., id}
 //   S = 8, 16: structure of arrays, an 8- or 16-byte key vector per item, then an id plane
+//              starting at byte offset idoff (256-byte aligned)
 template <int S>
 struct Item {
   static constexpr int K = S / 4;
@@ -146,6 +166,10 @@ struct ItemIO<4> {
     uint2 v = reinterpret_cast<const uint2*>(buf)[i];
     it.k[0] = v.x; it.id = v.y;
   }
+  static __device__ __forceinline__ void load_cs(const unsigned char* buf, int64_t, int64_t i, Item<4>& it) {
+    uint2 v = __ldcs(reinterpret_cast<const uint2*>(buf) + i);
+    it.k[0] = v.x; it.id = v.y;
+  }
   static __device__ __forceinline__ void store(unsigned char* buf, int64_t, int64_t i, const Item<4>& it) {
     reinterpret_cast<uint2*>(buf)[i] = make_uint2(it.k[0], it.id);
   }
@@ -157,6 +181,10 @@ struct ItemIO<12> {
     uint4 v = reinterpret_cast<const uint4*>(buf)[i];
     it.k[0] = v.x; it.k[1] = v.y; it.k[2] = v.z; it.id = v.w;
   }
+  static __device__ __forceinline__ void load_cs(const unsigned char* buf, int64_t, int64_t i, Item<12>& it) {
+    uint4 v = __ldcs(reinterpret_cast<const uint4*>(buf) + i);
+    it.k[0] = v.x; it.k[1] = v.y; it.k[2] = v.z; it.id = v.w;
+  }
   static __device__ __forceinline__ void store(unsigned char* buf, int64_t, int64_t i, const Item<12>& it) {
     reinterpret_cast<uint4*>(buf)[i] = make_uint4(it.k[0], it.k[1], it.k[2], it.id);
   }
@@ -164,59 +192,93 @@ struct ItemIO<12> {
 
 template <>
 struct ItemIO<8> {
-  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t cap, int64_t i, Item<8>& it) {
+  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t idoff, int64_t i, Item<8>& it) {
     uint2 v = reinterpret_cast<const uint2*>(buf)[i];
     it.k[0] = v.x; it.k[1] = v.y;
-    it.id = reinterpret_cast<const uint32_t*>(buf + cap * 8)[i];
+    it.id = reinterpret_cast<const uint32_t*>(buf + idoff)[i];
   }
-  static __device__ __forceinline__ void store(unsigned char* buf, int64_t cap, int64_t i, const Item<8>& it) {
+  static __device__ __forceinline__ void load_cs(const unsigned char* buf, int64_t idoff, int64_t i, Item<8>& it) {
+    uint2 v = __ldcs(reinterpret_cast<const uint2*>(buf) + i);
+    it.k[0] = v.x; it.k[1] = v.y;
+    it.id = __ldcs(reinterpret_cast<const uint32_t*>(buf + idoff) + i);
+  }
+  static __device__ __forceinline__ void store(unsigned char* buf, int64_t idoff, int64_t i, const Item<8>& it) {
     reinterpret_cast<uint2*>(buf)[i] = make_uint2(it.k[0], it.k[1]);
-    reinterpret_cast<uint32_t*>(buf + cap * 8)[i] = it.id;
+    reinterpret_cast<uint32_t*>(buf + idoff)[i] = it.id;
   }
 };
 
 template <>
 struct ItemIO<16> {
-  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t cap, int64_t i, Item<16>& it) {
+  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t idoff, int64_t i, Item<16>& it) {
     uint4 v = reinterpret_cast<const uint4*>(buf)[i];
     it.k[0] = v.x; it.k[1] = v.y; it.k[2] = v.z; it.k[3] = v.w;
-    it.id = reinterpret_cast<const uint32_t*>(buf + cap * 16)[i];
+    it.id = reinterpret_cast<const uint32_t*>(buf + idoff)[i];
   }
-  static __device__ __forceinline__ void store(unsigned char* buf, int64_t cap, int64_t i, const Item<16>& it) {
+  static __device__ __forceinline__ void load_cs(const unsigned char* buf, int64_t idoff, int64_t i, Item<16>& it) {
+    uint4 v = __ldcs(reinterpret_cast<const uint4*>(buf) + i);
+    it.k[0] = v.x; it.k[1] = v.y; it.k[2] = v.z; it.k[3] = v.w;
+    it.id = __ldcs(reinterpret_cast<const uint32_t*>(buf + idoff) + i);
+  }
+  static __device__ __forceinline__ void store(unsigned char* buf, int64_t idoff, int64_t i, const Item<16>& it) {
     reinterpret_cast<uint4*>(buf)[i] = make_uint4(it.k[0], it.k[1], it.k[2], it.k[3]);
-    reinterpret_cast<uint32_t*>(buf + cap * 16)[i] = it.id;
+    reinterpret_cast<uint32_t*>(buf + idoff)[i] = it.id;
   }
 };
 
 // Vertex key loads from the caller's vertex array (stride S, natural alignment).
+// (streaming: the caller's vertex array is read once per call)
 template <int S>
 __device__ __forceinline__ void load_key(const void* vtx, int64_t i, uint32_t (&k)[S / 4]) {
   if constexpr (S == 4) {
-    k[0] = reinterpret_cast<const uint32_t*>(vtx)[i];
+    k[0] = __ldcs(reinterpret_cast<const uint32_t*>(vtx) + i);
   } else if constexpr (S == 8) {
-    uint2 v = reinterpret_cast<const uint2*>(vtx)[i];
+    uint2 v = __ldcs(reinterpret_cast<const uint2*>(vtx) + i);
     k[0] = v.x; k[1] = v.y;
   } else if constexpr (S == 12) {
     const uint32_t* p = reinterpret_cast<const uint32_t*>(vtx) + i * 3;
-    k[0] = p[0]; k[1] = p[1]; k[2] = p[2];
+    k[0] = __ldcs(p); k[1] = __ldcs(p + 1); k[2] = __ldcs(p + 2);
   } else {
-    uint4 v = reinterpret_cast<const uint4*>(vtx)[i];
+    uint4 v = __ldcs(reinterpret_cast<const uint4*>(vtx) + i);
     k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
   }
 }
 
+// (streaming: the caller's output vertex array is written once)
 template <int S>
 __device__ __forceinline__ void store_key(void* out, int64_t i, const uint32_t (&k)[S / 4]) {
   if constexpr (S == 4) {
-    reinterpret_cast<uint32_t*>(out)[i] = k[0];
+    __stcs(reinterpret_cast<uint32_t*>(out) + i, k[0]);
   } else if constexpr (S == 8) {
-    reinterpret_cast<uint2*>(out)[i] = make_uint2(k[0], k[1]);
+    __stcs(reinterpret_cast<uint2*>(out) + i, make_uint2(k[0], k[1]));
   } else if constexpr (S == 12) {
     uint32_t* p = reinterpret_cast<uint32_t*>(out) + i * 3;
-    p[0] = k[0]; p[1] = k[1]; p[2] = k[2];
+    __stcs(p, k[0]); __stcs(p + 1, k[1]); __stcs(p + 2, k[2]);
   } else {
-    reinterpret_cast<uint4*>(out)[i] = make_uint4(k[0], k[1], k[2], k[3]);
+    __stcs(reinterpret_cast<uint4*>(out) + i, make_uint4(k[0], k[1], k[2], k[3]));
   }
+}
+
+// L2 eviction-priority policies (createpolicy) and hinted 32-bit accesses.  oldToNew is written
+// at random by the head scan and read at random by the remap right after; marking its lines
+// evict-last while the item stream is marked evict-first keeps as much of it in L2 as fits.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void st_u32_hint(uint32_t* a, uint32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_u32_hint(const uint32_t* a, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
 }
 
 // Byte digit d of a key (d = 0 is the least significant byte of the least significant word).
@@ -261,19 +323,18 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 // Wait until *p carries a flag; bounded.  Returns the status word (flag + value), or on
-// timeout records the error and returns a prefix flag with value 0.
+// timeout records the error and returns a prefix flag with value 0.  Failed polls back off
+// briefly so that waiting threads leave issue slots to the warps doing useful work.
 __device__ __forceinline__ uint32_t wait_status(const uint32_t* p, Control* c) {
   uint32_t s = ld_relaxed(p);
   uint32_t polls = 0;
   while ((s & kFlagMask) == 0) {
     ++polls;
-    if ((polls & 255u) == 0) {
-      if (polls >= kSpinLimit || ld_relaxed(&c->err) != 0) {
-        record_error(c, kErrTimeout);
-        return kFlagPre;
-      }
-      __nanosleep(64);
+    if ((polls & 255u) == 0 && (polls >= kSpinLimit || ld_relaxed(&c->err) != 0)) {
+      record_error(c, kErrTimeout);
+      return kFlagPre;
     }
+    __nanosleep(polls < 4 ? 32 : 128);
     s = ld_relaxed(p);
   }
   return s;
@@ -299,6 +360,50 @@ __device__ __forceinline__ uint32_t warp_lookback(const uint32_t* lb, int64_t ti
     hi -= 32;
   }
   return excl;
+}
+
+// Warp-cooperative decoupled look-back for the DPW consecutive digits d0 .. d0+DPW-1 of tile
+// `cur` on the tile-major status table (status of tile q, digit d at lb[q * 256 + d]).  Each
+// load instruction of the warp covers 32/DPW predecessor tiles x DPW digits (contiguous words
+// per tile), so DPW loads, all issued before any is used, cover the 32 nearest predecessors of
+// every digit.  Per digit the lanes agree on the nearest inclusive prefix and sum the counts up
+// to it; digits without a prefix in the window continue with the next 32 predecessors.
+// Lanes 0 .. DPW-1 return the exclusive prefix of digit d0 + lane.
+template <int DPW>
+__device__ __forceinline__ uint32_t warp_lookback_tiles(const uint32_t* lb, uint32_t cur, int d0, Control* c) {
+  constexpr int TPL = 32 / DPW;  // predecessor tiles per load instruction
+  const int lane = threadIdx.x & 31;
+  const int dl = lane % DPW, h = lane / DPW;
+  uint32_t total = 0;
+  bool found = false;
+  for (int64_t top = (int64_t)cur;; top -= 32) {
+    uint32_t v[DPW];
+#pragma unroll
+    for (int i = 0; i < DPW; ++i) {
+      const int64_t q = top - 1 - (i * TPL + h);
+      v[i] = q >= 0 ? ld_relaxed(lb + (size_t)q * kRadix + d0 + dl) : kFlagPre;
+    }
+    int mypos = 64;  // nearest predecessor (0 = tile top-1) carrying an inclusive prefix
+#pragma unroll
+    for (int i = 0; i < DPW; ++i) {
+      const int64_t q = top - 1 - (i * TPL + h);
+      if (q >= 0 && (v[i] & kFlagMask) == 0) v[i] = wait_status(lb + (size_t)q * kRadix + d0 + dl, c);
+      if ((v[i] & kFlagMask) == kFlagPre && mypos == 64) mypos = i * TPL + h;
+    }
+    int cut = mypos;
+#pragma unroll
+    for (int o = DPW; o < 32; o <<= 1) cut = min(cut, __shfl_xor_sync(0xffffffffu, cut, o));
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < DPW; ++i)
+      if (i * TPL + h <= cut) sum += v[i] & kValMask;
+#pragma unroll
+    for (int o = DPW; o < 32; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (!found) total += sum;
+    found = found || cut < 64;
+    if (__all_sync(0xffffffffu, found)) break;
+  }
+  return total;
 }
 
 // Inclusive warp scan.

@@ -14,6 +14,10 @@ struct LaunchCfg {
   int occ_compact = 0;  // resident CTAs per SM of each persistent kernel
   int occ_sort = 0;
   int occ_head = 0;
+  int occ_sort_pipe = 0;
+  int sort_kernel = kSortRegs;  // kSortRegs (k_onesweep) or kSortPipe (k_onesweep_pipe)
+  int rank_mode = kRankBallot;  // onesweep digit matching (kRank*)
+  int hist_mode = kHistUniform; // compaction histogram method (kHist*)
 };
 
 // Per-device launch configuration (computed once per device, thread-safe).
@@ -26,6 +30,7 @@ cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int6
                            cudaStream_t st);
 cudaError_t launch_sort_plan(int S, WsPtrs ws, cudaStream_t st);
 cudaError_t launch_onesweep(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_onesweep_pipe(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx,
                              const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_remap(const int32_t* idx, int32_t* out_idx, int64_t M, WsPtrs ws, const LaunchCfg& c,
@@ -36,6 +41,7 @@ cudaError_t launch_set_count(int64_t* out_nVtx, int64_t value, cudaStream_t st);
 // Occupancy queries for the persistent kernels (per template instantiation).
 int occupancy_compact(int S);
 int occupancy_sort(int S);
+int occupancy_sort_pipe(int S);
 int occupancy_head(int S);
 
 // Device-wide sticky error word (read and cleared by reindex_stream_status).

@@ -13,7 +13,7 @@
 
 namespace reindex {
 
-template <int S>
+template <int S, int kHist>
 __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ vtx, int64_t nVtx, WsPtrs ws,
                                                        int64_t tilesV) {
   constexpr int K = S / 4;
@@ -88,20 +88,31 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
 #pragma unroll
         for (int q = 0; q < K; ++q) it.k[q] = k[r][q];
         it.id = (uint32_t)(vbase + r * 32 + lane);
-        ItemIO<S>::store(ws.itemsA, ws.Umax, obase + pos[r], it);
+        ItemIO<S>::store(ws.itemsA, ws.idoff, obase + pos[r], it);
       }
-      // Histograms: one shared-memory atomic per used item and digit, or a single one per warp
-      // when the digit is the same in every used lane (common for constant bytes).
+      // Histograms.  Many key bytes are heavily skewed (exponent bytes, the zero low bytes of
+      // small integers), and lanes adding to the same bin in one instruction serialise, so the
+      // lanes that share a digit are combined first (three variants, chosen per device).
       const int leader = __ffs(umask) - 1;
-      const uint32_t n_used = __popc(umask);
 #pragma unroll
       for (int d = 0; d < P; ++d) {
         const uint32_t dig = u ? key_digit<K>(k[r], d) : 0u;
-        const uint32_t d0 = __shfl_sync(0xffffffffu, dig, leader);
-        if (__all_sync(0xffffffffu, !u || dig == d0)) {
-          if (lane == leader) atomicAdd(&s_hist[d * kRadix + d0], n_used);
-        } else if (u) {
-          atomicAdd(&s_hist[d * kRadix + dig], 1u);
+        if (kHist == kHistMatchAny) {
+          const uint32_t peers = __match_any_sync(0xffffffffu, u ? dig : 0x100u);
+          if (u && (peers & lanemask_lt()) == 0) atomicAdd(&s_hist[d * kRadix + dig], (uint32_t)__popc(peers));
+        } else if (kHist == kHistPeel) {
+          const uint32_t d0 = __shfl_sync(0xffffffffu, dig, leader);
+          const bool same = u && dig == d0;
+          const uint32_t same_mask = __ballot_sync(0xffffffffu, same);
+          if (lane == leader) atomicAdd(&s_hist[d * kRadix + d0], (uint32_t)__popc(same_mask));
+          if (u && !same) atomicAdd(&s_hist[d * kRadix + dig], 1u);
+        } else {
+          const uint32_t d0 = __shfl_sync(0xffffffffu, dig, leader);
+          if (__all_sync(0xffffffffu, !u || dig == d0)) {
+            if (lane == leader) atomicAdd(&s_hist[d * kRadix + d0], (uint32_t)__popc(umask));
+          } else if (u) {
+            atomicAdd(&s_hist[d * kRadix + dig], 1u);
+          }
         }
       }
     }
@@ -116,8 +127,11 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
 
 template <int S>
 static int occ() {
-  int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_compact<S>, kThreads, 0);
+  int a = 0, b = 0, c = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistUniform>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistPeel>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_compact<S, kHistMatchAny>, kThreads, 0);
+  const int n = min(a, min(b, c));
   return n < 1 ? 1 : n;
 }
 
@@ -130,16 +144,26 @@ int occupancy_compact(int S) {
   }
 }
 
+template <int S>
+static void launch_s(int g, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, int mode, cudaStream_t st) {
+  if (mode == kHistMatchAny)
+    k_compact<S, kHistMatchAny><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV);
+  else if (mode == kHistPeel)
+    k_compact<S, kHistPeel><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV);
+  else
+    k_compact<S, kHistUniform><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV);
+}
+
 cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
                            cudaStream_t st) {
   if (tilesV == 0) return cudaSuccess;
   int64_t g = (int64_t)c.sms * c.occ_compact;
   if (g > tilesV) g = tilesV;
   switch (S) {
-    case 4: k_compact<4><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV); break;
-    case 8: k_compact<8><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV); break;
-    case 12: k_compact<12><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV); break;
-    default: k_compact<16><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV); break;
+    case 4: launch_s<4>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, st); break;
+    case 8: launch_s<8>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, st); break;
+    case 12: launch_s<12>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, st); break;
+    default: launch_s<16>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, st); break;
   }
   return cudaGetLastError();
 }

@@ -5,17 +5,19 @@
 //   oldToNew[orgID[j]] = newIdx[j]                           (Section 2.4: perm composed with newIdx)
 //   newVtx[newIdx[j]] = key[j] for every head j              (Section 2.3)
 //   *out_nVtx = total number of heads                        (Section 2.3, newN)
-// The prefix sum is a decoupled look-back scan over tiles of 4096 items; neither nodup nor
-// newIdx is materialised.
+// The prefix sum is a decoupled look-back scan over tiles of 4096 items (512 threads x 8);
+// neither nodup nor newIdx is materialised.
 #include "internal.h"
 
 namespace reindex {
 
+constexpr int kHeadWarps = kHeadThreads / 32;
+
 template <int S>
-__global__ void __launch_bounds__(kThreads) k_head_scan(WsPtrs ws, void* __restrict__ out_vtx,
+__global__ void __launch_bounds__(kHeadThreads, 2) k_head_scan(WsPtrs ws, void* __restrict__ out_vtx,
                                                          int64_t* __restrict__ out_nVtx, uint32_t nVtx) {
   constexpr int K = S / 4;
-  __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint32_t s_warp[kHeadWarps];
   __shared__ uint32_t s_tile, s_prefix;
   Control* ctrl = ws.ctrl;
   if (block_error(ctrl)) return;
@@ -24,6 +26,7 @@ __global__ void __launch_bounds__(kThreads) k_head_scan(WsPtrs ws, void* __restr
   const int64_t ntiles = ((int64_t)U + kHeadTile - 1) / kHeadTile;
   const unsigned char* buf = plan->final_sel ? ws.itemsB : ws.itemsA;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const uint64_t keep = l2_policy_evict_last();
   if (U == 0) {
     if (blockIdx.x == 0 && t == 0) *out_nVtx = 0;
     return;
@@ -40,14 +43,14 @@ __global__ void __launch_bounds__(kThreads) k_head_scan(WsPtrs ws, void* __restr
 #pragma unroll
     for (int r = 0; r < kHeadIpt; ++r) {
       const int64_t j = wbase + r * 32 + lane;
-      if (j < U) ItemIO<S>::load(buf, ws.Umax, j, it[r]);
+      if (j < U) ItemIO<S>::load_cs(buf, ws.idoff, j, it[r]);
     }
     uint32_t prevk[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) prevk[q] = 0;
     if (lane == 0 && wbase > 0 && wbase < U) {
       Item<S> p;
-      ItemIO<S>::load(buf, ws.Umax, wbase - 1, p);
+      ItemIO<S>::load(buf, ws.idoff, wbase - 1, p);
 #pragma unroll
       for (int q = 0; q < K; ++q) prevk[q] = p.k[q];
     }
@@ -80,7 +83,7 @@ __global__ void __launch_bounds__(kThreads) k_head_scan(WsPtrs ws, void* __restr
     __syncthreads();
     uint32_t woff = 0, total = 0;
 #pragma unroll
-    for (int q = 0; q < kWarps; ++q) {
+    for (int q = 0; q < kHeadWarps; ++q) {
       const uint32_t c = s_warp[q];
       woff += (q < w) ? c : 0u;
       total += c;
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_head_scan(WsPtrs ws, void* __restr
         const uint32_t e = ebase + within[r];  // heads strictly before j
         const uint32_t nid = head ? e : e - 1u;
         if (it[r].id < nVtx) {
-          ws.old2new[it[r].id] = nid;
+          st_u32_hint(ws.old2new + it[r].id, nid, keep);
           if (head) store_key<S>(out_vtx, nid, it[r].k);
         } else {
           record_error(ctrl, kErrInternal);  // corrupted item: never write out of range
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(kThreads) k_head_scan(WsPtrs ws, void* __restr
 template <int S>
 static int occ() {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_head_scan<S>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_head_scan<S>, kHeadThreads, 0);
   return n < 1 ? 1 : n;
 }
 
@@ -144,10 +147,10 @@ cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx,
   if (g > tiles) g = tiles;
   if (g < 1) g = 1;
   switch (S) {
-    case 4: k_head_scan<4><<<(int)g, kThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
-    case 8: k_head_scan<8><<<(int)g, kThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
-    case 12: k_head_scan<12><<<(int)g, kThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
-    default: k_head_scan<16><<<(int)g, kThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
+    case 4: k_head_scan<4><<<(int)g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
+    case 8: k_head_scan<8><<<(int)g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
+    case 12: k_head_scan<12><<<(int)g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
+    default: k_head_scan<16><<<(int)g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
   }
   return cudaGetLastError();
 }

@@ -3,42 +3,120 @@
 // upfront histograms (k_compact + k_sort_plan), and each tile's offset within a digit from a
 // decoupled look-back over per-tile digit counts, so every item is read and written once per pass.
 //
-// Per tile of 4096 items (256 threads x 16 items, warp-striped so loads are coalesced):
-//   1. load items; 2. rank digits inside each warp with __match_any_sync (stable: row-major,
-//   lane order); 3. per-digit tile counts and warp offsets; publish the counts (aggregate) and
-//   look back for each digit's exclusive prefix over earlier tiles, then publish the inclusive
-//   prefix; 4. stage the items in shared memory in digit order; 5. write them out so that
-//   consecutive threads write consecutive addresses of the same digit run.
+// Per tile of 4096 items (512 threads x 8 items, warp-striped so loads are coalesced):
+//   1. load items;
+//   2. rank digits inside each warp: find the lanes holding the same digit (8 ballots, one per
+//      digit bit, or one match.any), the group's lowest lane adds the group size to the warp's
+//      shared-memory counter for that digit and broadcasts the old value (stable: row-major,
+//      lane order);
+//   3. per-digit tile counts; publish them (aggregate) and load the preceding tile's status;
+//      tile-local digit starts and per-(warp, digit) offsets;
+//   4. stage the items in shared memory in digit order while that load is in flight, then walk
+//      back (one earlier tile per step) to the nearest inclusive prefix and publish this tile's;
+//   5. write the items out so that consecutive threads write consecutive addresses of one run.
 // The pass is stable, so the composition of passes sorts by the whole key (ties keep vertex order).
 // A pass whose digit is constant over all items is skipped (it would be the identity).
 #include "internal.h"
 
 namespace reindex {
 
+// Shared-memory staging of one tile: a vector per item (the key words, plus the old index for
+// the array-of-structures layouts) and, for S = 8 and 16, a separate old-index plane.
 template <int S>
-struct SortSmem {
-  static constexpr int K = S / 4;
-  static constexpr size_t planes = (size_t)(K + 1) * kSortTile * 4;
-  static constexpr size_t whist = (size_t)kWarps * kRadix * 4;
-  static constexpr size_t bytes = planes + whist + 2 * kRadix * 4 + 16 * 4;
+struct Stage;
+
+template <>
+struct Stage<4> {
+  static constexpr size_t bytes = (size_t)kSortTile * 8;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<4>& it) {
+    reinterpret_cast<uint2*>(sm)[p] = make_uint2(it.k[0], it.id);
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<4>& it) {
+    const uint2 v = reinterpret_cast<const uint2*>(sm)[p];
+    it.k[0] = v.x; it.id = v.y;
+  }
+};
+template <>
+struct Stage<12> {
+  static constexpr size_t bytes = (size_t)kSortTile * 16;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<12>& it) {
+    reinterpret_cast<uint4*>(sm)[p] = make_uint4(it.k[0], it.k[1], it.k[2], it.id);
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<12>& it) {
+    const uint4 v = reinterpret_cast<const uint4*>(sm)[p];
+    it.k[0] = v.x; it.k[1] = v.y; it.k[2] = v.z; it.id = v.w;
+  }
+};
+template <>
+struct Stage<8> {
+  static constexpr size_t bytes = (size_t)kSortTile * 12;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<8>& it) {
+    reinterpret_cast<uint2*>(sm)[p] = make_uint2(it.k[0], it.k[1]);
+    reinterpret_cast<uint32_t*>(sm + (size_t)kSortTile * 8)[p] = it.id;
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<8>& it) {
+    const uint2 v = reinterpret_cast<const uint2*>(sm)[p];
+    it.k[0] = v.x; it.k[1] = v.y;
+    it.id = reinterpret_cast<const uint32_t*>(sm + (size_t)kSortTile * 8)[p];
+  }
+};
+template <>
+struct Stage<16> {
+  static constexpr size_t bytes = (size_t)kSortTile * 20;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<16>& it) {
+    reinterpret_cast<uint4*>(sm)[p] = make_uint4(it.k[0], it.k[1], it.k[2], it.k[3]);
+    reinterpret_cast<uint32_t*>(sm + (size_t)kSortTile * 16)[p] = it.id;
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<16>& it) {
+    const uint4 v = reinterpret_cast<const uint4*>(sm)[p];
+    it.k[0] = v.x; it.k[1] = v.y; it.k[2] = v.z; it.k[3] = v.w;
+    it.id = reinterpret_cast<const uint32_t*>(sm + (size_t)kSortTile * 16)[p];
+  }
 };
 
+constexpr int kSortWarps = kSortThreads / 32;
+
 template <int S>
-__global__ void __launch_bounds__(kThreads, 2) k_onesweep(WsPtrs ws, int d) {
+struct SortSmem {
+  static constexpr size_t stage = Stage<S>::bytes;
+  static constexpr size_t whist = (size_t)kSortWarps * kRadix * 4;
+  static constexpr size_t bytes = stage + whist + 2 * kRadix * 4 + 32 * 4;
+};
+
+// Mask of the lanes whose 8-bit digit equals this lane's (and whose validity matches).
+template <int kMode>
+__device__ __forceinline__ uint32_t match_digit(uint32_t dig, bool valid) {
+  if (kMode == kRankMatchAny) {
+    return __match_any_sync(0xffffffffu, valid ? dig : 0x100u);
+  } else {
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    if (!valid) peers = ~peers;
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const bool bit = (dig >> b) & 1u;
+      const uint32_t vote = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? vote : ~vote;
+    }
+    return peers;
+  }
+}
+
+template <int S, int kWord, int kMode>
+__global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(WsPtrs ws, int d) {
   constexpr int K = S / 4;
-  extern __shared__ __align__(16) uint32_t sm[];
-  uint32_t* planes = sm;                                   // [K+1][kSortTile]
-  uint32_t* whist = planes + (K + 1) * kSortTile;          // [kWarps][256]
-  uint32_t* tstart = whist + kWarps * kRadix;              // [256] digit start inside the tile
-  int32_t* goff = reinterpret_cast<int32_t*>(tstart + kRadix);  // [256] global pos - local pos
-  uint32_t* s_misc = reinterpret_cast<uint32_t*>(goff + kRadix);  // [16]
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  unsigned char* stage = sm_raw;                                               // tile in digit order
+  uint32_t* whist = reinterpret_cast<uint32_t*>(sm_raw + SortSmem<S>::stage);  // [warps][256]
+  int32_t* goff = reinterpret_cast<int32_t*>(whist + kSortWarps * kRadix);     // [256] global - local pos
+  uint32_t* gbase = reinterpret_cast<uint32_t*>(goff + kRadix);                // [256] pass digit offsets
+  uint32_t* s_misc = gbase + kRadix;                                           // [32]
 
   const Plan* plan = ws.plan;
   if (plan->skip[d]) return;
   Control* ctrl = ws.ctrl;
   if (block_error(ctrl)) return;
   const uint32_t U = plan->U;
-  const int64_t ntiles = ((int64_t)U + kSortTile - 1) / kSortTile;
+  const uint32_t ntiles = (U + kSortTile - 1) / kSortTile;
   const bool fromB = plan->src[d] != 0;
   const unsigned char* src = fromB ? ws.itemsB : ws.itemsA;
   unsigned char* dst = fromB ? ws.itemsA : ws.itemsB;
@@ -46,103 +124,113 @@ __global__ void __launch_bounds__(kThreads, 2) k_onesweep(WsPtrs ws, int d) {
   uint32_t* lb = ws.lb_sort + (size_t)plan->area[d] * area;
   uint32_t* lb_next = ws.lb_sort + (size_t)(plan->area[d] ^ 1) * area;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const uint32_t gbase = plan->base[d][t];  // thread t owns digit value t
+  const bool digit_thread = t < kRadix;  // threads 0..255 own digit value t
+  if (digit_thread) gbase[t] = plan->base[d][t];
+  const int shift = (d & 3) * 8;
+  uint32_t* wh = whist + w * kRadix;
+  const int wbase = w * 32 * kSortIpt;
 
   for (;;) {
     if (t == 0) s_misc[0] = atomicAdd(&ctrl->ctr[1 + d], 1u);
     __syncthreads();
-    const int64_t tile = s_misc[0];
+    const uint32_t tile = s_misc[0];
     if (tile >= ntiles) break;
-    const int64_t base = tile * kSortTile;
-    const int n = (int)min((int64_t)kSortTile, (int64_t)U - base);
+    const uint32_t base = tile * kSortTile;
+    const int n = (int)min((uint32_t)kSortTile, U - base);
 
-    // 1. load (warp-striped)
+    // 1. load (warp-striped: row r of warp w is 32 consecutive items)
     Item<S> it[kSortIpt];
 #pragma unroll
     for (int r = 0; r < kSortIpt; ++r) {
-      const int local = w * 32 * kSortIpt + r * 32 + lane;
-      if (local < n) ItemIO<S>::load(src, ws.Umax, base + local, it[r]);
+      const int local = wbase + r * 32 + lane;
+      if (local < n) ItemIO<S>::load_cs(src, ws.idoff, (int64_t)(base + local), it[r]);
     }
-    uint32_t* wh = whist + w * kRadix;
 #pragma unroll
     for (int i = lane; i < kRadix; i += 32) wh[i] = 0;
     __syncwarp();
 
     // 2. warp-level ranking
-    uint32_t rank[kSortIpt];
+    uint32_t rank[kSortIpt / 2];  // two 16-bit ranks per register (ranks < 4096)
 #pragma unroll
     for (int r = 0; r < kSortIpt; ++r) {
-      const int local = w * 32 * kSortIpt + r * 32 + lane;
-      const bool valid = local < n;
-      const uint32_t dig = valid ? key_digit<K>(it[r].k, d) : (uint32_t)kRadix;
-      const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+      const bool valid = wbase + r * 32 + lane < n;
+      const uint32_t dig = (it[r].k[kWord] >> shift) & 0xFFu;
+      const uint32_t peers = match_digit<kMode>(dig, valid);
       const uint32_t lt = peers & lanemask_lt();
-      const uint32_t pre = valid ? wh[dig] : 0u;
-      __syncwarp();
-      if (valid && lt == 0) wh[dig] = pre + __popc(peers);
-      __syncwarp();
-      rank[r] = pre + __popc(lt);
+      const int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (valid && lt == 0) old = atomicAdd(wh + dig, (uint32_t)__popc(peers));
+      old = __shfl_sync(0xffffffffu, old, leader);
+      const uint32_t rk = old + __popc(lt);
+      if (r & 1)
+        rank[r >> 1] |= rk << 16;
+      else
+        rank[r >> 1] = rk;
     }
     __syncthreads();
 
-    // 3. per-digit tile count (thread t = digit t), warp offsets, aggregate publication
-    uint32_t cnt = 0;
+    // 3. per-digit tile count, aggregate publication, first look-back load, local digit start
+    uint32_t cnt = 0, s_prev = kFlagPre;
+    if (digit_thread) {
 #pragma unroll
-    for (int q = 0; q < kWarps; ++q) {
-      const uint32_t c = whist[q * kRadix + t];
-      whist[q * kRadix + t] = cnt;
-      cnt += c;
+      for (int q = 0; q < kSortWarps; ++q) cnt += whist[q * kRadix + t];
+      st_relaxed(lb + (size_t)tile * kRadix + t, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
+      lb_next[(size_t)tile * kRadix + t] = 0;  // the next non-trivial pass uses the other area
+      if (tile > 0) s_prev = ld_relaxed(lb + (size_t)(tile - 1) * kRadix + t);  // consumed after staging
     }
-    uint32_t* my = lb + tile * kRadix + t;
-    st_relaxed(my, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
-    lb_next[tile * kRadix + t] = 0;  // the next non-trivial pass uses the other area
     const uint32_t incl = warp_incl_scan(cnt);
-    if (lane == 31) s_misc[1 + w] = incl;
+    if (lane == 31 && digit_thread) s_misc[1 + w] = incl;
     __syncthreads();
-    uint32_t woff = 0;
+    uint32_t ts = 0;
+    if (digit_thread) {
 #pragma unroll
-    for (int q = 0; q < kWarps; ++q) woff += (q < w) ? s_misc[1 + q] : 0u;
-    const uint32_t ts = woff + incl - cnt;
-    tstart[t] = ts;
-    uint32_t excl = 0;
-    if (tile > 0) {
-      for (int64_t k = tile - 1;; --k) {
-        const uint32_t s = wait_status(lb + k * kRadix + t, ctrl);
-        excl += s & kValMask;
-        if ((s & kFlagMask) == kFlagPre) break;
+      for (int q = 0; q < kRadix / 32; ++q) ts += (q < w) ? s_misc[1 + q] : 0u;
+      ts += incl - cnt;  // tile-local start of digit t
+      uint32_t run = ts;
+#pragma unroll
+      for (int q = 0; q < kSortWarps; ++q) {  // -> tile-local start of (warp q, digit t)
+        const uint32_t c = whist[q * kRadix + t];
+        whist[q * kRadix + t] = run;
+        run += c;
       }
-      st_relaxed(my, kFlagPre | ((excl + cnt) & kValMask));
     }
-    goff[t] = (int32_t)(gbase + excl) - (int32_t)ts;
     __syncthreads();
 
-    // 4. stage in digit order
+    // 4. stage in digit order (the first look-back load is in flight meanwhile), then walk back
 #pragma unroll
     for (int r = 0; r < kSortIpt; ++r) {
-      const int local = w * 32 * kSortIpt + r * 32 + lane;
-      if (local < n) {
-        const uint32_t dig = key_digit<K>(it[r].k, d);
-        const uint32_t p = tstart[dig] + wh[dig] + rank[r];
-#pragma unroll
-        for (int q = 0; q < K; ++q) planes[q * kSortTile + p] = it[r].k[q];
-        planes[K * kSortTile + p] = it[r].id;
+      if (wbase + r * 32 + lane < n) {
+        const uint32_t dig = (it[r].k[kWord] >> shift) & 0xFFu;
+        const uint32_t rk = (rank[r >> 1] >> ((r & 1) * 16)) & 0xFFFFu;
+        Stage<S>::put(stage, (int)(wh[dig] + rk), it[r]);
       }
+    }
+    if (digit_thread) {
+      uint32_t excl = 0;
+      if (tile > 0) {
+        uint32_t s = s_prev;
+        if ((s & kFlagMask) == 0) s = wait_status(lb + (size_t)(tile - 1) * kRadix + t, ctrl);
+        excl = s & kValMask;
+        for (int64_t q = (int64_t)tile - 2; (s & kFlagMask) != kFlagPre; --q) {
+          s = wait_status(lb + (size_t)q * kRadix + t, ctrl);
+          excl += s & kValMask;
+        }
+        st_relaxed(lb + (size_t)tile * kRadix + t, kFlagPre | ((excl + cnt) & kValMask));
+      }
+      goff[t] = (int32_t)(gbase[t] + excl) - (int32_t)ts;
     }
     __syncthreads();
 
     // 5. coalesced scatter
 #pragma unroll
     for (int r = 0; r < kSortIpt; ++r) {
-      const int i = r * kThreads + t;
+      const int i = r * kSortThreads + t;
       if (i < n) {
         Item<S> o;
-#pragma unroll
-        for (int q = 0; q < K; ++q) o.k[q] = planes[q * kSortTile + i];
-        o.id = planes[K * kSortTile + i];
-        const uint32_t dig = key_digit<K>(o.k, d);
-        const int64_t gpos = (int64_t)goff[dig] + i;
-        if (gpos >= 0 && gpos < (int64_t)U)
-          ItemIO<S>::store(dst, ws.Umax, gpos, o);
+        Stage<S>::get(stage, i, o);
+        const uint32_t gpos = (uint32_t)(goff[(o.k[kWord] >> shift) & 0xFFu] + i);
+        if (gpos < U)
+          ItemIO<S>::store(dst, ws.idoff, (int64_t)gpos, o);
         else
           record_error(ctrl, kErrInternal);  // histogram/ranking inconsistency: never write out of range
       }
@@ -151,12 +239,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_onesweep(WsPtrs ws, int d) {
   }
 }
 
+template <int S, int kWord, int kMode>
+static int occ_one() {
+  cudaFuncSetAttribute(k_onesweep<S, kWord, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)SortSmem<S>::bytes);
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_onesweep<S, kWord, kMode>, kSortThreads,
+                                                SortSmem<S>::bytes);
+  return n < 1 ? 1 : n;
+}
+
+template <int S, int kMode>
+static int occ_mode() {
+  int n = occ_one<S, 0, kMode>();
+  if constexpr (S >= 8) n = min(n, occ_one<S, 1, kMode>());
+  if constexpr (S >= 12) n = min(n, occ_one<S, 2, kMode>());
+  if constexpr (S >= 16) n = min(n, occ_one<S, 3, kMode>());
+  return n;
+}
+
 template <int S>
 static int occ() {
-  cudaFuncSetAttribute(k_onesweep<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SortSmem<S>::bytes);
-  int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_onesweep<S>, kThreads, SortSmem<S>::bytes);
-  return n < 1 ? 1 : n;
+  return min(occ_mode<S, kRankBallot>(), occ_mode<S, kRankMatchAny>());
 }
 
 int occupancy_sort(int S) {
@@ -168,15 +272,34 @@ int occupancy_sort(int S) {
   }
 }
 
+template <int S, int kMode>
+static void launch_mode(int g, int digit, WsPtrs ws, cudaStream_t st) {
+  const int word = S / 4 - 1 - (digit >> 2);  // word 0 is the most significant
+  switch (word) {
+    case 0: k_onesweep<S, 0, kMode><<<g, kSortThreads, SortSmem<S>::bytes, st>>>(ws, digit); break;
+    case 1: if constexpr (S >= 8) k_onesweep<S, 1, kMode><<<g, kSortThreads, SortSmem<S>::bytes, st>>>(ws, digit); break;
+    case 2: if constexpr (S >= 12) k_onesweep<S, 2, kMode><<<g, kSortThreads, SortSmem<S>::bytes, st>>>(ws, digit); break;
+    default: if constexpr (S >= 16) k_onesweep<S, 3, kMode><<<g, kSortThreads, SortSmem<S>::bytes, st>>>(ws, digit); break;
+  }
+}
+
+template <int S>
+static void launch_s(int g, int digit, WsPtrs ws, int mode, cudaStream_t st) {
+  if (mode == kRankMatchAny)
+    launch_mode<S, kRankMatchAny>(g, digit, ws, st);
+  else
+    launch_mode<S, kRankBallot>(g, digit, ws, st);
+}
+
 cudaError_t launch_onesweep(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st) {
   int64_t g = (int64_t)c.sms * c.occ_sort;
   if (g > ws.tilesS) g = ws.tilesS;
   if (g < 1) return cudaSuccess;
   switch (S) {
-    case 4: k_onesweep<4><<<(int)g, kThreads, SortSmem<4>::bytes, st>>>(ws, digit); break;
-    case 8: k_onesweep<8><<<(int)g, kThreads, SortSmem<8>::bytes, st>>>(ws, digit); break;
-    case 12: k_onesweep<12><<<(int)g, kThreads, SortSmem<12>::bytes, st>>>(ws, digit); break;
-    default: k_onesweep<16><<<(int)g, kThreads, SortSmem<16>::bytes, st>>>(ws, digit); break;
+    case 4: launch_s<4>((int)g, digit, ws, c.rank_mode, st); break;
+    case 8: launch_s<8>((int)g, digit, ws, c.rank_mode, st); break;
+    case 12: launch_s<12>((int)g, digit, ws, c.rank_mode, st); break;
+    default: launch_s<16>((int)g, digit, ws, c.rank_mode, st); break;
   }
   return cudaGetLastError();
 }

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int
     const int4* v4 = reinterpret_cast<const int4*>(idx);
     const int64_t n4 = M >> 2;
     for (int64_t i = t0; i < n4; i += stride) {
-      const int4 q = v4[i];
+      const int4 q = __ldcs(v4 + i);
       mark_used(q.x, nVtx, bitmask, bad);
       mark_used(q.y, nVtx, bitmask, bad);
       mark_used(q.z, nVtx, bitmask, bad);
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int
     }
     done = n4 << 2;
   }
-  for (int64_t i = done + t0; i < M; i += stride) mark_used(idx[i], nVtx, bitmask, bad);
+  for (int64_t i = done + t0; i < M; i += stride) mark_used(__ldcs(idx + i), nVtx, bitmask, bad);
   if (bad) record_error(ctrl, kErrIndexRange);
 }
 
@@ -93,6 +93,7 @@ template <bool kVec>
 __global__ void __launch_bounds__(kThreads) k_remap(const int32_t* idx, int32_t* out, int64_t M,
                                                      const uint32_t* __restrict__ o2n, const Control* ctrl) {
   if (ctrl->err) return;  // outputs are unspecified after a device-detected error
+  const uint64_t drop = l2_policy_evict_first();  // oldToNew is dead after this kernel
   const int64_t t0 = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * kThreads;
   int64_t done = 0;
@@ -101,17 +102,17 @@ __global__ void __launch_bounds__(kThreads) k_remap(const int32_t* idx, int32_t*
     int4* out4 = reinterpret_cast<int4*>(out);
     const int64_t n4 = M >> 2;
     for (int64_t i = t0; i < n4; i += stride) {
-      const int4 q = in4[i];
+      const int4 q = __ldcs(in4 + i);
       int4 r;
-      r.x = (int32_t)__ldg(o2n + q.x);
-      r.y = (int32_t)__ldg(o2n + q.y);
-      r.z = (int32_t)__ldg(o2n + q.z);
-      r.w = (int32_t)__ldg(o2n + q.w);
-      out4[i] = r;
+      r.x = (int32_t)ld_u32_hint(o2n + q.x, drop);
+      r.y = (int32_t)ld_u32_hint(o2n + q.y, drop);
+      r.z = (int32_t)ld_u32_hint(o2n + q.z, drop);
+      r.w = (int32_t)ld_u32_hint(o2n + q.w, drop);
+      __stcs(out4 + i, r);
     }
     done = n4 << 2;
   }
-  for (int64_t i = done + t0; i < M; i += stride) out[i] = (int32_t)__ldg(o2n + idx[i]);
+  for (int64_t i = done + t0; i < M; i += stride) out[i] = (int32_t)ld_u32_hint(o2n + idx[i], drop);
 }
 
 __global__ void k_finalize(Control* ctrl, int64_t* out_nVtx) {

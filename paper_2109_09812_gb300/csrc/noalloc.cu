@@ -15,7 +15,7 @@
 // calls on two streams without ordering between them) race on it.
 #include <mutex>
 
-#include "../../include/reindex.h"
+#include "reindex.h"
 
 namespace {
 
