@@ -40,6 +40,9 @@ WORKLOADS = {
                        "+ 10% unused = 432,538 vertices, permuted), int32 idx x3, seed 1", 1),
     "tet128": ("tetrahedral soup 128^3 hex cells x 5 tets (10,485,760 tets, 41,943,040 soup vertices of 16 B "
                "+ 3% unused = 43,201,331 vertices, permuted), int32 idx x4, seed 3", 3),
+    "batched4096": ("4096 independent heightfield triangle soups (float32 xyz, int32 idx x3), triangle counts "
+                    "log-uniform in [64, 200000], 0-10% unused vertices each, each permuted, seed 4; one "
+                    "reindex_meshes launch sequence replayed as a CUDA graph vs one reindex_mesh_ws call per mesh", 4),
     # a half-size case of the 2048^2 workload, for profiler captures (still larger than L2)
     "heightfield1448": ("heightfield triangle soup 1448x1448 cells (4,193,408 tris, 12,580,224 soup vertices "
                         "float32 xyz + 5% unused, permuted), int32 idx x3, seed 2", (1448, 0.05, 2)),
@@ -172,7 +175,11 @@ def run_reference(args, world, rank):
     from paper_2109_09812_gb300 import synth
 
     cfg = WORKLOADS[args.workload][1]
-    if cfg == 3:
+    if args.workload == "batched4096":
+        meshes = synth.batched_heightfield(64, seed=4)
+        sample = synth.Mesh(vtx=None, idx=None)
+        sample_desc = "the first 64 meshes of the 4096-mesh batch (same sizes and seeds), one oracle call each"
+    elif cfg == 3:
         sample = synth.tet_soup(48, 0.03, 3)
         sample_desc = "tetrahedral soup 48^3 cells x 5 tets, same construction (552,960 tets)"
     else:
@@ -182,13 +189,20 @@ def run_reference(args, world, rank):
     import oracle
 
     oracle.lib()
+    work = [(m.vtx, m.idx) for m in meshes] if args.workload == "batched4096" else [(sample.vtx, sample.idx)]
+    n_elem = sum(w[1].shape[0] for w in work)
+
+    def one_step():
+        for v, i in work:
+            oracle.reindex_sort(v, i)
+
     for _ in range(args.warmup):
-        oracle.reindex_sort(sample.vtx, sample.idx)
+        one_step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.reindex_sort(sample.vtx, sample.idx)
+        one_step()
     dt = (time.perf_counter() - t0) / args.steps
-    value = sample.n_elem / dt
+    value = n_elem / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -199,6 +213,141 @@ def run_reference(args, world, rank):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def _gen_chunk(specs):
+    from paper_2109_09812_gb300 import synth
+
+    out = []
+    for (g, gy, uf, sd) in specs:
+        m = synth.heightfield_soup(g, gy, uf, sd)
+        out.append((m.vtx, m.idx))
+    return out
+
+
+def generate_batched(n_meshes, seed, workers):
+    """The batched workload, generated in a pool of spawned processes (before any CUDA use)."""
+    import multiprocessing as mp
+
+    from paper_2109_09812_gb300 import synth
+
+    specs = synth.batched_heightfield_sizes(n_meshes, seed=seed)
+    chunks = [specs[i::workers] for i in range(workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        parts = pool.map(_gen_chunk, chunks)
+    meshes = [None] * n_meshes
+    for w, part in enumerate(parts):
+        for j, m in enumerate(part):
+            meshes[w + j * workers] = m
+    return meshes
+
+
+def run_batched_bench(args, world, rank, local):
+    """Batched path: one CUDA-graph replay of reindex_meshes over all meshes vs one
+    reindex_mesh_ws call per mesh (same library, preallocated workspace, one stream)."""
+    import ctypes
+
+    workers = max(1, min(16, os.cpu_count() or 1))
+    meshes = generate_batched(4096, 4, workers)
+    import torch
+
+    import paper_2109_09812_gb300 as rx
+    from paper_2109_09812_gb300 import build as rxbuild
+
+    rxbuild.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nv = np.array([m[0].shape[0] for m in meshes], dtype=np.int64)
+    ne = np.array([m[1].shape[0] for m in meshes], dtype=np.int64)
+    voff = np.concatenate([[0], np.cumsum(nv)]).astype(np.int64)
+    eoff = np.concatenate([[0], np.cumsum(ne)]).astype(np.int64)
+    vtx_h = np.concatenate([m[0] for m in meshes])
+    idx_h = np.concatenate([m[1] for m in meshes])
+    del meshes
+    N, E, k, S = vtx_h.shape[0], idx_h.shape[0], 3, 12
+    vtx = torch.from_numpy(vtx_h.view(np.int32)).to(dev)
+    idx = torch.from_numpy(idx_h).to(dev)
+    vo, eo = torch.from_numpy(voff).to(dev), torch.from_numpy(eoff).to(dev)
+    ws = torch.empty(rx.reindex_meshes_workspace_size(len(nv), N, S, E, k), dtype=torch.uint8, device=dev)
+    out_v = torch.empty((min(N, E * k), 3), dtype=torch.int32, device=dev)
+    out_off = torch.empty(len(nv) + 1, dtype=torch.int64, device=dev)
+    out_i = torch.empty_like(idx)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        rx.reindex_meshes(vtx, vo, idx, eo, ws, out_v, out_off, out_i)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        rx.reindex_meshes(vtx, vo, idx, eo, ws, out_v, out_off, out_i, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):  # CUDAGraph.replay launches on the current stream
+        for _ in range(max(args.warmup, 1)):
+            graph.replay()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(local) as clocks:
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(args.steps):
+                graph.replay()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+    ms_batched = e0.elapsed_time(e1) / args.steps
+    D = int(out_off[-1].item())
+    if D < 0:
+        raise SystemExit(f"batched run reported device error {-D}")
+
+    # one call per mesh through the C ABI (pointers precomputed; one shared workspace)
+    L = rx.lib()
+    per_ws = torch.empty(max(rx.reindex_workspace_size(int(a), S, int(b), k) for a, b in zip(nv, ne)),
+                         dtype=torch.uint8, device=dev)
+    pv = torch.empty((N, 3), dtype=torch.int32, device=dev)
+    pn = torch.empty(len(nv), dtype=torch.int64, device=dev)
+    pi = torch.empty_like(out_i)
+    h = ctypes.c_void_p(stream.cuda_stream)
+    calls = []
+    for m in range(len(nv)):
+        calls.append((ctypes.c_void_p(vtx.data_ptr() + int(voff[m]) * S), int(nv[m]), S,
+                      ctypes.c_void_p(idx.data_ptr() + int(eoff[m]) * k * 4), int(ne[m]), k,
+                      ctypes.c_void_p(pv.data_ptr() + int(voff[m]) * S), ctypes.c_void_p(pn.data_ptr() + 8 * m),
+                      ctypes.c_void_p(pi.data_ptr() + int(eoff[m]) * k * 4), ctypes.c_void_p(per_ws.data_ptr()),
+                      per_ws.numel(), h))
+
+    def loop():
+        for c in calls:
+            rc = L.reindex_mesh_ws(*c)
+            if rc:
+                raise SystemExit(f"reindex_mesh_ws failed: {rc}")
+
+    loop()
+    torch.cuda.synchronize(dev)
+    loop_steps = max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(loop_steps):
+        loop()
+    torch.cuda.synchronize(dev)
+    ms_loop = (time.perf_counter() - t0) / loop_steps * 1e3
+    # untimed check: every mesh identical in both paths
+    counts = pn.cpu().numpy()
+    offs = out_off.cpu().numpy()
+    same = bool(np.array_equal(np.diff(offs), counts) and torch.equal(out_i, pi))
+    if same:
+        ov, pv_h = out_v.cpu().numpy(), pv.cpu().numpy()
+        same = all(np.array_equal(ov[offs[m]:offs[m + 1]], pv_h[voff[m]:voff[m] + counts[m]]) for m in range(len(nv)))
+    value = E / (ms_batched / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][0], "n_meshes": int(len(nv)), "n_vtx": int(N),
+                   "n_elem": int(E), "unique_out": D, "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2 ({(N * S + E * k * 4) / 1e9:.2f} GB)"},
+        "per_mesh_loop": {"value": E / (ms_loop / 1e3), "unit": UNIT, "ms_per_step": ms_loop,
+                          "launch_sequences": int(len(nv))},
+        "batched_vs_per_mesh": ms_loop / ms_batched, "identical_results": same,
+        "clocks": clocks.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_ours(args, world, rank, local):
@@ -340,6 +489,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.workload == "batched4096":
+            run_batched_bench(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

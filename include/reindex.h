@@ -42,8 +42,8 @@
  *     reported after the stream is synchronised in two ways: *out_nVtx holds the NEGATED
  *     status code (e.g. -REINDEX_ERR_INDEX_RANGE), and reindex_stream_status() returns it.
  *     When one occurs the contents of out_vtx and out_idx are unspecified.
- *   - Supported strides: vtxStrideBytes in {4, 8, 12, 16}.  vtx and out_vtx must be aligned
- *     to the stride's natural vector type: 4 bytes for S = 4 and 12, 8 bytes for S = 8,
+ *   - Supported strides: vtxStrideBytes in {4, 8, 12, 16, 20}.  vtx and out_vtx must be aligned
+ *     to the stride's natural vector type: 4 bytes for S = 4, 12 and 20, 8 bytes for S = 8,
  *     16 bytes for S = 16.  idx and out_idx must be 4-byte aligned (16-byte alignment enables
  *     128-bit vector loads and stores).
  *   - nVtx <= 2^30 - 1 and nElem * idxPerElem <= 2^31 - 1 (int32 indices; the look-back
@@ -69,7 +69,7 @@ typedef struct CUstream_st* reindex_stream_t;
 typedef enum {
   REINDEX_OK = 0,
   REINDEX_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or workspace too small */
-  REINDEX_ERR_UNSUPPORTED = 2, /* stride not in {4,8,12,16}, or sizes beyond the limits above */
+  REINDEX_ERR_UNSUPPORTED = 2, /* stride not supported, or sizes beyond the limits above */
   REINDEX_ERR_OOM = 3,         /* a library allocation failed */
   REINDEX_ERR_INDEX_RANGE = 4, /* some index < 0 or >= nVtx (device-detected) */
   REINDEX_ERR_TIMEOUT = 5,     /* a look-back wait exceeded its iteration limit (device-detected) */
@@ -145,6 +145,31 @@ reindex_status reindex_mesh_noalloc(const void* vtx, int64_t nVtx, int vtxStride
                                     void* out_vtx, int64_t* out_nVtx, int32_t* out_idx,
                                     reindex_stream_t stream);
 
+/* ---- batched: many independent meshes in one launch sequence ---------------------------------
+ * Mesh m owns vertices [vtxOffsets[m], vtxOffsets[m+1]) of the concatenated vtx array and
+ * elements [elemOffsets[m], elemOffsets[m+1]) of the concatenated idx array; its indices are
+ * LOCAL to its own vertices (0 .. nVtx_m - 1).  vtxOffsets and elemOffsets are DEVICE int64 arrays
+ * of nMeshes+1 entries, non-decreasing, starting at 0 and ending at nVtxTotal / nElemTotal (the
+ * host passes the two totals so that no device value has to be read back).
+ * Output: mesh m's unique vertices are out_vtx[out_vtxOffsets[m] .. out_vtxOffsets[m+1]) (a DEVICE
+ * int64 array of nMeshes+1 entries written by the library; out_vtxOffsets[nMeshes] = total D, or
+ * -status after a device-detected error), and mesh m's out_idx entries (same slots as its input
+ * indices) are local to its own output range.  Each mesh's result is bitwise identical to
+ * reindex_mesh on that mesh alone: duplicates are merged only inside a mesh.
+ * vtxStrideBytes in {4, 8, 12, 16}; internally the mesh id is an extra key word.  Sizes as for
+ * reindex_mesh over the totals.  out_idx may alias idx.  The workspace (reindex_meshes_workspace_size
+ * bytes, 256-byte aligned) is caller-supplied; the call allocates nothing and never synchronises,
+ * so the whole sequence can be captured into a CUDA graph and replayed.
+ * Device-detected errors: INDEX_RANGE (a local index outside its mesh), INVALID_ARG (offsets
+ * that are not non-decreasing from 0 to the totals). */
+size_t reindex_meshes_workspace_size(int nMeshes, int64_t nVtxTotal, int vtxStrideBytes, int64_t nElemTotal,
+                                     int idxPerElem);
+reindex_status reindex_meshes(const void* vtx, const int64_t* vtxOffsets, int vtxStrideBytes,
+                              const int32_t* idx, const int64_t* elemOffsets, int idxPerElem,
+                              int nMeshes, int64_t nVtxTotal, int64_t nElemTotal,
+                              void* out_vtx, int64_t* out_vtxOffsets, int32_t* out_idx,
+                              void* ws, size_t wsBytes, reindex_stream_t stream);
+
 /* Synchronises `stream`, then returns and clears this device's sticky device-side error: the
  * first INDEX_RANGE or TIMEOUT raised by any call on the current device since the last
  * reindex_stream_status() (REINDEX_OK if none).  A CUDA error from the synchronisation is
@@ -171,7 +196,9 @@ typedef enum {
   REINDEX_K_HEAD_SCAN = 5,  /* steps 4-7 fused */
   REINDEX_K_REMAP = 6,      /* step 8 */
   REINDEX_K_FINALIZE = 7,   /* error propagation */
-  REINDEX_K_COUNT = 8
+  REINDEX_K_SEG_PREPARE = 8, /* batched: mesh lookup tables, offsets check */
+  REINDEX_K_SEG_OFFSETS = 9, /* batched: per-mesh output offsets fix-up */
+  REINDEX_K_COUNT = 10
 } reindex_kernel_id;
 
 void reindex_profile_enable(int on);

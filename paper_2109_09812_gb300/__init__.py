@@ -30,12 +30,13 @@ REINDEX_ERR_TIMEOUT = 5
 REINDEX_ERR_CUDA = 6
 REINDEX_ERR_INTERNAL = 7
 
-KERNEL_NAMES = ["clear", "used_flags", "compact_hist", "sort_plan", "onesweep", "head_scan", "remap", "finalize"]
+KERNEL_NAMES = ["clear", "used_flags", "compact_hist", "sort_plan", "onesweep", "head_scan", "remap", "finalize",
+                "seg_prepare", "seg_offsets"]
 
 # Symbols declared in include/reindex.h (checked by the ABI test).
 EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "reindex_mesh_ws",
             "reindex_mesh_host", "reindex_stream_status", "reindex_profile_enable", "reindex_profile_collect",
-            "reindex_kernel_name", "reindex_mesh_noalloc"]
+            "reindex_kernel_name", "reindex_mesh_noalloc", "reindex_meshes", "reindex_meshes_workspace_size"]
 
 _lock = threading.Lock()
 _lib = None
@@ -80,6 +81,10 @@ def lib() -> ctypes.CDLL:
             L.reindex_profile_collect.restype = ci
             L.reindex_kernel_name.argtypes = [ci]
             L.reindex_kernel_name.restype = ctypes.c_char_p
+            L.reindex_meshes_workspace_size.argtypes = [ci, i64, ci, i64, ci]
+            L.reindex_meshes_workspace_size.restype = ctypes.c_size_t
+            L.reindex_meshes.argtypes = [vp, vp, ci, vp, vp, ci, ci, i64, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]
+            L.reindex_meshes.restype = ci
             _lib = L
     return _lib
 
@@ -188,6 +193,42 @@ def reindex_mesh_host(vtx, idx, out_vtx=None, out_idx=None, stream=None):
     if rc:
         raise ReindexError(rc, "reindex_mesh_host")
     return out_vtx[: D.value], out_idx
+
+
+def reindex_meshes_workspace_size(n_meshes: int, n_vtx_total: int, stride_bytes: int, n_elem_total: int,
+                                  idx_per_elem: int) -> int:
+    return int(lib().reindex_meshes_workspace_size(n_meshes, n_vtx_total, stride_bytes, n_elem_total, idx_per_elem))
+
+
+def reindex_meshes(vtx, vtx_offsets, idx, elem_offsets, ws=None, out_vtx=None, out_offsets=None, out_idx=None,
+                   stream=None):
+    """Re-index many independent meshes in one launch sequence (asynchronous, allocation-free
+    inside the C call, graph-capturable when ws and the outputs are given).
+
+    vtx: CUDA tensor (nVtxTotal, ...) of concatenated vertices; idx: CUDA int32 (nElemTotal, k)
+    of concatenated elements with mesh-local indices; vtx_offsets / elem_offsets: CUDA int64
+    tensors of nMeshes+1 offsets.  Returns (out_vtx, out_offsets, out_idx): mesh m's unique
+    vertices are out_vtx[out_offsets[m]:out_offsets[m+1]] and its indices are local to them."""
+    torch = _torch()
+    n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx)
+    n_meshes = int(vtx_offsets.numel()) - 1
+    if elem_offsets.numel() != n_meshes + 1 or vtx_offsets.dtype != torch.int64 or elem_offsets.dtype != torch.int64:
+        raise ValueError("vtx_offsets and elem_offsets must be int64 tensors of nMeshes+1 entries")
+    if ws is None:
+        ws = torch.empty(max(1, reindex_meshes_workspace_size(n_meshes, n_vtx, S, n_elem, k)), dtype=torch.uint8,
+                         device=vtx.device)
+    if out_vtx is None:
+        out_vtx = torch.empty((min(n_vtx, n_elem * k),) + tuple(vtx.shape[1:]), dtype=vtx.dtype, device=vtx.device)
+    if out_offsets is None:
+        out_offsets = torch.empty(n_meshes + 1, dtype=torch.int64, device=vtx.device)
+    if out_idx is None:
+        out_idx = torch.empty_like(idx)
+    rc = lib().reindex_meshes(_ptr(vtx), _ptr(vtx_offsets), S, _ptr(idx), _ptr(elem_offsets), k, n_meshes, n_vtx,
+                              n_elem, _ptr(out_vtx), _ptr(out_offsets), _ptr(out_idx), _ptr(ws),
+                              ws.numel() * ws.element_size(), _stream_handle(stream))
+    if rc:
+        raise ReindexError(rc, "reindex_meshes")
+    return out_vtx, out_offsets, out_idx
 
 
 def reindex_stream_status(stream=None) -> int:

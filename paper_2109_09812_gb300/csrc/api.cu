@@ -34,6 +34,8 @@ const LaunchCfg& launch_cfg(int S) {
   // Kernel variants: defaults measured on GB300; REINDEX_TUNE="sort=regs|pipe,rank=ballot|match,hist=uniform|peel|match"
   // overrides them (used to compare variants; every variant computes the same result).
   if (const char* tune = std::getenv("REINDEX_TUNE")) {
+    if (std::strstr(tune, "grid=tile")) c.grid_per_tile = 1;
+    if (std::strstr(tune, "grid=persist")) c.grid_per_tile = 0;
     if (std::strstr(tune, "sort=regs")) c.sort_kernel = kSortRegs;
     if (std::strstr(tune, "sort=pipe") && c.occ_sort_pipe > 0) c.sort_kernel = kSortPipe;
     if (std::strstr(tune, "rank=match")) c.rank_mode = kRankMatchAny;
@@ -115,7 +117,7 @@ static uintptr_t vtx_alignment(int S) { return S == 8 ? 8 : (S == 16 ? 16 : 4); 
 
 // Host-side checks shared by every entry point.  Sets M.
 static reindex_status check_args(int64_t nVtx, int S, int64_t nElem, int k, int64_t* M) {
-  if (S != 4 && S != 8 && S != 12 && S != 16) return REINDEX_ERR_UNSUPPORTED;
+  if (S != 4 && S != 8 && S != 12 && S != 16 && S != 20) return REINDEX_ERR_UNSUPPORTED;
   if (nVtx < 0 || nElem < 0 || k < 1) return REINDEX_ERR_INVALID_ARG;
   if (nVtx > kMaxCount) return REINDEX_ERR_UNSUPPORTED;
   if (nElem > (int64_t)INT32_MAX / k) return REINDEX_ERR_UNSUPPORTED;
@@ -150,7 +152,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
   }
   {
     prof::Scope s(REINDEX_K_COMPACT, -1, st);
-    REINDEX_TRY(launch_compact(S, vtx, nVtx, p, L.tilesV, c, st));
+    REINDEX_TRY(launch_compact(S, vtx, nVtx, p, L.tilesV, c, nullptr, st));
   }
   {
     prof::Scope s(REINDEX_K_SORT_PLAN, -1, st);
@@ -163,7 +165,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
   }
   {
     prof::Scope s(REINDEX_K_HEAD_SCAN, -1, st);
-    REINDEX_TRY(launch_head_scan(S, p, out_vtx, out_nVtx, (uint32_t)nVtx, c, st));
+    REINDEX_TRY(launch_head_scan(S, p, out_vtx, out_nVtx, (uint32_t)nVtx, c, nullptr, st));
   }
   {
     prof::Scope s(REINDEX_K_REMAP, -1, st);
@@ -172,6 +174,85 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
   {
     prof::Scope s(REINDEX_K_FINALIZE, -1, st);
     REINDEX_TRY(launch_finalize(p, out_nVtx, st));
+  }
+  return REINDEX_OK;
+}
+
+// Workspace of the batched path: the single-mesh layout for (S + 4)-byte keys over all vertices
+// and indices, followed by the two position -> mesh lookup tables.
+struct SegLayout {
+  WsLayout L;
+  size_t off_blkV = 0, off_blkI = 0, total = 0;
+  void compute(int64_t n, int s, int64_t m) {
+    L.compute(n, s + 4, m);
+    size_t o = L.total;
+    off_blkV = o;
+    o = align_up(o + (size_t)((n + kSegBlock - 1) / kSegBlock + 1) * 4, 256);
+    off_blkI = o;
+    o = align_up(o + (size_t)((m + kSegBlock - 1) / kSegBlock + 1) * 4, 256);
+    total = o;
+  }
+};
+
+static reindex_status run_batched(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t M, int k,
+                                  const int64_t* vtxOff, const int64_t* elemOff, int nMeshes, void* out_vtx,
+                                  int64_t* outOff, int32_t* out_idx, void* ws, const SegLayout& SL,
+                                  cudaStream_t st) {
+  const LaunchCfg& cS = launch_cfg(S);
+  const LaunchCfg& c = launch_cfg(S + 4);
+  const WsPtrs p = ws_ptrs(ws, SL.L);
+  unsigned char* b = static_cast<unsigned char*>(ws);
+  SegArgs seg;
+  seg.vtxOff = vtxOff;
+  seg.elemOff = elemOff;
+  seg.outOff = outOff;
+  seg.blkV = reinterpret_cast<const uint32_t*>(b + SL.off_blkV);
+  seg.blkI = reinterpret_cast<const uint32_t*>(b + SL.off_blkI);
+  seg.nMeshes = nMeshes;
+  seg.k = k;
+  int64_t* total = outOff + nMeshes;  // D, or -status after a device-detected error
+  {
+    prof::Scope sc(REINDEX_K_CLEAR, -1, st);
+    REINDEX_TRY(launch_clear(ws, SL.L.zero_bytes, c, st));
+  }
+  {
+    prof::Scope sc(REINDEX_K_SEG_PREPARE, -1, st);
+    REINDEX_TRY(launch_seg_prepare(seg, nVtx, M, reinterpret_cast<uint32_t*>(b + SL.off_blkV),
+                                   reinterpret_cast<uint32_t*>(b + SL.off_blkI), p.ctrl, c, st));
+  }
+  {
+    prof::Scope sc(REINDEX_K_USED_FLAGS, -1, st);
+    REINDEX_TRY(launch_seg_flags(idx, out_idx, M, seg, p, c, st));
+  }
+  {
+    prof::Scope sc(REINDEX_K_COMPACT, -1, st);
+    REINDEX_TRY(launch_compact(S, vtx, nVtx, p, SL.L.tilesV, cS, &seg, st));
+  }
+  {
+    prof::Scope sc(REINDEX_K_SORT_PLAN, -1, st);
+    REINDEX_TRY(launch_sort_plan(S + 4, p, st));
+  }
+  const uint8_t* skip = prof::skip_buffer(p.plan, st);
+  for (int d = 0; d < S + 4; ++d) {
+    prof::Scope sc(REINDEX_K_ONESWEEP, d, st, skip);
+    REINDEX_TRY(c.sort_kernel == kSortPipe ? launch_onesweep_pipe(S + 4, d, p, c, st)
+                                           : launch_onesweep(S + 4, d, p, c, st));
+  }
+  {
+    prof::Scope sc(REINDEX_K_HEAD_SCAN, -1, st);
+    REINDEX_TRY(launch_head_scan(S + 4, p, out_vtx, total, (uint32_t)nVtx, c, &seg, st));
+  }
+  {
+    prof::Scope sc(REINDEX_K_SEG_OFFSETS, -1, st);
+    REINDEX_TRY(launch_seg_offsets(seg, p.ctrl, st));
+  }
+  {
+    prof::Scope sc(REINDEX_K_REMAP, -1, st);
+    REINDEX_TRY(launch_seg_remap(out_idx, M, seg, p, c, st));
+  }
+  {
+    prof::Scope sc(REINDEX_K_FINALIZE, -1, st);
+    REINDEX_TRY(launch_finalize(p, total, st));
   }
   return REINDEX_OK;
 }
@@ -309,6 +390,41 @@ reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int S, cons
   return REINDEX_OK;
 }
 
+static reindex_status check_batched(int64_t nVtxTotal, int S, int64_t nElemTotal, int k, int nMeshes, int64_t* M) {
+  if (S != 4 && S != 8 && S != 12 && S != 16) return REINDEX_ERR_UNSUPPORTED;
+  if (nMeshes < 1) return REINDEX_ERR_INVALID_ARG;
+  return check_args(nVtxTotal, S, nElemTotal, k, M);
+}
+
+size_t reindex_meshes_workspace_size(int nMeshes, int64_t nVtxTotal, int vtxStrideBytes, int64_t nElemTotal,
+                                     int idxPerElem) {
+  int64_t M = 0;
+  if (check_batched(nVtxTotal, vtxStrideBytes, nElemTotal, idxPerElem, nMeshes, &M) != REINDEX_OK) return 0;
+  SegLayout SL;
+  SL.compute(nVtxTotal, vtxStrideBytes, M);
+  return SL.total;
+}
+
+reindex_status reindex_meshes(const void* vtx, const int64_t* vtxOffsets, int vtxStrideBytes, const int32_t* idx,
+                              const int64_t* elemOffsets, int idxPerElem, int nMeshes, int64_t nVtxTotal,
+                              int64_t nElemTotal, void* out_vtx, int64_t* out_vtxOffsets, int32_t* out_idx,
+                              void* ws, size_t wsBytes, reindex_stream_t stream) {
+  int64_t M = 0;
+  const int S = vtxStrideBytes;
+  reindex_status r = check_batched(nVtxTotal, S, nElemTotal, idxPerElem, nMeshes, &M);
+  if (r != REINDEX_OK) return r;
+  if (!vtxOffsets || !elemOffsets || !out_vtxOffsets || !aligned(vtxOffsets, 8) || !aligned(elemOffsets, 8) ||
+      !aligned(out_vtxOffsets, 8))
+    return REINDEX_ERR_INVALID_ARG;
+  if ((r = check_ptrs(vtx, nVtxTotal, S, idx, M, out_vtx, out_vtxOffsets, out_idx)) != REINDEX_OK) return r;
+  if (M > 0 && nVtxTotal == 0) return REINDEX_ERR_INDEX_RANGE;
+  SegLayout SL;
+  SL.compute(nVtxTotal, S, M);
+  if (ws == nullptr || !aligned(ws, 256) || wsBytes < SL.total) return REINDEX_ERR_INVALID_ARG;
+  return run_batched(vtx, nVtxTotal, S, idx, M, idxPerElem, vtxOffsets, elemOffsets, nMeshes, out_vtx,
+                     out_vtxOffsets, out_idx, ws, SL, reinterpret_cast<cudaStream_t>(stream));
+}
+
 reindex_status reindex_stream_status(reindex_stream_t stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaStreamSynchronize(st);
@@ -350,8 +466,9 @@ int reindex_profile_collect(reindex_profile_record* out, int maxRecords) {
 }
 
 const char* reindex_kernel_name(int kernel) {
-  static const char* names[REINDEX_K_COUNT] = {"clear", "used_flags", "compact_hist", "sort_plan",
-                                               "onesweep", "head_scan", "remap", "finalize"};
+  static const char* names[REINDEX_K_COUNT] = {"clear",     "used_flags", "compact_hist", "sort_plan",
+                                               "onesweep",  "head_scan",  "remap",        "finalize",
+                                               "seg_prepare", "seg_offsets"};
   return (kernel >= 0 && kernel < REINDEX_K_COUNT) ? names[kernel] : "unknown";
 }
 

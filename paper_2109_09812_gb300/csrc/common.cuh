@@ -18,12 +18,12 @@ constexpr int kSortThreads = 512;          // threads per CTA of a sort pass
 constexpr int kSortIpt = 8;                // items per thread in a sort pass
 constexpr int kSortTile = kSortThreads * kSortIpt;         // 4096 items per tile
 constexpr int kSortTileMin = 2048;         // smallest sort tile of any variant (sizes the look-back)
-constexpr int kHeadThreads = 512;          // threads per CTA of the head scan
+constexpr int kHeadThreads = 256;          // threads per CTA of the head scan
 constexpr int kHeadIpt = 8;                // items per thread in the head scan
-constexpr int kHeadTile = kHeadThreads * kHeadIpt;         // 4096 items per tile
+constexpr int kHeadTile = kHeadThreads * kHeadIpt;         // 2048 items per tile
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;    // 256 digit values
-constexpr int kMaxDigits = 16;             // 16-byte keys -> 16 byte-digits
+constexpr int kMaxDigits = 20;             // 20-byte keys (16-byte vertices + a mesh id) -> 20 digits
 
 // Kernel variants (chosen per device by launch_cfg; see REINDEX_TUNE in api.cu).
 constexpr int kSortRegs = 0;      // radix pass with items in registers (k_onesweep)
@@ -146,8 +146,34 @@ inline WsPtrs ws_ptrs(void* ws, const WsLayout& L) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Batched (segmented) re-indexing: many meshes concatenated, mesh m owning vertices
+// [vtxOff[m], vtxOff[m+1]) and indices [elemOff[m]*k, elemOff[m+1]*k).  The mesh id becomes the
+// most significant key word, so one sort orders all items by (mesh, vertex key).
+constexpr int kSegBlock = 1024;  // granularity of the position -> mesh lookup tables
+
+struct SegArgs {
+  const int64_t* vtxOff;   // [nMeshes+1] device
+  const int64_t* elemOff;  // [nMeshes+1] device
+  int64_t* outOff;         // [nMeshes+1] device: first output vertex of each mesh; [nMeshes] = D
+  const uint32_t* blkV;    // mesh of vertex b*kSegBlock
+  const uint32_t* blkI;    // mesh of index b*kSegBlock
+  int32_t nMeshes;
+  int32_t k;               // indices per element
+};
+
+// Mesh owning position pos, given the mesh of pos's block and the offsets (scaled by `scale`).
+// The walk never passes the last mesh, whatever the offsets hold.
+__device__ __forceinline__ uint32_t seg_mesh(int64_t pos, const int64_t* off, int64_t scale, const uint32_t* blk,
+                                             int32_t nMeshes) {
+  uint32_t m = __ldg(blk + (pos / kSegBlock));
+  while ((int32_t)m + 1 < nMeshes && __ldg(off + m + 1) * scale <= pos) ++m;
+  return m;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Sort items: K key words (word 0 most significant) plus the old vertex index.
 //   S = 4, 12: array of structures, one 8- or 16-byte vector per item {k..., id}
+//   S = 20:    array of structures, three 8-byte vectors per item {k0,k1}{k2,k3}{k4,id}
 //   S = 8, 16: structure of arrays, an 8- or 16-byte key vector per item, then an id plane
 //              starting at byte offset idoff (256-byte aligned)
 template <int S>
@@ -226,6 +252,26 @@ struct ItemIO<16> {
   }
 };
 
+template <>
+struct ItemIO<20> {
+  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t, int64_t i, Item<20>& it) {
+    const uint2* p = reinterpret_cast<const uint2*>(buf) + 3 * i;
+    const uint2 a = p[0], b = p[1], c = p[2];
+    it.k[0] = a.x; it.k[1] = a.y; it.k[2] = b.x; it.k[3] = b.y; it.k[4] = c.x; it.id = c.y;
+  }
+  static __device__ __forceinline__ void load_cs(const unsigned char* buf, int64_t, int64_t i, Item<20>& it) {
+    const uint2* p = reinterpret_cast<const uint2*>(buf) + 3 * i;
+    const uint2 a = __ldcs(p), b = __ldcs(p + 1), c = __ldcs(p + 2);
+    it.k[0] = a.x; it.k[1] = a.y; it.k[2] = b.x; it.k[3] = b.y; it.k[4] = c.x; it.id = c.y;
+  }
+  static __device__ __forceinline__ void store(unsigned char* buf, int64_t, int64_t i, const Item<20>& it) {
+    uint2* p = reinterpret_cast<uint2*>(buf) + 3 * i;
+    p[0] = make_uint2(it.k[0], it.k[1]);
+    p[1] = make_uint2(it.k[2], it.k[3]);
+    p[2] = make_uint2(it.k[4], it.id);
+  }
+};
+
 // Vertex key loads from the caller's vertex array (stride S, natural alignment).
 // (streaming: the caller's vertex array is read once per call)
 template <int S>
@@ -238,9 +284,13 @@ __device__ __forceinline__ void load_key(const void* vtx, int64_t i, uint32_t (&
   } else if constexpr (S == 12) {
     const uint32_t* p = reinterpret_cast<const uint32_t*>(vtx) + i * 3;
     k[0] = __ldcs(p); k[1] = __ldcs(p + 1); k[2] = __ldcs(p + 2);
-  } else {
+  } else if constexpr (S == 16) {
     uint4 v = __ldcs(reinterpret_cast<const uint4*>(vtx) + i);
     k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+  } else {
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(vtx) + i * (S / 4);
+#pragma unroll
+    for (int q = 0; q < S / 4; ++q) k[q] = __ldcs(p + q);
   }
 }
 
@@ -254,8 +304,12 @@ __device__ __forceinline__ void store_key(void* out, int64_t i, const uint32_t (
   } else if constexpr (S == 12) {
     uint32_t* p = reinterpret_cast<uint32_t*>(out) + i * 3;
     __stcs(p, k[0]); __stcs(p + 1, k[1]); __stcs(p + 2, k[2]);
-  } else {
+  } else if constexpr (S == 16) {
     __stcs(reinterpret_cast<uint4*>(out) + i, make_uint4(k[0], k[1], k[2], k[3]));
+  } else {
+    uint32_t* p = reinterpret_cast<uint32_t*>(out) + i * (S / 4);
+#pragma unroll
+    for (int q = 0; q < S / 4; ++q) __stcs(p + q, k[q]);
   }
 }
 

@@ -18,6 +18,7 @@ struct LaunchCfg {
   int sort_kernel = kSortRegs;  // kSortRegs (k_onesweep) or kSortPipe (k_onesweep_pipe)
   int rank_mode = kRankBallot;  // onesweep digit matching (kRank*)
   int hist_mode = kHistUniform; // compaction histogram method (kHist*)
+  int grid_per_tile = 0;        // 1: one CTA per tile; 0: persistent CTAs (SMs x occupancy)
 };
 
 // Per-device launch configuration (computed once per device, thread-safe).
@@ -26,13 +27,23 @@ const LaunchCfg& launch_cfg(int S);
 cudaError_t launch_clear(void* p, size_t bytes, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_used_flags(const int32_t* idx, int64_t M, int64_t nVtx, WsPtrs ws, const LaunchCfg& c,
                               cudaStream_t st);
+// seg == nullptr: single mesh; otherwise batched, S being the vertex stride (items carry S + 4 bytes).
 cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
-                           cudaStream_t st);
+                           const SegArgs* seg, cudaStream_t st);
 cudaError_t launch_sort_plan(int S, WsPtrs ws, cudaStream_t st);
 cudaError_t launch_onesweep(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_onesweep_pipe(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
+// seg != nullptr: batched, S being the item key size (vertex stride + 4); writes seg->outOff.
 cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx,
+                             const LaunchCfg& c, const SegArgs* seg, cudaStream_t st);
+// Batched helpers (batched.cu).
+cudaError_t launch_seg_prepare(const SegArgs& seg, int64_t nVtx, int64_t M, uint32_t* blkV, uint32_t* blkI,
+                               Control* ctrl, const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_seg_flags(const int32_t* idx, int32_t* gidx, int64_t M, const SegArgs& seg, WsPtrs ws,
                              const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_seg_offsets(const SegArgs& seg, const Control* ctrl, cudaStream_t st);
+cudaError_t launch_seg_remap(int32_t* out_idx, int64_t M, const SegArgs& seg, WsPtrs ws, const LaunchCfg& c,
+                             cudaStream_t st);
 cudaError_t launch_remap(const int32_t* idx, int32_t* out_idx, int64_t M, WsPtrs ws, const LaunchCfg& c,
                          cudaStream_t st);
 cudaError_t launch_finalize(WsPtrs ws, int64_t* out_nVtx, cudaStream_t st);

@@ -13,11 +13,14 @@
 
 namespace reindex {
 
-template <int S, int kHist>
+// S is the vertex stride.  In batched mode (kSeg) the item key is the owning mesh's id followed
+// by the vertex words (SI = S + 4 bytes), so that one sort groups the items by mesh.
+template <int S, int kHist, bool kSeg>
 __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ vtx, int64_t nVtx, WsPtrs ws,
-                                                       int64_t tilesV) {
-  constexpr int K = S / 4;
-  constexpr int P = S;  // byte digits per key
+                                                       int64_t tilesV, SegArgs seg) {
+  constexpr int SI = kSeg ? S + 4 : S;  // item key bytes
+  constexpr int K = SI / 4;
+  constexpr int P = SI;  // byte digits per key
   __shared__ uint32_t s_hist[P * kRadix];
   __shared__ uint32_t s_warp[kWarps];
   __shared__ uint32_t s_tile, s_prefix;
@@ -46,7 +49,18 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
     for (int r = 0; r < kCompactRows; ++r) {
       const uint32_t word = __shfl_sync(0xffffffffu, myword, r);
       const uint32_t u = (word >> lane) & 1u;
-      if (u) load_key<S>(vtx, vbase + r * 32 + lane, k[r]);
+      if (u) {
+        const int64_t v = vbase + r * 32 + lane;
+        if constexpr (kSeg) {
+          uint32_t kv[S / 4];
+          load_key<S>(vtx, v, kv);
+          k[r][0] = seg_mesh(v, seg.vtxOff, 1, seg.blkV, seg.nMeshes);
+#pragma unroll
+          for (int q = 0; q < S / 4; ++q) k[r][1 + q] = kv[q];
+        } else {
+          load_key<S>(vtx, v, k[r]);
+        }
+      }
       pos[r] = cnt + __popc(word & lanemask_lt());
       cnt += __popc(word);
       used |= u << r;
@@ -84,11 +98,11 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
       const uint32_t umask = __ballot_sync(0xffffffffu, u);
       if (umask == 0) continue;  // warp-uniform
       if (u) {
-        Item<S> it;
+        Item<SI> it;
 #pragma unroll
         for (int q = 0; q < K; ++q) it.k[q] = k[r][q];
         it.id = (uint32_t)(vbase + r * 32 + lane);
-        ItemIO<S>::store(ws.itemsA, ws.idoff, obase + pos[r], it);
+        ItemIO<SI>::store(ws.itemsA, ws.idoff, obase + pos[r], it);
       }
       // Histograms.  Many key bytes are heavily skewed (exponent bytes, the zero low bytes of
       // small integers), and lanes adding to the same bin in one instruction serialise, so the
@@ -128,10 +142,14 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
 template <int S>
 static int occ() {
   int a = 0, b = 0, c = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistUniform>, kThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistPeel>, kThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_compact<S, kHistMatchAny>, kThreads, 0);
-  const int n = min(a, min(b, c));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistUniform, false>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistPeel, false>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_compact<S, kHistMatchAny, false>, kThreads, 0);
+  int n = min(a, min(b, c));
+  if constexpr (S <= 16) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistUniform, true>, kThreads, 0);
+    n = min(n, a);
+  }
   return n < 1 ? 1 : n;
 }
 
@@ -140,30 +158,43 @@ int occupancy_compact(int S) {
     case 4: return occ<4>();
     case 8: return occ<8>();
     case 12: return occ<12>();
-    default: return occ<16>();
+    case 16: return occ<16>();
+    default: return occ<20>();
   }
 }
 
-template <int S>
-static void launch_s(int g, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, int mode, cudaStream_t st) {
-  if (mode == kHistMatchAny)
-    k_compact<S, kHistMatchAny><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV);
-  else if (mode == kHistPeel)
-    k_compact<S, kHistPeel><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV);
+template <int S, bool kSeg>
+static void launch_s(int g, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, int mode, const SegArgs& seg,
+                     cudaStream_t st) {
+  if (kSeg || mode == kHistUniform)
+    k_compact<S, kHistUniform, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg);
+  else if (mode == kHistMatchAny)
+    k_compact<S, kHistMatchAny, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg);
   else
-    k_compact<S, kHistUniform><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV);
+    k_compact<S, kHistPeel, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg);
 }
 
 cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
-                           cudaStream_t st) {
+                           const SegArgs* seg, cudaStream_t st) {
   if (tilesV == 0) return cudaSuccess;
-  int64_t g = (int64_t)c.sms * c.occ_compact;
+  int64_t g = c.grid_per_tile ? tilesV : (int64_t)c.sms * c.occ_compact;
   if (g > tilesV) g = tilesV;
-  switch (S) {
-    case 4: launch_s<4>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, st); break;
-    case 8: launch_s<8>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, st); break;
-    case 12: launch_s<12>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, st); break;
-    default: launch_s<16>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, st); break;
+  const SegArgs none{};
+  if (seg) {
+    switch (S) {
+      case 4: launch_s<4, true>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, *seg, st); break;
+      case 8: launch_s<8, true>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, *seg, st); break;
+      case 12: launch_s<12, true>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, *seg, st); break;
+      default: launch_s<16, true>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, *seg, st); break;
+    }
+  } else {
+    switch (S) {
+      case 4: launch_s<4, false>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, none, st); break;
+      case 8: launch_s<8, false>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, none, st); break;
+      case 12: launch_s<12, false>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, none, st); break;
+      case 16: launch_s<16, false>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, none, st); break;
+      default: launch_s<20, false>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, none, st); break;
+    }
   }
   return cudaGetLastError();
 }

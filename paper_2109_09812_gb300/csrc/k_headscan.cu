@@ -5,7 +5,8 @@
 //   oldToNew[orgID[j]] = newIdx[j]                           (Section 2.4: perm composed with newIdx)
 //   newVtx[newIdx[j]] = key[j] for every head j              (Section 2.3)
 //   *out_nVtx = total number of heads                        (Section 2.3, newN)
-// The prefix sum is a decoupled look-back scan over tiles of 4096 items (512 threads x 8);
+// The prefix sum is a decoupled look-back scan over tiles of 2048 items (256 threads x 8; four
+// CTAs per SM, so that the others keep working while one waits in its look-back);
 // neither nodup nor newIdx is materialised.
 #include "internal.h"
 
@@ -13,9 +14,12 @@ namespace reindex {
 
 constexpr int kHeadWarps = kHeadThreads / 32;
 
-template <int S>
-__global__ void __launch_bounds__(kHeadThreads, 2) k_head_scan(WsPtrs ws, void* __restrict__ out_vtx,
-                                                         int64_t* __restrict__ out_nVtx, uint32_t nVtx) {
+// S is the item key size.  In batched mode (kSeg) key word 0 is the mesh id: only words 1.. are
+// written to out_vtx, and the first item of each mesh records that mesh's first output vertex.
+template <int S, bool kSeg>
+__global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsPtrs ws, void* __restrict__ out_vtx,
+                                                         int64_t* __restrict__ out_nVtx, uint32_t nVtx,
+                                                         SegArgs seg) {
   constexpr int K = S / 4;
   __shared__ uint32_t s_warp[kHeadWarps];
   __shared__ uint32_t s_tile, s_prefix;
@@ -56,11 +60,11 @@ __global__ void __launch_bounds__(kHeadThreads, 2) k_head_scan(WsPtrs ws, void* 
     }
 
     uint32_t within[kHeadIpt];
-    uint32_t heads = 0, cnt = 0;
+    uint32_t heads = 0, cnt = 0, firsts = 0;
 #pragma unroll
     for (int r = 0; r < kHeadIpt; ++r) {
       const int64_t j = wbase + r * 32 + lane;
-      bool diff = false;
+      bool diff = false, mesh_diff = false;
 #pragma unroll
       for (int q = 0; q < K; ++q) {
         const uint32_t up = __shfl_up_sync(0xffffffffu, it[r].k[q], 1);
@@ -72,11 +76,13 @@ __global__ void __launch_bounds__(kHeadThreads, 2) k_head_scan(WsPtrs ws, void* 
           pk = lane ? up : last;
         }
         diff |= it[r].k[q] != pk;
+        if (q == 0) mesh_diff = it[r].k[0] != pk;
       }
       const bool head = (j < U) && (j == 0 || diff);
       const uint32_t m = __ballot_sync(0xffffffffu, head);
       within[r] = cnt + __popc(m & lanemask_lt());
       heads |= (uint32_t)head << r;
+      if (kSeg) firsts |= (uint32_t)((j < U) && (j == 0 || mesh_diff)) << r;
       cnt += __popc(m);
     }
     if (lane == 0) s_warp[w] = cnt;
@@ -114,7 +120,17 @@ __global__ void __launch_bounds__(kHeadThreads, 2) k_head_scan(WsPtrs ws, void* 
         const uint32_t nid = head ? e : e - 1u;
         if (it[r].id < nVtx) {
           st_u32_hint(ws.old2new + it[r].id, nid, keep);
-          if (head) store_key<S>(out_vtx, nid, it[r].k);
+          if constexpr (kSeg) {
+            if (head) {
+              uint32_t v[K - 1];
+#pragma unroll
+              for (int q = 1; q < K; ++q) v[q - 1] = it[r].k[q];
+              store_key<S - 4>(out_vtx, nid, v);
+            }
+            if ((firsts >> r) & 1u) seg.outOff[it[r].k[0]] = (int64_t)nid;
+          } else {
+            if (head) store_key<S>(out_vtx, nid, it[r].k);
+          }
         } else {
           record_error(ctrl, kErrInternal);  // corrupted item: never write out of range
         }
@@ -127,7 +143,7 @@ __global__ void __launch_bounds__(kHeadThreads, 2) k_head_scan(WsPtrs ws, void* 
 template <int S>
 static int occ() {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_head_scan<S>, kHeadThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_head_scan<S, false>, kHeadThreads, 0);
   return n < 1 ? 1 : n;
 }
 
@@ -136,21 +152,39 @@ int occupancy_head(int S) {
     case 4: return occ<4>();
     case 8: return occ<8>();
     case 12: return occ<12>();
-    default: return occ<16>();
+    case 16: return occ<16>();
+    default: return occ<20>();
   }
 }
 
+template <int S, bool kSeg>
+static void launch_s(int g, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx, const SegArgs& seg,
+                     cudaStream_t st) {
+  k_head_scan<S, kSeg><<<g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx, seg);
+}
+
 cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx,
-                             const LaunchCfg& c, cudaStream_t st) {
+                             const LaunchCfg& c, const SegArgs* seg, cudaStream_t st) {
   int64_t tiles = (ws.Umax + kHeadTile - 1) / kHeadTile;
-  int64_t g = (int64_t)c.sms * c.occ_head;
+  int64_t g = c.grid_per_tile ? tiles : (int64_t)c.sms * c.occ_head;
   if (g > tiles) g = tiles;
   if (g < 1) g = 1;
-  switch (S) {
-    case 4: k_head_scan<4><<<(int)g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
-    case 8: k_head_scan<8><<<(int)g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
-    case 12: k_head_scan<12><<<(int)g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
-    default: k_head_scan<16><<<(int)g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx); break;
+  const SegArgs none{};
+  if (seg) {
+    switch (S) {
+      case 8: launch_s<8, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, st); break;
+      case 12: launch_s<12, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, st); break;
+      case 16: launch_s<16, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, st); break;
+      default: launch_s<20, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, st); break;
+    }
+  } else {
+    switch (S) {
+      case 4: launch_s<4, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, st); break;
+      case 8: launch_s<8, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, st); break;
+      case 12: launch_s<12, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, st); break;
+      case 16: launch_s<16, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, st); break;
+      default: launch_s<20, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, st); break;
+    }
   }
   return cudaGetLastError();
 }

@@ -74,6 +74,22 @@ struct Stage<16> {
   }
 };
 
+template <>
+struct Stage<20> {
+  static constexpr size_t bytes = (size_t)kSortTile * 24;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<20>& it) {
+    uint2* q = reinterpret_cast<uint2*>(sm) + 3 * p;
+    q[0] = make_uint2(it.k[0], it.k[1]);
+    q[1] = make_uint2(it.k[2], it.k[3]);
+    q[2] = make_uint2(it.k[4], it.id);
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<20>& it) {
+    const uint2* q = reinterpret_cast<const uint2*>(sm) + 3 * p;
+    const uint2 a = q[0], b = q[1], c = q[2];
+    it.k[0] = a.x; it.k[1] = a.y; it.k[2] = b.x; it.k[3] = b.y; it.k[4] = c.x; it.id = c.y;
+  }
+};
+
 constexpr int kSortWarps = kSortThreads / 32;
 
 template <int S>
@@ -101,8 +117,9 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t dig, bool valid) {
   }
 }
 
+// 20-byte items need more registers and shared memory: one CTA per SM.
 template <int S, int kWord, int kMode>
-__global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(WsPtrs ws, int d) {
+__global__ void __launch_bounds__(kSortThreads, S >= 20 ? 1 : 2) k_onesweep(WsPtrs ws, int d) {
   constexpr int K = S / 4;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   unsigned char* stage = sm_raw;                                               // tile in digit order
@@ -255,6 +272,7 @@ static int occ_mode() {
   if constexpr (S >= 8) n = min(n, occ_one<S, 1, kMode>());
   if constexpr (S >= 12) n = min(n, occ_one<S, 2, kMode>());
   if constexpr (S >= 16) n = min(n, occ_one<S, 3, kMode>());
+  if constexpr (S >= 20) n = min(n, occ_one<S, 4, kMode>());
   return n;
 }
 
@@ -268,7 +286,8 @@ int occupancy_sort(int S) {
     case 4: return occ<4>();
     case 8: return occ<8>();
     case 12: return occ<12>();
-    default: return occ<16>();
+    case 16: return occ<16>();
+    default: return occ<20>();
   }
 }
 
@@ -279,7 +298,8 @@ static void launch_mode(int g, int digit, WsPtrs ws, cudaStream_t st) {
     case 0: k_onesweep<S, 0, kMode><<<g, kSortThreads, SortSmem<S>::bytes, st>>>(ws, digit); break;
     case 1: if constexpr (S >= 8) k_onesweep<S, 1, kMode><<<g, kSortThreads, SortSmem<S>::bytes, st>>>(ws, digit); break;
     case 2: if constexpr (S >= 12) k_onesweep<S, 2, kMode><<<g, kSortThreads, SortSmem<S>::bytes, st>>>(ws, digit); break;
-    default: if constexpr (S >= 16) k_onesweep<S, 3, kMode><<<g, kSortThreads, SortSmem<S>::bytes, st>>>(ws, digit); break;
+    case 3: if constexpr (S >= 16) k_onesweep<S, 3, kMode><<<g, kSortThreads, SortSmem<S>::bytes, st>>>(ws, digit); break;
+    default: if constexpr (S >= 20) k_onesweep<S, 4, kMode><<<g, kSortThreads, SortSmem<S>::bytes, st>>>(ws, digit); break;
   }
 }
 
@@ -292,14 +312,15 @@ static void launch_s(int g, int digit, WsPtrs ws, int mode, cudaStream_t st) {
 }
 
 cudaError_t launch_onesweep(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st) {
-  int64_t g = (int64_t)c.sms * c.occ_sort;
+  int64_t g = c.grid_per_tile ? (ws.Umax + kSortTile - 1) / kSortTile : (int64_t)c.sms * c.occ_sort;
   if (g > ws.tilesS) g = ws.tilesS;
   if (g < 1) return cudaSuccess;
   switch (S) {
     case 4: launch_s<4>((int)g, digit, ws, c.rank_mode, st); break;
     case 8: launch_s<8>((int)g, digit, ws, c.rank_mode, st); break;
     case 12: launch_s<12>((int)g, digit, ws, c.rank_mode, st); break;
-    default: launch_s<16>((int)g, digit, ws, c.rank_mode, st); break;
+    case 16: launch_s<16>((int)g, digit, ws, c.rank_mode, st); break;
+    default: launch_s<20>((int)g, digit, ws, c.rank_mode, st); break;
   }
   return cudaGetLastError();
 }

@@ -36,11 +36,15 @@ template <>
 struct Pipe<16> {
   static constexpr int kThreads = 512, kTile = 3072;
 };
+template <>
+struct Pipe<20> {
+  static constexpr int kThreads = 512, kTile = 2048;
+};
 
 template <int S>
 struct PipeSmem {
   static constexpr int T = Pipe<S>::kTile, NT = Pipe<S>::kThreads, NW = NT / 32;
-  static constexpr bool kAos = (S == 4 || S == 12);
+  static constexpr bool kAos = (S == 4 || S == 12 || S == 20);
   static constexpr int kRows = T / NT;  // 32-item rows per warp
   static constexpr size_t buf = kAos ? (size_t)T * (S + 4) : (size_t)T * (S + 4);
   static constexpr size_t ids = kAos ? 0 : (size_t)T * S;  // id plane offset inside a buffer (SoA)
@@ -130,10 +134,14 @@ __device__ __forceinline__ void smem_item(const unsigned char* buf, int i, Item<
     const uint2 v = reinterpret_cast<const uint2*>(buf)[i];
     it.k[0] = v.x; it.k[1] = v.y;
     it.id = reinterpret_cast<const uint32_t*>(buf + PipeSmem<S>::ids)[i];
-  } else {
+  } else if constexpr (S == 16) {
     const uint4 v = reinterpret_cast<const uint4*>(buf)[i];
     it.k[0] = v.x; it.k[1] = v.y; it.k[2] = v.z; it.k[3] = v.w;
     it.id = reinterpret_cast<const uint32_t*>(buf + PipeSmem<S>::ids)[i];
+  } else {
+    const uint2* q = reinterpret_cast<const uint2*>(buf) + 3 * i;
+    const uint2 a = q[0], b = q[1], c = q[2];
+    it.k[0] = a.x; it.k[1] = a.y; it.k[2] = b.x; it.k[3] = b.y; it.k[4] = c.x; it.id = c.y;
   }
 }
 
@@ -321,6 +329,7 @@ static int occ() {
   if constexpr (S >= 8) n = min(n, occ_one<S, 1>());
   if constexpr (S >= 12) n = min(n, occ_one<S, 2>());
   if constexpr (S >= 16) n = min(n, occ_one<S, 3>());
+  if constexpr (S >= 20) n = min(n, occ_one<S, 4>());
   return n;
 }
 
@@ -329,7 +338,8 @@ int occupancy_sort_pipe(int S) {
     case 4: return occ<4>();
     case 8: return occ<8>();
     case 12: return occ<12>();
-    default: return occ<16>();
+    case 16: return occ<16>();
+    default: return occ<20>();
   }
 }
 
@@ -342,7 +352,8 @@ static void launch_s(int g, int digit, WsPtrs ws, cudaStream_t st) {
     case 0: k_onesweep_pipe<S, 0><<<g, NT, sm, st>>>(ws, digit); break;
     case 1: if constexpr (S >= 8) k_onesweep_pipe<S, 1><<<g, NT, sm, st>>>(ws, digit); break;
     case 2: if constexpr (S >= 12) k_onesweep_pipe<S, 2><<<g, NT, sm, st>>>(ws, digit); break;
-    default: if constexpr (S >= 16) k_onesweep_pipe<S, 3><<<g, NT, sm, st>>>(ws, digit); break;
+    case 3: if constexpr (S >= 16) k_onesweep_pipe<S, 3><<<g, NT, sm, st>>>(ws, digit); break;
+    default: if constexpr (S >= 20) k_onesweep_pipe<S, 4><<<g, NT, sm, st>>>(ws, digit); break;
   }
 }
 
@@ -354,7 +365,8 @@ cudaError_t launch_onesweep_pipe(int S, int digit, WsPtrs ws, const LaunchCfg& c
     case 4: launch_s<4>((int)g, digit, ws, st); break;
     case 8: launch_s<8>((int)g, digit, ws, st); break;
     case 12: launch_s<12>((int)g, digit, ws, st); break;
-    default: launch_s<16>((int)g, digit, ws, st); break;
+    case 16: launch_s<16>((int)g, digit, ws, st); break;
+    default: launch_s<20>((int)g, digit, ws, st); break;
   }
   return cudaGetLastError();
 }

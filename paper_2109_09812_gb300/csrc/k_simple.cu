@@ -28,7 +28,10 @@ __device__ __forceinline__ void mark_used(int32_t v, uint32_t nVtx, uint32_t* bi
 }
 
 // One bit per vertex, set by every index that references it (Section 2.1).  Indices are read
-// with 128-bit loads when the array is 16-byte aligned.
+// with 128-bit loads when the array is 16-byte aligned, kBatch vectors per thread at a time so
+// that enough loads are in flight.
+constexpr int kBatch = 4;
+
 template <bool kVec>
 __global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int64_t M, uint32_t nVtx,
                                                           uint32_t* bitmask, Control* ctrl) {
@@ -39,12 +42,20 @@ __global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int
   if (kVec) {
     const int4* v4 = reinterpret_cast<const int4*>(idx);
     const int64_t n4 = M >> 2;
-    for (int64_t i = t0; i < n4; i += stride) {
-      const int4 q = __ldcs(v4 + i);
-      mark_used(q.x, nVtx, bitmask, bad);
-      mark_used(q.y, nVtx, bitmask, bad);
-      mark_used(q.z, nVtx, bitmask, bad);
-      mark_used(q.w, nVtx, bitmask, bad);
+    for (int64_t i = t0; i < n4; i += stride * kBatch) {
+      int4 q[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b)
+        if (i + b * stride < n4) q[b] = __ldcs(v4 + i + b * stride);
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        if (i + b * stride < n4) {
+          mark_used(q[b].x, nVtx, bitmask, bad);
+          mark_used(q[b].y, nVtx, bitmask, bad);
+          mark_used(q[b].z, nVtx, bitmask, bad);
+          mark_used(q[b].w, nVtx, bitmask, bad);
+        }
+      }
     }
     done = n4 << 2;
   }
@@ -88,12 +99,11 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P) {
 }
 
 // out_idx[j] = oldToNew[idx[j]] (Section 2.4).  Safe in place: each slot is read and written
-// by the same thread.
+// by the same thread.  kBatch index vectors are loaded before their 4*kBatch gathers are issued.
 template <bool kVec>
 __global__ void __launch_bounds__(kThreads) k_remap(const int32_t* idx, int32_t* out, int64_t M,
                                                      const uint32_t* __restrict__ o2n, const Control* ctrl) {
   if (ctrl->err) return;  // outputs are unspecified after a device-detected error
-  const uint64_t drop = l2_policy_evict_first();  // oldToNew is dead after this kernel
   const int64_t t0 = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * kThreads;
   int64_t done = 0;
@@ -101,18 +111,29 @@ __global__ void __launch_bounds__(kThreads) k_remap(const int32_t* idx, int32_t*
     const int4* in4 = reinterpret_cast<const int4*>(idx);
     int4* out4 = reinterpret_cast<int4*>(out);
     const int64_t n4 = M >> 2;
-    for (int64_t i = t0; i < n4; i += stride) {
-      const int4 q = __ldcs(in4 + i);
-      int4 r;
-      r.x = (int32_t)ld_u32_hint(o2n + q.x, drop);
-      r.y = (int32_t)ld_u32_hint(o2n + q.y, drop);
-      r.z = (int32_t)ld_u32_hint(o2n + q.z, drop);
-      r.w = (int32_t)ld_u32_hint(o2n + q.w, drop);
-      __stcs(out4 + i, r);
+    for (int64_t i = t0; i < n4; i += stride * kBatch) {
+      int4 q[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b)
+        if (i + b * stride < n4) q[b] = __ldcs(in4 + i + b * stride);
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        if (i + b * stride < n4) {
+          int4 r;
+          r.x = (int32_t)__ldg(o2n + q[b].x);
+          r.y = (int32_t)__ldg(o2n + q[b].y);
+          r.z = (int32_t)__ldg(o2n + q[b].z);
+          r.w = (int32_t)__ldg(o2n + q[b].w);
+          q[b] = r;
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b)
+        if (i + b * stride < n4) __stcs(out4 + i + b * stride, q[b]);
     }
     done = n4 << 2;
   }
-  for (int64_t i = done + t0; i < M; i += stride) out[i] = (int32_t)ld_u32_hint(o2n + idx[i], drop);
+  for (int64_t i = done + t0; i < M; i += stride) out[i] = (int32_t)__ldg(o2n + idx[i]);
 }
 
 __global__ void k_finalize(Control* ctrl, int64_t* out_nVtx) {

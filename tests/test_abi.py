@@ -39,7 +39,7 @@ def test_status_strings(L):
                        (6, "REINDEX_ERR_CUDA"), (7, "REINDEX_ERR_INTERNAL")]:
         assert rx.reindex_status_string(code) == name
     assert rx.reindex_status_string(99) == "REINDEX_ERR_UNKNOWN"
-    assert [L.reindex_kernel_name(i).decode() for i in range(8)] == rx.KERNEL_NAMES
+    assert [L.reindex_kernel_name(i).decode() for i in range(len(rx.KERNEL_NAMES))] == rx.KERNEL_NAMES
 
 
 def test_workspace_size_model(L):

@@ -71,7 +71,7 @@ SIZES = [(1, 3), (2, 4), (33, 30), (2047, 2047), (2049, 6000), (4096, 4096), (40
          (70001, 70001), (150_000, 40_000)]
 
 
-@pytest.mark.parametrize("S", [4, 8, 12, 16])
+@pytest.mark.parametrize("S", [4, 8, 12, 16, 20])
 @pytest.mark.parametrize("mode", ["random", "dups", "floats", "const"])
 def test_random_meshes(rx, S, mode):
     rng = np.random.default_rng(1000 + S * 10 + ["random", "dups", "floats", "const"].index(mode))
@@ -240,7 +240,7 @@ def test_profile_records_every_kernel(rx):
     recs = rx.profile_collect()
     names = [r["name"] for r in recs]
     assert names.count("onesweep") == 12
-    assert set(names) == set(rx.KERNEL_NAMES)
+    assert set(names) == set(rx.KERNEL_NAMES) - {"seg_prepare", "seg_offsets"}
     # x and y are integers 0..256 as float32: their lowest byte is always zero -> skipped passes
     sk = {r["digit"]: r["skipped"] for r in recs if r["name"] == "onesweep"}
     assert sk[8] and sk[4] and not sk[0]
