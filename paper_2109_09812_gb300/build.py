@@ -16,6 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libreindex.so")
+SYNTH_SRC = os.path.join(HERE, "synth_gpu.cu")
+SYNTH_LIB = os.path.join(HERE, "libsynth.so")  # device input generators (not part of the method)
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr",
@@ -70,6 +72,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         tmp = LIB + f".tmp{os.getpid()}"
         run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-ldl", "-lpthread", "-lrt"])
         os.replace(tmp, LIB)
+    if force or _stale(SYNTH_LIB, [SYNTH_SRC]):
+        tmp = SYNTH_LIB + f".tmp{os.getpid()}"
+        run([cc, *ARCH, *FLAGS, *extra_flags, "-shared", "-o", tmp, SYNTH_SRC, "-lcudart_static", "-ldl", "-lpthread",
+             "-lrt"])
+        os.replace(tmp, SYNTH_LIB)
     return LIB
 
 

@@ -72,11 +72,40 @@ def unit_float(h: np.ndarray) -> np.ndarray:
     return (h >> _U64(40)).astype(np.float32) * np.float32(1.0 / 16777216.0)
 
 
+def _feistel(x: np.ndarray, half_bits: int, seed: int) -> np.ndarray:
+    """Four-round balanced Feistel network on 2*half_bits-bit integers (a bijection), round
+    function = low half_bits of hash(seed, TAG_PERM, round, right half)."""
+    mask = _U64((1 << half_bits) - 1)
+    hb = _U64(half_bits)
+    left, right = x >> hb, x & mask
+    for rnd in range(4):
+        f = hash_u64(seed, TAG_PERM, rnd, right.astype(np.int64)) & mask
+        left, right = right, left ^ f
+    return (left << hb) | right
+
+
+def permutation_dest(n: int, seed: int, i: np.ndarray) -> np.ndarray:
+    """Destination of position i under a random permutation of [0, n): a Feistel network on the
+    smallest even-bit-width power-of-two domain >= n, with cycle walking into [0, n) (Black and
+    Rogaway, "Ciphers with arbitrary finite domains", CT-RSA 2002).  Counter-based: every
+    position is computed on its own, so a GPU computes the same permutation element by element."""
+    bits = max(2, int(n - 1).bit_length() if n > 1 else 1)
+    bits += bits & 1
+    x = np.asarray(i, dtype=_U64).copy()
+    pending = np.ones(x.shape, dtype=bool)
+    nn = _U64(n)
+    while pending.any():
+        x[pending] = _feistel(x[pending], bits // 2, seed)
+        pending = x >= nn
+    return x.astype(np.int64)
+
+
 def permutation(n: int, seed: int) -> np.ndarray:
-    """Random permutation of [0, n): argsort of per-position hashes (ties impossible in practice,
-    broken by position through the stable sort)."""
-    keys = hash_u64(seed, TAG_PERM, np.arange(n, dtype=np.int64))
-    return np.argsort(keys, kind="stable").astype(np.int64)
+    """src array of a random permutation of [0, n): position p receives element src[p]."""
+    dst = permutation_dest(n, seed, np.arange(n, dtype=np.int64))
+    src = np.empty(n, dtype=np.int64)
+    src[dst] = np.arange(n, dtype=np.int64)
+    return src
 
 
 @dataclass
@@ -139,10 +168,10 @@ def _append_unused_and_permute(soup: np.ndarray, n_extra: int, extra_fn, seed: i
     n = vtx.shape[0]
     if not permute:
         return np.ascontiguousarray(vtx), np.arange(m, dtype=np.int32)
-    src = permutation(n, seed)
-    dst = np.empty(n, dtype=np.int64)
-    dst[src] = np.arange(n, dtype=np.int64)
-    return np.ascontiguousarray(vtx[src]), dst[:m].astype(np.int32)
+    dst = permutation_dest(n, seed, np.arange(n, dtype=np.int64))  # vertex i moves to dst[i]
+    out = np.empty_like(vtx)
+    out[dst] = vtx
+    return out, dst[:m].astype(np.int32)
 
 
 def heightfield_soup(G: int, Gy: int | None = None, unused_frac: float = 0.10, seed: int = 1,
@@ -297,6 +326,74 @@ def batched_heightfield_sizes(n_meshes: int, seed: int = 4, min_tris: int = 64, 
 def batched_heightfield(n_meshes: int, seed: int = 4, **kw) -> list[Mesh]:
     """Independent heightfield soups for the batched workload (see ``batched_heightfield_sizes``)."""
     return [heightfield_soup(g, gy, uf, s) for (g, gy, uf, s) in batched_heightfield_sizes(n_meshes, seed, **kw)]
+
+
+# ---------------------------------------------------------------------------------------------
+# Device generators (libsynth.so): bit-identical to the functions above, for workloads too large
+# to build on the host.  They return torch CUDA tensors and never touch the re-indexing library.
+_synth_lib = None
+
+
+def _gpu_lib():
+    global _synth_lib
+    if _synth_lib is None:
+        import ctypes
+        import os
+
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsynth.so")
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -m paper_2109_09812_gb300.build`")
+        L = ctypes.CDLL(path)
+        vp, i64 = ctypes.c_void_p, ctypes.c_int64
+        L.synth_heightfield.argtypes = [vp, vp, i64, i64, i64, ctypes.c_uint64, ctypes.c_int, vp]
+        L.synth_heightfield.restype = ctypes.c_int
+        L.synth_tets.argtypes = [vp, vp, i64, i64, ctypes.c_uint64, ctypes.c_int, vp]
+        L.synth_tets.restype = ctypes.c_int
+        _synth_lib = L
+    return _synth_lib
+
+
+def _stream_ptr(torch, stream):
+    import ctypes
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def heightfield_soup_gpu(G: int, Gy: int | None = None, unused_frac: float = 0.10, seed: int = 1, device="cuda",
+                         permute: bool = True, stream=None):
+    """heightfield_soup on the GPU: returns (vtx float32 (N, 3), idx int32 (2*G*Gy, 3)) CUDA tensors."""
+    import ctypes
+
+    import torch
+
+    Gy = G if Gy is None else Gy
+    m = 6 * G * Gy
+    n_extra = int(math.floor(unused_frac * m + 0.5))
+    vtx = torch.empty((m + n_extra, 3), dtype=torch.float32, device=device)
+    idx = torch.empty((2 * G * Gy, 3), dtype=torch.int32, device=device)
+    rc = _gpu_lib().synth_heightfield(ctypes.c_void_p(vtx.data_ptr()), ctypes.c_void_p(idx.data_ptr()), G, Gy, n_extra,
+                                      seed, int(permute), _stream_ptr(torch, stream))
+    if rc:
+        raise RuntimeError(f"synth_heightfield: CUDA error {rc}")
+    return vtx, idx
+
+
+def tet_soup_gpu(L: int, unused_frac: float = 0.03, seed: int = 3, device="cuda", permute: bool = True, stream=None):
+    """tet_soup on the GPU: returns (vtx float32 (N, 4), idx int32 (5*L^3, 4)) CUDA tensors."""
+    import ctypes
+
+    import torch
+
+    m = 20 * L ** 3
+    n_extra = int(math.floor(unused_frac * m + 0.5))
+    vtx = torch.empty((m + n_extra, 4), dtype=torch.float32, device=device)
+    idx = torch.empty((5 * L ** 3, 4), dtype=torch.int32, device=device)
+    rc = _gpu_lib().synth_tets(ctypes.c_void_p(vtx.data_ptr()), ctypes.c_void_p(idx.data_ptr()), L, n_extra, seed,
+                               int(permute), _stream_ptr(torch, stream))
+    if rc:
+        raise RuntimeError(f"synth_tets: CUDA error {rc}")
+    return vtx, idx
 
 
 def config_mesh(cfg: int) -> Mesh:

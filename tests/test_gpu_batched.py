@@ -153,3 +153,24 @@ def test_batched_graph_capture_replay(rx):
     g.replay()
     torch.cuda.synchronize()
     check_against_oracle(meshes, out_v.cpu().numpy().view(np.uint32), out_off.cpu().numpy(), out_i.cpu().numpy())
+
+
+# ------------------------------------------------------------------------- device generators
+
+
+@pytest.mark.parametrize("G,Gy,frac,seed", [(1, 1, 0.0, 1), (7, 3, 0.1, 2), (64, 50, 0.05, 9), (256, 256, 0.10, 1)])
+def test_device_heightfield_generator_matches_host(rx, G, Gy, frac, seed):
+    m = synth.heightfield_soup(G, Gy, frac, seed)
+    v, i = synth.heightfield_soup_gpu(G, Gy, frac, seed)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(v.cpu().numpy().view(np.uint32), m.vtx)
+    np.testing.assert_array_equal(i.cpu().numpy(), m.idx)
+
+
+@pytest.mark.parametrize("L,frac,seed", [(1, 0.0, 3), (5, 0.03, 4), (24, 0.03, 3)])
+def test_device_tet_generator_matches_host(rx, L, frac, seed):
+    m = synth.tet_soup(L, frac, seed)
+    v, i = synth.tet_soup_gpu(L, frac, seed)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(v.cpu().numpy().view(np.uint32), m.vtx)
+    np.testing.assert_array_equal(i.cpu().numpy(), m.idx)
