@@ -43,6 +43,10 @@ WORKLOADS = {
     "batched4096": ("4096 independent heightfield triangle soups (float32 xyz, int32 idx x3), triangle counts "
                     "log-uniform in [64, 200000], 0-10% unused vertices each, each permuted, seed 4; one "
                     "reindex_meshes launch sequence replayed as a CUDA graph vs one reindex_mesh_ws call per mesh", 4),
+    "serving20000": ("serving: Poisson arrivals of 20,000 re-index requests, element counts log-uniform in "
+                     "[1e3, 4e6] (70% heightfield triangle soups, float32 xyz, 3 idx; 30% tet soups, 16-B vertices, "
+                     "4 idx), 0-10% unused, generated on the device just before arrival, admitted against a 40 GB "
+                     "HBM budget and coalesced into reindex_meshes batches on 2 streams", 5),
     # a half-size case of the 2048^2 workload, for profiler captures (still larger than L2)
     "heightfield1448": ("heightfield triangle soup 1448x1448 cells (4,193,408 tris, 12,580,224 soup vertices "
                         "float32 xyz + 5% unused, permuted), int32 idx x3, seed 2", (1448, 0.05, 2)),
@@ -350,6 +354,99 @@ def run_batched_bench(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_serving_bench(args, world, rank, local):
+    """Serving: capacity from a closed-loop run, then open-loop Poisson arrivals at fractions of
+    that capacity; latency = completion - arrival (host monotonic clock, as the library's)."""
+    import collections
+
+    import torch
+
+    import paper_2109_09812_gb300 as rx
+    from paper_2109_09812_gb300 import build as rxbuild
+    from paper_2109_09812_gb300 import synth
+
+    rxbuild.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n_req = args.requests
+    specs = synth.serving_requests(n_req, seed=5)
+    elems = np.array([sp["n_elem"] for sp in specs], dtype=np.float64)
+    gen_stream = torch.cuda.Stream(dev)
+
+    def gen(r):
+        with torch.cuda.stream(gen_stream):
+            v, i = synth.generate_request(specs[r], device=dev, stream=gen_stream)
+            ev = torch.cuda.Event()
+            ev.record(gen_stream)
+        return v.view(torch.int32), i, ev
+
+    def run(rate_rps, n):
+        """Submit requests 0..n-1 at Poisson times (rate_rps <= 0: all at once); returns stats."""
+        rng = np.random.default_rng(12345)
+        gaps = rng.exponential(1.0 / rate_rps, size=n) if rate_rps > 0 else np.zeros(n)
+        arrive = np.cumsum(gaps)
+        lat, inflight, ahead = [], {}, collections.deque()
+        srv = rx.Server(hbm_budget_bytes=40 << 30, max_batch_requests=256, num_streams=2, device=local)
+        state = {"done": 0, "last_us": 0.0}
+
+        def take(results):
+            for res in results:
+                _, _, a = inflight.pop(res["id"])
+                if res["status"] != 0:
+                    raise SystemExit(f"request failed with status {res['status']}")
+                lat.append(res["done_us"] / 1e6 - a)
+                state["last_us"] = max(state["last_us"], res["done_us"])
+                srv.release(res["id"])
+                state["done"] += 1
+
+        try:
+            t0 = time.perf_counter()
+            nxt = 0
+            for r in range(n):
+                while nxt < n and nxt < r + 32:  # inputs prepared shortly before they arrive
+                    ahead.append((nxt,) + gen(nxt))
+                    nxt += 1
+                rr, v, i, ev = ahead.popleft()
+                while time.perf_counter() - t0 < arrive[r]:
+                    take(srv.poll(wait_ms=0))
+                ev.synchronize()
+                rid = srv.submit(v, i)
+                inflight[rid] = (v, i, t0 + arrive[r])
+                take(srv.poll(wait_ms=0))
+            while state["done"] < n:
+                take(srv.poll(wait_ms=20))
+            st = srv.stats()
+        finally:
+            srv.close()
+        span = state["last_us"] / 1e6 - t0
+        lat_ms = np.array(lat) * 1e3
+        return {"requests": n, "elements": float(elems[:n].sum()), "seconds": span,
+                "elements_per_s": float(elems[:n].sum() / span), "p50_ms": float(np.percentile(lat_ms, 50)),
+                "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(lat_ms.max()),
+                "batches": st["batches"], "failed": st["requests_failed"]}
+
+    calib_n = min(n_req, 2000)
+    run(0, min(64, n_req))  # warm-up (kernels, allocator)
+    cap = run(0, calib_n)
+    capacity_eps = cap["elements_per_s"]
+    mean_elems = float(elems.mean())
+    loads = {}
+    for frac in [float(x) for x in args.loads.split(",")]:
+        loads[f"{frac:.2f}"] = run(frac * capacity_eps / mean_elems, n_req)
+    head = loads.get("0.70") or next(iter(loads.values()))
+    line = {
+        "metric": METRIC, "value": head["elements_per_s"], "unit": UNIT, "n_gpus": world, "steps": 1,
+        "warmup": 1, "ms_per_step": head["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (generated on the device)",
+        "config": {"workload": WORKLOADS[args.workload][0], "requests": n_req, "mean_elements": mean_elems,
+                   "parallelism": f"replicas x{world}", "headline_load": 0.7},
+        "latency_ms": {"p50": head["p50_ms"], "p99": head["p99_ms"], "max": head["max_ms"]},
+        "capacity_closed_loop": cap, "loads": loads,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -484,6 +581,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="heightfield2048")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--requests", type=int, default=20000, help="serving workload: number of requests")
+    ap.add_argument("--loads", default="0.5,0.7,0.9", help="serving workload: offered loads (fractions of capacity)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     try:
@@ -491,6 +590,8 @@ def main():
             run_reference(args, world, rank)
         elif args.workload == "batched4096":
             run_batched_bench(args, world, rank, local)
+        elif args.workload == "serving20000":
+            run_serving_bench(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

@@ -170,6 +170,65 @@ reindex_status reindex_meshes(const void* vtx, const int64_t* vtxOffsets, int vt
                               void* out_vtx, int64_t* out_vtxOffsets, int32_t* out_idx,
                               void* ws, size_t wsBytes, reindex_stream_t stream);
 
+/* ---- serving: a request loop with continuous batching ------------------------------------------
+ * A server owns one arena of device memory (the HBM budget) and a scheduler thread.  Clients
+ * submit requests (device-resident meshes, which must stay valid and unchanged until the request
+ * completes) at any time.  Whenever one of num_streams CUDA streams is free, the scheduler
+ * coalesces the pending requests of the oldest request's stride/arity class, in arrival order,
+ * into one reindex_meshes launch sequence, admitting only what fits the free part of the budget;
+ * requests that arrive meanwhile join the next batch, and batches on different streams overlap.
+ * Each result is identical to reindex_mesh on the request alone.  A batch whose device run fails
+ * is split and its requests re-run one by one, so that only a faulty request fails.  Results
+ * (pointers into the arena) stay valid until reindex_server_release. */
+typedef struct reindex_server reindex_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;  /* device memory for staging, outputs and workspaces (>= 1 MiB) */
+  int max_batch_requests;   /* most requests per launch sequence (<= 0: 256) */
+  int num_streams;          /* batches in flight at once (<= 0: 2) */
+  int device;               /* CUDA device ordinal */
+} reindex_server_config;
+
+typedef struct {
+  const void* vtx;          /* device, nVtx * vtxStrideBytes; vtxStrideBytes in {4, 8, 12, 16} */
+  int64_t nVtx;
+  int vtxStrideBytes;
+  const int32_t* idx;       /* device, nElem * idxPerElem */
+  int64_t nElem;
+  int idxPerElem;
+} reindex_request;
+
+typedef struct {
+  int64_t id;
+  reindex_status status;    /* REINDEX_OK or this request's error */
+  int64_t nVtxOut;          /* D */
+  const void* out_vtx;      /* device, D * stride bytes (NULL after an error) */
+  const int32_t* out_idx;   /* device, nElem * idxPerElem */
+  double submit_us, start_us, done_us;  /* host steady-clock times: submitted, launched, finished */
+} reindex_result;
+
+typedef struct {
+  int64_t requests_submitted, requests_started, requests_done, requests_failed, requests_rejected;
+  int64_t batches, batches_split, arena_bytes_in_use, pending;
+} reindex_server_stats;
+
+/* Allocates the arena (cudaMalloc, once) and starts the scheduler thread. */
+reindex_status reindex_server_create(const reindex_server_config* cfg, reindex_server** out);
+/* Non-blocking.  REINDEX_ERR_OOM: the request could not fit the budget even alone. */
+reindex_status reindex_server_submit(reindex_server* s, const reindex_request* req, int64_t* id_out);
+/* Up to max_results finished requests (waiting up to wait_ms for the first); returns the count. */
+int reindex_server_poll(reindex_server* s, reindex_result* out, int max_results, int wait_ms);
+/* Returns a finished request's outputs to the arena. */
+reindex_status reindex_server_release(reindex_server* s, int64_t id);
+/* Waits until every submitted request has finished (REINDEX_ERR_TIMEOUT after timeout_ms). */
+reindex_status reindex_server_drain(reindex_server* s, int timeout_ms);
+reindex_status reindex_server_get_stats(reindex_server* s, reindex_server_stats* out);
+/* Drops requests not yet started, waits for running batches, frees everything. */
+void reindex_server_destroy(reindex_server* s);
+/* Host-only self-check of the server's arena allocator against a brute-force model; returns the
+ * number of inconsistencies (0 = correct).  Needs no GPU. */
+int reindex_debug_arena_check(uint64_t seed, int ops, size_t size);
+
 /* Synchronises `stream`, then returns and clears this device's sticky device-side error: the
  * first INDEX_RANGE or TIMEOUT raised by any call on the current device since the last
  * reindex_stream_status() (REINDEX_OK if none).  A CUDA error from the synchronisation is

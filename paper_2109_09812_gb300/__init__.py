@@ -36,7 +36,9 @@ KERNEL_NAMES = ["clear", "used_flags", "compact_hist", "sort_plan", "onesweep", 
 # Symbols declared in include/reindex.h (checked by the ABI test).
 EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "reindex_mesh_ws",
             "reindex_mesh_host", "reindex_stream_status", "reindex_profile_enable", "reindex_profile_collect",
-            "reindex_kernel_name", "reindex_mesh_noalloc", "reindex_meshes", "reindex_meshes_workspace_size"]
+            "reindex_kernel_name", "reindex_mesh_noalloc", "reindex_meshes", "reindex_meshes_workspace_size",
+            "reindex_server_create", "reindex_server_submit", "reindex_server_poll", "reindex_server_release",
+            "reindex_server_drain", "reindex_server_get_stats", "reindex_server_destroy", "reindex_debug_arena_check"]
 
 _lock = threading.Lock()
 _lib = None
@@ -46,6 +48,28 @@ class ReindexError(RuntimeError):
     def __init__(self, code: int, where: str = ""):
         self.code = int(code)
         super().__init__(f"{where}: {reindex_status_string(self.code)}" if where else reindex_status_string(self.code))
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch_requests", ctypes.c_int),
+                ("num_streams", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("vtx", ctypes.c_void_p), ("nVtx", ctypes.c_int64), ("vtxStrideBytes", ctypes.c_int),
+                ("idx", ctypes.c_void_p), ("nElem", ctypes.c_int64), ("idxPerElem", ctypes.c_int)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int), ("nVtxOut", ctypes.c_int64),
+                ("out_vtx", ctypes.c_void_p), ("out_idx", ctypes.c_void_p), ("submit_us", ctypes.c_double),
+                ("start_us", ctypes.c_double), ("done_us", ctypes.c_double)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("requests_submitted", "requests_started", "requests_done",
+                                               "requests_failed", "requests_rejected", "batches", "batches_split",
+                                               "arena_bytes_in_use", "pending")]
 
 
 class _ProfileRecord(ctypes.Structure):
@@ -85,6 +109,22 @@ def lib() -> ctypes.CDLL:
             L.reindex_meshes_workspace_size.restype = ctypes.c_size_t
             L.reindex_meshes.argtypes = [vp, vp, ci, vp, vp, ci, ci, i64, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]
             L.reindex_meshes.restype = ci
+            L.reindex_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
+            L.reindex_server_create.restype = ci
+            L.reindex_server_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(i64)]
+            L.reindex_server_submit.restype = ci
+            L.reindex_server_poll.argtypes = [vp, ctypes.POINTER(_Result), ci, ci]
+            L.reindex_server_poll.restype = ci
+            L.reindex_server_release.argtypes = [vp, i64]
+            L.reindex_server_release.restype = ci
+            L.reindex_server_drain.argtypes = [vp, ci]
+            L.reindex_server_drain.restype = ci
+            L.reindex_server_get_stats.argtypes = [vp, ctypes.POINTER(_ServerStats)]
+            L.reindex_server_get_stats.restype = ci
+            L.reindex_server_destroy.argtypes = [vp]
+            L.reindex_server_destroy.restype = None
+            L.reindex_debug_arena_check.argtypes = [ctypes.c_uint64, ci, ctypes.c_size_t]
+            L.reindex_debug_arena_check.restype = ci
             _lib = L
     return _lib
 
@@ -257,3 +297,87 @@ def profile_collect(max_records: int = 1 << 16):
         raise ReindexError(REINDEX_ERR_CUDA, "reindex_profile_collect")
     return [dict(kernel=r.kernel, name=KERNEL_NAMES[r.kernel], digit=r.digit, skipped=bool(r.skipped), ms=r.ms)
             for r in buf[: min(n, max_records)]]
+
+
+class _DeviceArray:
+    """A view of device memory owned by the server (exposes __cuda_array_interface__)."""
+
+    def __init__(self, ptr, shape, typestr, keep):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr or 0), False),
+                                         "version": 3, "strides": None}
+        self._keep = keep
+
+
+class Server:
+    """Request loop with continuous batching (reindex_server_* in the C ABI).
+
+    submit(vtx, idx) takes CUDA tensors that must stay alive and unchanged until the request
+    finishes; poll() returns finished requests as dicts with zero-copy torch views of the outputs
+    (valid until release(id))."""
+
+    def __init__(self, hbm_budget_bytes: int, max_batch_requests: int = 256, num_streams: int = 2, device: int = 0):
+        cfg = _ServerConfig(hbm_budget_bytes, max_batch_requests, num_streams, device)
+        h = ctypes.c_void_p()
+        rc = lib().reindex_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc:
+            raise ReindexError(rc, "reindex_server_create")
+        self._h = h
+        self._inputs = {}  # id -> (vtx, idx, stride, shape info) kept alive until finished
+
+    def submit(self, vtx, idx) -> int:
+        n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx)
+        req = _Request(_ptr(vtx), n_vtx, S, _ptr(idx), n_elem, k)
+        rid = ctypes.c_int64(-1)
+        rc = lib().reindex_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid))
+        if rc:
+            raise ReindexError(rc, "reindex_server_submit")
+        self._inputs[rid.value] = (vtx, idx, S, tuple(vtx.shape[1:]), vtx.dtype)
+        return rid.value
+
+    def poll(self, max_results: int = 1024, wait_ms: int = 0):
+        torch = _torch()
+        buf = (_Result * max_results)()
+        n = lib().reindex_server_poll(self._h, buf, max_results, wait_ms)
+        out = []
+        for r in buf[:max(n, 0)]:
+            vtx, idx, S, vshape, vdtype = self._inputs.pop(r.id)
+            res = dict(id=r.id, status=r.status, n_out=r.nVtxOut, submit_us=r.submit_us, start_us=r.start_us,
+                       done_us=r.done_us, out_vtx=None, out_idx=None)
+            if r.status == REINDEX_OK:
+                res["out_idx"] = torch.as_tensor(_DeviceArray(r.out_idx, tuple(idx.shape), "<i4", self),
+                                                 device=idx.device)
+                words = _DeviceArray(r.out_vtx if r.nVtxOut else 0, (r.nVtxOut, S // 4), "<i4", self)
+                res["out_vtx"] = torch.as_tensor(words, device=vtx.device)
+            out.append(res)
+        return out
+
+    def release(self, rid: int) -> None:
+        rc = lib().reindex_server_release(self._h, rid)
+        if rc:
+            raise ReindexError(rc, "reindex_server_release")
+
+    def drain(self, timeout_ms: int = 600_000) -> None:
+        rc = lib().reindex_server_drain(self._h, timeout_ms)
+        if rc:
+            raise ReindexError(rc, "reindex_server_drain")
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        lib().reindex_server_get_stats(self._h, ctypes.byref(st))
+        return {n: getattr(st, n) for n, _ in _ServerStats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().reindex_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def debug_arena_check(seed: int, ops: int, size: int) -> int:
+    """Host-only self-check of the server's arena allocator (0 = no inconsistency)."""
+    return int(lib().reindex_debug_arena_check(seed, ops, size))

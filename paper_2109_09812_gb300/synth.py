@@ -396,6 +396,46 @@ def tet_soup_gpu(L: int, unused_frac: float = 0.03, seed: int = 3, device="cuda"
     return vtx, idx
 
 
+def serving_requests(n: int, seed: int = 5, min_tris: int = 1000, max_tris: int = 4_000_000, tet_frac: float = 0.3,
+                     max_unused: float = 0.10):
+    """Request specs of the serving workload: element counts log-uniform in [min_tris, max_tris];
+    a fraction tet_frac are tet soups (16-byte vertices, 4 indices), the rest heightfield triangle
+    soups (12-byte vertices, 3 indices); unused fraction uniform in [0, max_unused); one seed each.
+    Returns a list of dicts(kind, size, unused, seed, n_elem)."""
+    r = np.arange(n, dtype=np.int64)
+    u_size = unit_float(hash_u64(seed, TAG_SIZES, 10, r)).astype(np.float64)
+    u_kind = unit_float(hash_u64(seed, TAG_SIZES, 11, r)).astype(np.float64)
+    u_unused = unit_float(hash_u64(seed, TAG_SIZES, 12, r)).astype(np.float64)
+    lo, hi = math.log(min_tris), math.log(max_tris)
+    out = []
+    for k in range(n):
+        t = int(round(math.exp(lo + (hi - lo) * u_size[k])))
+        if u_kind[k] < tet_frac:
+            L = max(1, int(round((t / 5.0) ** (1.0 / 3.0))))
+            out.append(dict(kind="tet", size=(L,), unused=float(max_unused * u_unused[k]), seed=seed * 1_000_000 + k,
+                            n_elem=5 * L ** 3))
+        else:
+            g = max(1, int(round(math.sqrt(t / 2.0))))
+            gy = max(1, -(-t // (2 * g)))
+            out.append(dict(kind="tri", size=(g, gy), unused=float(max_unused * u_unused[k]),
+                            seed=seed * 1_000_000 + k, n_elem=2 * g * gy))
+    return out
+
+
+def generate_request(spec: dict, device="cuda", host: bool = False, stream=None):
+    """The mesh of one serving request: on the device (torch tensors) or, with host=True, the
+    identical Mesh built on the host."""
+    if spec["kind"] == "tet":
+        (L,) = spec["size"]
+        if host:
+            return tet_soup(L, spec["unused"], spec["seed"])
+        return tet_soup_gpu(L, spec["unused"], spec["seed"], device=device, stream=stream)
+    g, gy = spec["size"]
+    if host:
+        return heightfield_soup(g, gy, spec["unused"], spec["seed"])
+    return heightfield_soup_gpu(g, gy, spec["unused"], spec["seed"], device=device, stream=stream)
+
+
 def config_mesh(cfg: int) -> Mesh:
     """The single-mesh workloads: 1 = 256^2 heightfield soup + 10% unused (seed 1);
     2 = 2048^2 heightfield soup + 5% unused (seed 2); 3 = 128^3 tet soup + 3% unused (seed 3)."""

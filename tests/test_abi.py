@@ -74,3 +74,10 @@ def test_host_side_argument_checks(L):
     assert L.reindex_mesh(z, 0, 12, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_INDEX_RANGE
     # workspace too small
     assert L.reindex_mesh_ws(fake, 10, 12, fake, 3, 3, fake, fake, fake, fake, 16, z) == rx.REINDEX_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("seed,size", [(1, 1 << 20), (2, 1 << 28), (3, 12345 * 256), (4, 256)])
+def test_server_arena_allocator_host_check(L, seed, size):
+    """The serving arena allocator (first fit, coalescing, 256-byte alignment) against a brute-force
+    model: no overlaps, no refusal while a large enough gap exists, full coalescing at the end."""
+    assert rx.debug_arena_check(seed, 5000, size) == 0
