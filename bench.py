@@ -160,6 +160,23 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value over all ranks (the slowest rank's time); no-op for one process."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Throughput of the whole job: every rank processed units_per_rank in at most `seconds`."""
+    return world * units_per_rank / seconds
+
+
 def oracle_rate(mesh, repeats=1):
     """Serial oracle (std::sort over (key, index) pairs) on the host: elements/s, seconds."""
     import oracle
@@ -498,11 +515,8 @@ def run_ours(args, world, rank, local):
     rx.profile_enable(False)
     ms = e0.elapsed_time(e1) / args.steps
     recs = rx.profile_collect()
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n_elem / (ms / 1e3)
+    ms = max_over_ranks(ms, world, dev)
+    value = whole_job_rate(n_elem, world, ms / 1e3)
 
     # ---- per-kernel breakdown and the dominant kernel's roofline
     per_kernel = {}
@@ -563,12 +577,8 @@ def run_e2e(rx, torch, mesh, world, dev, args):
     e2e_steps = max(3, min(args.steps, 10))
     for _ in range(e2e_steps):
         rv, _ = rx.reindex_mesh_host(hv, hi, ho_v, ho_i)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    return {"value": world * n_elem / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n_vtx * S + M * 4,
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
+    return {"value": whole_job_rate(n_elem, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": n_vtx * S + M * 4,
             "d2h_bytes_per_step": rv.shape[0] * S + M * 4 + 8, "ms_per_step": e2e_s * 1e3}
 
 

@@ -170,6 +170,36 @@ reindex_status reindex_meshes(const void* vtx, const int64_t* vtxOffsets, int vt
                               void* out_vtx, int64_t* out_vtxOffsets, int32_t* out_idx,
                               void* ws, size_t wsBytes, reindex_stream_t stream);
 
+/* ---- merging meshes (Section 3.2) ----------------------------------------------------------------
+ * Same inputs as reindex_meshes (concatenated meshes, mesh-local indices, device offsets), but ONE
+ * output mesh: the paper's merge -- concatenate the vertex arrays, offset each mesh's indices by
+ * the number of vertices before it, then remove duplicate and unused vertices ACROSS meshes.
+ * out_vtx / *out_nVtx / out_idx as for reindex_mesh over the concatenation (out_idx may alias
+ * idx); workspace of reindex_merge_workspace_size bytes, 256-byte aligned; no allocation, no
+ * synchronisation.  Device-detected errors: INDEX_RANGE (a local index outside its mesh),
+ * INVALID_ARG (bad offsets). */
+size_t reindex_merge_workspace_size(int nMeshes, int64_t nVtxTotal, int vtxStrideBytes, int64_t nElemTotal,
+                                    int idxPerElem);
+reindex_status reindex_merge_meshes(const void* vtx, const int64_t* vtxOffsets, int vtxStrideBytes,
+                                    const int32_t* idx, const int64_t* elemOffsets, int idxPerElem,
+                                    int nMeshes, int64_t nVtxTotal, int64_t nElemTotal,
+                                    void* out_vtx, int64_t* out_nVtx, int32_t* out_idx,
+                                    void* ws, size_t wsBytes, reindex_stream_t stream);
+
+/* ---- subset of a mesh (Section 3.4) -------------------------------------------------------------
+ * Keeps only the elements listed in elemList (device int32[nSel], each in [0, nElem); repeats
+ * allowed, order kept) with the FULL vertex array, and removes the vertices they do not use and
+ * the duplicates: out_idx (device int32[nSel * idxPerElem], must not alias idx) is the compact
+ * subset mesh's index array, out_vtx its vertices (room for min(nVtx, nSel*idxPerElem)).
+ * Workspace of reindex_submesh_workspace_size bytes.  Device-detected errors: INDEX_RANGE (a list
+ * entry outside [0, nElem) or an index outside [0, nVtx)). */
+size_t reindex_submesh_workspace_size(int64_t nVtx, int vtxStrideBytes, int64_t nSel, int idxPerElem);
+reindex_status reindex_submesh(const void* vtx, int64_t nVtx, int vtxStrideBytes,
+                               const int32_t* idx, int64_t nElem, int idxPerElem,
+                               const int32_t* elemList, int64_t nSel,
+                               void* out_vtx, int64_t* out_nVtx, int32_t* out_idx,
+                               void* ws, size_t wsBytes, reindex_stream_t stream);
+
 /* ---- serving: a request loop with continuous batching ------------------------------------------
  * A server owns one arena of device memory (the HBM budget) and a scheduler thread.  Clients
  * submit requests (device-resident meshes, which must stay valid and unchanged until the request

@@ -38,7 +38,9 @@ EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "
             "reindex_mesh_host", "reindex_stream_status", "reindex_profile_enable", "reindex_profile_collect",
             "reindex_kernel_name", "reindex_mesh_noalloc", "reindex_meshes", "reindex_meshes_workspace_size",
             "reindex_server_create", "reindex_server_submit", "reindex_server_poll", "reindex_server_release",
-            "reindex_server_drain", "reindex_server_get_stats", "reindex_server_destroy", "reindex_debug_arena_check"]
+            "reindex_server_drain", "reindex_server_get_stats", "reindex_server_destroy", "reindex_debug_arena_check",
+            "reindex_merge_workspace_size", "reindex_merge_meshes", "reindex_submesh_workspace_size",
+            "reindex_submesh"]
 
 _lock = threading.Lock()
 _lib = None
@@ -123,6 +125,14 @@ def lib() -> ctypes.CDLL:
             L.reindex_server_get_stats.restype = ci
             L.reindex_server_destroy.argtypes = [vp]
             L.reindex_server_destroy.restype = None
+            L.reindex_merge_workspace_size.argtypes = [ci, i64, ci, i64, ci]
+            L.reindex_merge_workspace_size.restype = ctypes.c_size_t
+            L.reindex_merge_meshes.argtypes = [vp, vp, ci, vp, vp, ci, ci, i64, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]
+            L.reindex_merge_meshes.restype = ci
+            L.reindex_submesh_workspace_size.argtypes = [i64, ci, i64, ci]
+            L.reindex_submesh_workspace_size.restype = ctypes.c_size_t
+            L.reindex_submesh.argtypes = [vp, i64, ci, vp, i64, ci, vp, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]
+            L.reindex_submesh.restype = ci
             L.reindex_debug_arena_check.argtypes = [ctypes.c_uint64, ci, ctypes.c_size_t]
             L.reindex_debug_arena_check.restype = ci
             _lib = L
@@ -269,6 +279,55 @@ def reindex_meshes(vtx, vtx_offsets, idx, elem_offsets, ws=None, out_vtx=None, o
     if rc:
         raise ReindexError(rc, "reindex_meshes")
     return out_vtx, out_offsets, out_idx
+
+
+def reindex_merge_meshes(vtx, vtx_offsets, idx, elem_offsets, ws=None, out_vtx=None, out_nVtx=None, out_idx=None,
+                         stream=None):
+    """Merge meshes (Section 3.2): one output mesh, duplicates removed across meshes.  Inputs as for
+    reindex_meshes; returns (out_vtx, out_nVtx, out_idx) as reindex_mesh does."""
+    torch = _torch()
+    n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx)
+    n_meshes = int(vtx_offsets.numel()) - 1
+    if ws is None:
+        ws = torch.empty(max(1, int(lib().reindex_merge_workspace_size(n_meshes, n_vtx, S, n_elem, k))),
+                         dtype=torch.uint8, device=vtx.device)
+    if out_vtx is None:
+        out_vtx = torch.empty((min(n_vtx, n_elem * k),) + tuple(vtx.shape[1:]), dtype=vtx.dtype, device=vtx.device)
+    if out_nVtx is None:
+        out_nVtx = torch.empty(1, dtype=torch.int64, device=vtx.device)
+    if out_idx is None:
+        out_idx = torch.empty_like(idx)
+    rc = lib().reindex_merge_meshes(_ptr(vtx), _ptr(vtx_offsets), S, _ptr(idx), _ptr(elem_offsets), k, n_meshes,
+                                    n_vtx, n_elem, _ptr(out_vtx), _ptr(out_nVtx), _ptr(out_idx), _ptr(ws),
+                                    ws.numel() * ws.element_size(), _stream_handle(stream))
+    if rc:
+        raise ReindexError(rc, "reindex_merge_meshes")
+    return out_vtx, out_nVtx, out_idx
+
+
+def reindex_submesh(vtx, idx, elem_list, ws=None, out_vtx=None, out_nVtx=None, out_idx=None, stream=None):
+    """Subset of a mesh (Section 3.4): the elements listed in elem_list (CUDA int32) with the full
+    vertex array, compacted.  Returns (out_vtx, out_nVtx, out_idx) with out_idx (nSel, k)."""
+    torch = _torch()
+    n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx)
+    n_sel = int(elem_list.numel())
+    if elem_list.dtype != torch.int32 or not elem_list.is_contiguous():
+        raise ValueError("elem_list must be a contiguous int32 tensor")
+    if ws is None:
+        ws = torch.empty(max(1, int(lib().reindex_submesh_workspace_size(n_vtx, S, n_sel, k))), dtype=torch.uint8,
+                         device=vtx.device)
+    if out_vtx is None:
+        out_vtx = torch.empty((min(n_vtx, n_sel * k),) + tuple(vtx.shape[1:]), dtype=vtx.dtype, device=vtx.device)
+    if out_nVtx is None:
+        out_nVtx = torch.empty(1, dtype=torch.int64, device=vtx.device)
+    if out_idx is None:
+        out_idx = torch.empty((n_sel, k), dtype=torch.int32, device=vtx.device)
+    rc = lib().reindex_submesh(_ptr(vtx), n_vtx, S, _ptr(idx), n_elem, k, _ptr(elem_list), n_sel, _ptr(out_vtx),
+                               _ptr(out_nVtx), _ptr(out_idx), _ptr(ws), ws.numel() * ws.element_size(),
+                               _stream_handle(stream))
+    if rc:
+        raise ReindexError(rc, "reindex_submesh")
+    return out_vtx, out_nVtx, out_idx
 
 
 def reindex_stream_status(stream=None) -> int:

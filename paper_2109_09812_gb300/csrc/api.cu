@@ -3,6 +3,7 @@
 // sticky error query and the per-launch timing facility.
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -136,17 +137,28 @@ static reindex_status check_ptrs(const void* vtx, int64_t nVtx, int S, const int
   return REINDEX_OK;
 }
 
+// Optional steps around the single-mesh sequence: `pre` runs right after the workspace is
+// cleared (it may record device errors), and with `flags_done` it has already set the used bits.
+struct PipeExtras {
+  std::function<cudaError_t(const WsPtrs&, const LaunchCfg&)> pre;
+  bool flags_done = false;
+};
+
 // The launch sequence (all on `st`, no host synchronisation).
 static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t M,
                                    void* out_vtx, int64_t* out_nVtx, int32_t* out_idx, void* ws,
-                                   const WsLayout& L, cudaStream_t st) {
+                                   const WsLayout& L, cudaStream_t st, const PipeExtras* extra = nullptr) {
   const LaunchCfg& c = launch_cfg(S);
   const WsPtrs p = ws_ptrs(ws, L);
   {
     prof::Scope s(REINDEX_K_CLEAR, -1, st);
     REINDEX_TRY(launch_clear(ws, L.zero_bytes, c, st));
   }
-  {
+  if (extra && extra->pre) {
+    prof::Scope s(extra->flags_done ? REINDEX_K_USED_FLAGS : REINDEX_K_SEG_PREPARE, -1, st);
+    REINDEX_TRY(extra->pre(p, c));
+  }
+  if (!(extra && extra->flags_done)) {
     prof::Scope s(REINDEX_K_USED_FLAGS, -1, st);
     REINDEX_TRY(launch_used_flags(idx, M, nVtx, p, c, st));
   }
@@ -423,6 +435,102 @@ reindex_status reindex_meshes(const void* vtx, const int64_t* vtxOffsets, int vt
   if (ws == nullptr || !aligned(ws, 256) || wsBytes < SL.total) return REINDEX_ERR_INVALID_ARG;
   return run_batched(vtx, nVtxTotal, S, idx, M, idxPerElem, vtxOffsets, elemOffsets, nMeshes, out_vtx,
                      out_vtxOffsets, out_idx, ws, SL, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---- mesh merging (Section 3.2) --------------------------------------------------------------
+// Workspace: the single-mesh layout over the concatenation, the two lookup tables of the batched
+// path, and nMeshes+1 offsets of scratch.
+struct MergeLayout {
+  WsLayout L;
+  size_t off_blkV = 0, off_blkI = 0, off_scratch = 0, total = 0;
+  void compute(int64_t n, int s, int64_t m, int nMeshes) {
+    L.compute(n, s, m);
+    size_t o = L.total;
+    off_blkV = o;
+    o = align_up(o + (size_t)((n + kSegBlock - 1) / kSegBlock + 1) * 4, 256);
+    off_blkI = o;
+    o = align_up(o + (size_t)((m + kSegBlock - 1) / kSegBlock + 1) * 4, 256);
+    off_scratch = o;
+    o = align_up(o + (size_t)(nMeshes + 1) * 8, 256);
+    total = o;
+  }
+};
+
+size_t reindex_merge_workspace_size(int nMeshes, int64_t nVtxTotal, int vtxStrideBytes, int64_t nElemTotal,
+                                    int idxPerElem) {
+  int64_t M = 0;
+  if (nMeshes < 1 || check_args(nVtxTotal, vtxStrideBytes, nElemTotal, idxPerElem, &M) != REINDEX_OK) return 0;
+  MergeLayout ML;
+  ML.compute(nVtxTotal, vtxStrideBytes, M, nMeshes);
+  return ML.total;
+}
+
+reindex_status reindex_merge_meshes(const void* vtx, const int64_t* vtxOffsets, int S, const int32_t* idx,
+                                    const int64_t* elemOffsets, int k, int nMeshes, int64_t nVtxTotal,
+                                    int64_t nElemTotal, void* out_vtx, int64_t* out_nVtx, int32_t* out_idx, void* ws,
+                                    size_t wsBytes, reindex_stream_t stream) {
+  int64_t M = 0;
+  reindex_status r = check_args(nVtxTotal, S, nElemTotal, k, &M);
+  if (r != REINDEX_OK) return r;
+  if (nMeshes < 1 || !vtxOffsets || !elemOffsets || !aligned(vtxOffsets, 8) || !aligned(elemOffsets, 8))
+    return REINDEX_ERR_INVALID_ARG;
+  if ((r = check_ptrs(vtx, nVtxTotal, S, idx, M, out_vtx, out_nVtx, out_idx)) != REINDEX_OK) return r;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (M == 0) return cuda_status(launch_set_count(out_nVtx, 0, st));
+  if (nVtxTotal == 0) return REINDEX_ERR_INDEX_RANGE;
+  MergeLayout ML;
+  ML.compute(nVtxTotal, S, M, nMeshes);
+  if (ws == nullptr || !aligned(ws, 256) || wsBytes < ML.total) return REINDEX_ERR_INVALID_ARG;
+  unsigned char* b = static_cast<unsigned char*>(ws);
+  SegArgs seg;
+  seg.vtxOff = vtxOffsets;
+  seg.elemOff = elemOffsets;
+  seg.outOff = reinterpret_cast<int64_t*>(b + ML.off_scratch);
+  seg.blkV = reinterpret_cast<const uint32_t*>(b + ML.off_blkV);
+  seg.blkI = reinterpret_cast<const uint32_t*>(b + ML.off_blkI);
+  seg.nMeshes = nMeshes;
+  seg.k = k;
+  PipeExtras ex;
+  ex.flags_done = true;  // the concatenation step marks the used vertices itself
+  ex.pre = [&](const WsPtrs& p, const LaunchCfg& c) -> cudaError_t {
+    // concatenate: local -> global indices (offset by the mesh's first vertex), range-checked
+    cudaError_t e = launch_seg_prepare(seg, nVtxTotal, M, reinterpret_cast<uint32_t*>(b + ML.off_blkV),
+                                       reinterpret_cast<uint32_t*>(b + ML.off_blkI), p.ctrl, c, st);
+    if (e != cudaSuccess) return e;
+    return launch_seg_flags(idx, out_idx, M, seg, p, c, st);
+  };
+  // Then the single-mesh method over the concatenation, reading the global indices in out_idx.
+  return run_pipeline(vtx, nVtxTotal, S, out_idx, M, out_vtx, out_nVtx, out_idx, ws, ML.L, st, &ex);
+}
+
+// ---- subset of a mesh (Section 3.4) ---------------------------------------------------------------
+size_t reindex_submesh_workspace_size(int64_t nVtx, int vtxStrideBytes, int64_t nSel, int idxPerElem) {
+  return reindex_workspace_size(nVtx, vtxStrideBytes, nSel, idxPerElem);
+}
+
+reindex_status reindex_submesh(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t nElem, int k,
+                               const int32_t* elemList, int64_t nSel, void* out_vtx, int64_t* out_nVtx,
+                               int32_t* out_idx, void* ws, size_t wsBytes, reindex_stream_t stream) {
+  int64_t M = 0, Mall = 0;
+  reindex_status r = check_args(nVtx, S, nSel, k, &M);
+  if (r != REINDEX_OK) return r;
+  if ((r = check_args(nVtx, S, nElem, k, &Mall)) != REINDEX_OK) return r;
+  if (nSel > 0 && (!elemList || !aligned(elemList, 4) || !idx)) return REINDEX_ERR_INVALID_ARG;
+  if ((r = check_ptrs(vtx, nVtx, S, out_idx, M, out_vtx, out_nVtx, out_idx)) != REINDEX_OK) return r;
+  if (out_idx == idx) return REINDEX_ERR_INVALID_ARG;  // the selection is gathered into out_idx first
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (M == 0) return cuda_status(launch_set_count(out_nVtx, 0, st));
+  if (nVtx == 0) return REINDEX_ERR_INDEX_RANGE;
+  WsLayout L;
+  L.compute(nVtx, S, M);
+  if (ws == nullptr || !aligned(ws, 256) || wsBytes < L.total) return REINDEX_ERR_INVALID_ARG;
+  PipeExtras ex;
+  ex.pre = [&](const WsPtrs& p, const LaunchCfg& c) -> cudaError_t {
+    return launch_gather_elements(idx, k, nElem, elemList, nSel, out_idx, p, c, st);
+  };
+  // The selected elements, with the full vertex array, go through the method unchanged: the
+  // vertices no selected element uses drop out as unused ones.
+  return run_pipeline(vtx, nVtx, S, out_idx, M, out_vtx, out_nVtx, out_idx, ws, L, st, &ex);
 }
 
 reindex_status reindex_stream_status(reindex_stream_t stream) {

@@ -47,6 +47,8 @@ cudaError_t launch_seg_remap(int32_t* out_idx, int64_t M, const SegArgs& seg, Ws
 cudaError_t launch_remap(const int32_t* idx, int32_t* out_idx, int64_t M, WsPtrs ws, const LaunchCfg& c,
                          cudaStream_t st);
 cudaError_t launch_finalize(WsPtrs ws, int64_t* out_nVtx, cudaStream_t st);
+cudaError_t launch_gather_elements(const int32_t* idx, int k, int64_t nElem, const int32_t* list, int64_t nSel,
+                                  int32_t* out, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_set_count(int64_t* out_nVtx, int64_t value, cudaStream_t st);
 
 // Occupancy queries for the persistent kernels (per template instantiation).

@@ -136,6 +136,25 @@ __global__ void __launch_bounds__(kThreads) k_remap(const int32_t* idx, int32_t*
   for (int64_t i = done + t0; i < M; i += stride) out[i] = (int32_t)__ldg(o2n + idx[i]);
 }
 
+// Subset of a mesh (Section 3.4): out[s*k + q] = idx[list[s]*k + q] for the selected elements.
+__global__ void __launch_bounds__(kThreads) k_gather_elements(const int32_t* idx, int k, int64_t nElem,
+                                                               const int32_t* list, int64_t nSel, int32_t* out,
+                                                               Control* ctrl) {
+  bool bad = false;
+  const int64_t n = nSel * k;
+  for (int64_t j = blockIdx.x * (int64_t)kThreads + threadIdx.x; j < n; j += (int64_t)gridDim.x * kThreads) {
+    const int64_t s = j / k;
+    const int32_t e = __ldg(list + s);
+    if (e < 0 || (int64_t)e >= nElem) {
+      bad = true;
+      out[j] = 0;
+    } else {
+      out[j] = __ldg(idx + (int64_t)e * k + (j - s * k));
+    }
+  }
+  if (bad) record_error(ctrl, kErrIndexRange);
+}
+
 __global__ void k_finalize(Control* ctrl, int64_t* out_nVtx) {
   const uint32_t e = ctrl->err;
   if (e) {
@@ -188,6 +207,13 @@ cudaError_t launch_remap(const int32_t* idx, int32_t* out_idx, int64_t M, WsPtrs
     k_remap<true><<<g, kThreads, 0, st>>>(idx, out_idx, M, ws.old2new, ws.ctrl);
   else
     k_remap<false><<<g, kThreads, 0, st>>>(idx, out_idx, M, ws.old2new, ws.ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_elements(const int32_t* idx, int k, int64_t nElem, const int32_t* list, int64_t nSel,
+                                  int32_t* out, WsPtrs ws, const LaunchCfg& c, cudaStream_t st) {
+  if (nSel == 0) return cudaSuccess;
+  k_gather_elements<<<grid_for(nSel * k, c, 8), kThreads, 0, st>>>(idx, k, nElem, list, nSel, out, ws.ctrl);
   return cudaGetLastError();
 }
 

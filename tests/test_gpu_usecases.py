@@ -1,0 +1,93 @@
+"""The paper's use cases beyond plain duplicate removal (Section 3): merging meshes that share
+vertices (3.2) and extracting a subset of a mesh's elements (3.4), each checked bit for bit
+against the oracle applied to the construction the paper describes."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_09812_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2109_09812_gb300 import build
+
+    build.build()
+    import paper_2109_09812_gb300 as rx
+
+    return rx
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("S", [4, 8, 12, 16, 20])
+def test_merge_equals_concatenate_offset_dedup(rx, S):
+    """Section 3.2: concatenate the vertex arrays, add each mesh's vertex offset to its indices,
+    then remove duplicates -- here across meshes."""
+    rng = np.random.default_rng(S)
+    K = S // 4
+    pool = rng.integers(0, 2**32, size=(300, K), dtype=np.uint64).astype(np.uint32)  # shared vertices
+    meshes = []
+    for m in range(9):
+        nv = int(rng.integers(1, 2500))
+        ne = 0 if m == 4 else int(rng.integers(1, 1500))
+        vtx = pool[rng.integers(0, pool.shape[0], size=nv)]
+        meshes.append((vtx, rng.integers(0, nv, size=(ne, 3)).astype(np.int32)))
+    vtx = np.concatenate([m[0] for m in meshes])
+    idx_local = np.concatenate([m[1] for m in meshes])
+    voff = np.concatenate([[0], np.cumsum([m[0].shape[0] for m in meshes])]).astype(np.int64)
+    eoff = np.concatenate([[0], np.cumsum([m[1].shape[0] for m in meshes])]).astype(np.int64)
+    idx_global = np.concatenate([m[1] + voff[j] for j, m in enumerate(meshes)]).astype(np.int32)
+    ov, oi = oracle.reindex_sort(vtx, idx_global)
+    out_v, out_n, out_i = rx.reindex_merge_meshes(dev(vtx.view(np.int32)), dev(voff), dev(idx_local), dev(eoff))
+    torch.cuda.synchronize()
+    D = int(out_n.item())
+    assert D == ov.shape[0] and D <= 300
+    np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+
+
+def test_merge_of_identical_meshes_is_one_mesh(rx):
+    m = synth.heightfield_soup(30, 20, 0.1, seed=4)
+    vtx = np.concatenate([m.vtx] * 3)
+    idx = np.concatenate([m.idx] * 3)
+    voff = np.array([0, m.n_vtx, 2 * m.n_vtx, 3 * m.n_vtx], np.int64)
+    eoff = np.array([0, m.n_elem, 2 * m.n_elem, 3 * m.n_elem], np.int64)
+    out_v, out_n, out_i = rx.reindex_merge_meshes(dev(vtx.view(np.int32)), dev(voff), dev(idx), dev(eoff))
+    torch.cuda.synchronize()
+    assert int(out_n.item()) == 31 * 21
+    single_v, single_i = oracle.reindex_sort(m.vtx, m.idx)
+    np.testing.assert_array_equal(out_i.cpu().numpy(), np.concatenate([single_i.reshape(-1, 3)] * 3))
+
+
+@pytest.mark.parametrize("keep", [0.0, 0.01, 0.3, 1.0])
+def test_submesh_equals_copy_of_selected_elements(rx, keep):
+    """Section 3.4: a mesh with the full vertex array but only the selected elements, re-indexed."""
+    m = synth.heightfield_soup(80, 70, 0.05, seed=8)
+    rng = np.random.default_rng(int(keep * 100))
+    sel = np.flatnonzero(rng.random(m.n_elem) < keep).astype(np.int32)
+    if keep == 1.0:
+        sel = np.concatenate([sel, sel[:17]])  # repeats are allowed and kept
+    ov, oi = oracle.reindex_sort(m.vtx, m.idx[sel])
+    out_v, out_n, out_i = rx.reindex_submesh(dev(m.vtx.view(np.int32)), dev(m.idx), dev(sel))
+    torch.cuda.synchronize()
+    D = int(out_n.item())
+    assert D == ov.shape[0]
+    np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+
+
+def test_submesh_bad_element_id(rx):
+    m = synth.heightfield_soup(10, 10, 0.0, seed=2)
+    sel = np.array([0, 5, m.n_elem], np.int32)
+    rx.reindex_stream_status()
+    out_v, out_n, out_i = rx.reindex_submesh(dev(m.vtx.view(np.int32)), dev(m.idx), dev(sel))
+    assert rx.reindex_stream_status() == rx.REINDEX_ERR_INDEX_RANGE
+    assert int(out_n.item()) == -rx.REINDEX_ERR_INDEX_RANGE
