@@ -47,11 +47,21 @@ WORKLOADS = {
                      "[1e3, 4e6] (70% heightfield triangle soups, float32 xyz, 3 idx; 30% tet soups, 16-B vertices, "
                      "4 idx), 0-10% unused, generated on the device just before arrival, admitted against a 40 GB "
                      "HBM budget and coalesced into reindex_meshes batches on 2 streams", 5),
+    # The paper's own evaluation workload (Section 3.5, Table 1): n x n quads, float2 vertices,
+    # 4 corners + 1 unused centre per quad; its GPU times (RTX 3090, thrust + CUDA) are context.
+    "quadgrid1024": ("quad grid 1024x1024 (Table 1 workload: 1,048,576 quads, float2 vertices, 5 per quad, "
+                     "every fifth unused), int32 idx x4", ("quad", 1024)),
+    "quadgrid4096": ("quad grid 4096x4096 (Table 1 workload: 16,777,216 quads, float2 vertices, 5 per quad, "
+                     "every fifth unused), int32 idx x4", ("quad", 4096)),
+    "quadgrid8192": ("quad grid 8192x8192 (Table 1 workload: 67,108,864 quads, float2 vertices, 5 per quad, "
+                     "every fifth unused), int32 idx x4", ("quad", 8192)),
     # a half-size case of the 2048^2 workload, for profiler captures (still larger than L2)
     "heightfield1448": ("heightfield triangle soup 1448x1448 cells (4,193,408 tris, 12,580,224 soup vertices "
                         "float32 xyz + 5% unused, permuted), int32 idx x3, seed 2", (1448, 0.05, 2)),
 }
 METRIC = "input elements re-indexed/sec"
+# The paper's GPU times for its quad-grid workload (Table 1), as elements (quads) per second.
+PAPER_RATE = {"quadgrid1024": 1048576 / 9.2e-3, "quadgrid4096": 16777216 / 92e-3, "quadgrid8192": 67108864 / 338e-3}
 UNIT = "elements/s"
 
 
@@ -200,6 +210,13 @@ def run_reference(args, world, rank):
         meshes = synth.batched_heightfield(64, seed=4)
         sample = synth.Mesh(vtx=None, idx=None)
         sample_desc = "the first 64 meshes of the 4096-mesh batch (same sizes and seeds), one oracle call each"
+    elif isinstance(cfg, tuple) and cfg[0] == "quad":
+        qn = min(cfg[1], 1024)
+        sample = synth.quad_grid(qn)
+        sample_desc = f"quad grid {qn}x{qn}, the same construction ({qn * qn:,} quads)"
+    elif isinstance(cfg, tuple):
+        sample = synth.heightfield_soup(min(cfg[0], 1024), min(cfg[0], 1024), cfg[1], cfg[2])
+        sample_desc = f"heightfield soup {min(cfg[0], 1024)}^2 cells, same construction"
     elif cfg == 3:
         sample = synth.tet_soup(48, 0.03, 3)
         sample_desc = "tetrahedral soup 48^3 cells x 5 tets, same construction (552,960 tets)"
@@ -464,6 +481,19 @@ def run_serving_bench(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def build_mesh(workload):
+    """(mesh, mesh the CPU baseline times) of a single-mesh workload."""
+    from paper_2109_09812_gb300 import synth
+
+    cfg = WORKLOADS[workload][1]
+    if isinstance(cfg, tuple) and cfg[0] == "quad":
+        # the oracle on 268M used vertices would take minutes: time it on the 2048^2 grid
+        return synth.quad_grid(cfg[1]), (synth.quad_grid(min(cfg[1], 2048)) if cfg[1] > 2048 else None)
+    if isinstance(cfg, tuple):
+        return synth.heightfield_soup(cfg[0], cfg[0], cfg[1], cfg[2]), None
+    return synth.config_mesh(cfg), None
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -477,8 +507,7 @@ def run_ours(args, world, rank, local):
         torch.distributed.barrier()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    cfg = WORKLOADS[args.workload][1]
-    mesh = synth.heightfield_soup(cfg[0], cfg[0], cfg[1], cfg[2]) if isinstance(cfg, tuple) else synth.config_mesh(cfg)
+    mesh, cpu_sample = build_mesh(args.workload)
     S, k, n_vtx, n_elem = mesh.stride_bytes, mesh.idx_per_elem, mesh.n_vtx, mesh.n_elem
     M = n_elem * k
     U = M  # soups: every soup vertex is referenced exactly once
@@ -490,6 +519,7 @@ def run_ours(args, world, rank, local):
     out_i = torch.empty_like(idx)
     stream = torch.cuda.current_stream(dev)
 
+    tuning = rx.reindex_autotune(vtx, idx, ws, reps=5) if not args.no_autotune else rx.reindex_tuning_get(S)
     for _ in range(max(args.warmup, 1)):
         rx.reindex_mesh_ws(vtx, idx, ws, out_v, out_n, out_i)
     torch.cuda.synchronize(dev)
@@ -544,17 +574,20 @@ def run_ours(args, world, rank, local):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        rate, secs = oracle_rate(mesh)
+        rate, secs = oracle_rate(cpu_sample if cpu_sample is not None else mesh)
+        what = (f"the same construction at {cpu_sample.name} ({cpu_sample.n_elem:,} elements)" if cpu_sample is not None
+                else "the full workload once")
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"the full workload once ({secs:.1f} s), serial std::sort oracle, one thread"}
+               "sample": f"{what} ({secs:.1f} s), serial std::sort oracle, one thread"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic",
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": (value / PAPER_RATE[args.workload]) if args.workload in PAPER_RATE else None,
+        "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][0], "n_vtx": n_vtx, "n_elem": n_elem, "stride_bytes": S,
                    "idx_per_elem": k, "unique_out": D, "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 ({(n_vtx * S + M * 4) / 1e6:.0f} MB read per step)"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "tuning": tuning,
         "gpu_launches": len(recs),
         "kernels": {k_: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k_, v in sorted(per_kernel.items())},
         "clocks": clocks.summary(),
@@ -591,6 +624,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="heightfield2048")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--requests", type=int, default=20000, help="serving workload: number of requests")
     ap.add_argument("--loads", default="0.5,0.7,0.9", help="serving workload: offered loads (fractions of capacity)")
     args = ap.parse_args()

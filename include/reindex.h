@@ -265,6 +265,26 @@ int reindex_debug_arena_check(uint64_t seed, int ops, size_t size);
  * returned as REINDEX_ERR_CUDA. */
 reindex_status reindex_stream_status(reindex_stream_t stream);
 
+/* ---- autotuning ---------------------------------------------------------------------------------
+ * The library has several kernel variants with identical results: the radix pass (register-tiled
+ * with 4096-item tiles, or pipelined through shared memory by the Tensor Memory Accelerator with
+ * 2048-4096-item tiles), the digit matching inside a warp (8 ballots or match.any), the compaction
+ * histogram method (warp-uniform check, peel, or match.any) and the grid shape (persistent CTAs or
+ * one CTA per tile).  reindex_autotune times them on the caller's mesh with whole reindex_mesh_ws
+ * runs (coordinate descent, median of `reps` runs each; BLOCKING: it synchronises `stream`) and
+ * keeps the fastest for this device and stride, for every later call of this process; if the
+ * environment variable REINDEX_TUNE_CACHE names a file, the choice is appended to it and read back
+ * by later processes.  out_idx must not alias idx.  desc (optional) receives the chosen
+ * configuration, e.g. "sort=regs,rank=ballot,hist=uniform,grid=persist". */
+reindex_status reindex_autotune(const void* vtx, int64_t nVtx, int vtxStrideBytes,
+                                const int32_t* idx, int64_t nElem, int idxPerElem,
+                                void* out_vtx, int64_t* out_nVtx, int32_t* out_idx,
+                                void* ws, size_t wsBytes, int reps, reindex_stream_t stream,
+                                char* desc, int descLen);
+/* The configuration in force for this device and stride (as above), or set one explicitly. */
+reindex_status reindex_tuning_get(int vtxStrideBytes, char* desc, int descLen);
+reindex_status reindex_tuning_set(int vtxStrideBytes, const char* spec);
+
 /* ---- per-kernel timing (measurement support) ------------------------------------------------
  * While enabled, every pipeline kernel launch made by this process is bracketed by a pair of
  * CUDA events recorded on its stream.  reindex_profile_collect() synchronises those events and

@@ -40,7 +40,7 @@ EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "
             "reindex_server_create", "reindex_server_submit", "reindex_server_poll", "reindex_server_release",
             "reindex_server_drain", "reindex_server_get_stats", "reindex_server_destroy", "reindex_debug_arena_check",
             "reindex_merge_workspace_size", "reindex_merge_meshes", "reindex_submesh_workspace_size",
-            "reindex_submesh"]
+            "reindex_submesh", "reindex_autotune", "reindex_tuning_get", "reindex_tuning_set"]
 
 _lock = threading.Lock()
 _lib = None
@@ -133,6 +133,13 @@ def lib() -> ctypes.CDLL:
             L.reindex_submesh_workspace_size.restype = ctypes.c_size_t
             L.reindex_submesh.argtypes = [vp, i64, ci, vp, i64, ci, vp, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]
             L.reindex_submesh.restype = ci
+            L.reindex_autotune.argtypes = [vp, i64, ci, vp, i64, ci, vp, vp, vp, vp, ctypes.c_size_t, ci, vp,
+                                           ctypes.c_char_p, ci]
+            L.reindex_autotune.restype = ci
+            L.reindex_tuning_get.argtypes = [ci, ctypes.c_char_p, ci]
+            L.reindex_tuning_get.restype = ci
+            L.reindex_tuning_set.argtypes = [ci, ctypes.c_char_p]
+            L.reindex_tuning_set.restype = ci
             L.reindex_debug_arena_check.argtypes = [ctypes.c_uint64, ci, ctypes.c_size_t]
             L.reindex_debug_arena_check.restype = ci
             _lib = L
@@ -328,6 +335,36 @@ def reindex_submesh(vtx, idx, elem_list, ws=None, out_vtx=None, out_nVtx=None, o
     if rc:
         raise ReindexError(rc, "reindex_submesh")
     return out_vtx, out_nVtx, out_idx
+
+
+def reindex_autotune(vtx, idx, ws=None, reps: int = 3, stream=None) -> str:
+    """Time the kernel variants on this mesh and keep the fastest for its stride (blocking).
+    Returns the chosen configuration."""
+    torch = _torch()
+    n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx)
+    if ws is None:
+        ws = torch.empty(max(1, reindex_workspace_size(n_vtx, S, n_elem, k)), dtype=torch.uint8, device=vtx.device)
+    out_vtx = torch.empty((min(n_vtx, n_elem * k),) + tuple(vtx.shape[1:]), dtype=vtx.dtype, device=vtx.device)
+    out_n = torch.empty(1, dtype=torch.int64, device=vtx.device)
+    out_idx = torch.empty_like(idx)
+    buf = ctypes.create_string_buffer(128)
+    rc = lib().reindex_autotune(_ptr(vtx), n_vtx, S, _ptr(idx), n_elem, k, _ptr(out_vtx), _ptr(out_n), _ptr(out_idx),
+                                _ptr(ws), ws.numel() * ws.element_size(), reps, _stream_handle(stream), buf, 128)
+    if rc:
+        raise ReindexError(rc, "reindex_autotune")
+    return buf.value.decode()
+
+
+def reindex_tuning_get(stride_bytes: int) -> str:
+    buf = ctypes.create_string_buffer(128)
+    lib().reindex_tuning_get(stride_bytes, buf, 128)
+    return buf.value.decode()
+
+
+def reindex_tuning_set(stride_bytes: int, spec: str) -> None:
+    rc = lib().reindex_tuning_set(stride_bytes, spec.encode())
+    if rc:
+        raise ReindexError(rc, "reindex_tuning_set")
 
 
 def reindex_stream_status(stream=None) -> int:

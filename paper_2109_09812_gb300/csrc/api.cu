@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <string>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -16,14 +17,37 @@ namespace reindex {
 
 // ---------------------------------------------------------------------------------------------
 // Per-device launch configuration.
-const LaunchCfg& launch_cfg(int S) {
-  static std::mutex mu;
-  static std::map<std::pair<int, int>, LaunchCfg> cache;
+static std::mutex g_cfg_mu;
+static std::map<std::pair<int, int>, LaunchCfg> g_cfg;
+
+// Applies "sort=regs|pipe,rank=ballot|match,hist=uniform|peel|match,grid=persist|tile" (any
+// subset, in any order).  Every variant computes the same result.
+void apply_tuning(LaunchCfg& c, const char* spec) {
+  if (!spec) return;
+  if (std::strstr(spec, "grid=tile")) c.grid_per_tile = 1;
+  if (std::strstr(spec, "grid=persist")) c.grid_per_tile = 0;
+  if (std::strstr(spec, "sort=regs")) c.sort_kernel = kSortRegs;
+  if (std::strstr(spec, "sort=pipe") && c.occ_sort_pipe > 0) c.sort_kernel = kSortPipe;
+  if (std::strstr(spec, "rank=match")) c.rank_mode = kRankMatchAny;
+  if (std::strstr(spec, "rank=ballot")) c.rank_mode = kRankBallot;
+  if (std::strstr(spec, "hist=uniform")) c.hist_mode = kHistUniform;
+  if (std::strstr(spec, "hist=peel")) c.hist_mode = kHistPeel;
+  if (std::strstr(spec, "hist=match")) c.hist_mode = kHistMatchAny;
+}
+
+std::string describe_tuning(const LaunchCfg& c) {
+  std::string d = c.sort_kernel == kSortPipe ? "sort=pipe" : "sort=regs";
+  d += c.rank_mode == kRankMatchAny ? ",rank=match" : ",rank=ballot";
+  d += c.hist_mode == kHistMatchAny ? ",hist=match" : (c.hist_mode == kHistPeel ? ",hist=peel" : ",hist=uniform");
+  d += c.grid_per_tile ? ",grid=tile" : ",grid=persist";
+  return d;
+}
+
+static LaunchCfg& launch_cfg_locked(int S) {
   int dev = 0;
   cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> g(mu);
-  auto it = cache.find({dev, S});
-  if (it != cache.end()) return it->second;
+  auto it = g_cfg.find({dev, S});
+  if (it != g_cfg.end()) return it->second;
   LaunchCfg c;
   cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
   if (c.sms < 1) c.sms = 1;
@@ -32,20 +56,21 @@ const LaunchCfg& launch_cfg(int S) {
   c.occ_head = occupancy_head(S);
   c.occ_sort_pipe = occupancy_sort_pipe(S);
   if (c.occ_sort_pipe < 1) c.sort_kernel = kSortRegs;  // shared memory too small on this device
-  // Kernel variants: defaults measured on GB300; REINDEX_TUNE="sort=regs|pipe,rank=ballot|match,hist=uniform|peel|match"
-  // overrides them (used to compare variants; every variant computes the same result).
-  if (const char* tune = std::getenv("REINDEX_TUNE")) {
-    if (std::strstr(tune, "grid=tile")) c.grid_per_tile = 1;
-    if (std::strstr(tune, "grid=persist")) c.grid_per_tile = 0;
-    if (std::strstr(tune, "sort=regs")) c.sort_kernel = kSortRegs;
-    if (std::strstr(tune, "sort=pipe") && c.occ_sort_pipe > 0) c.sort_kernel = kSortPipe;
-    if (std::strstr(tune, "rank=match")) c.rank_mode = kRankMatchAny;
-    if (std::strstr(tune, "rank=ballot")) c.rank_mode = kRankBallot;
-    if (std::strstr(tune, "hist=uniform")) c.hist_mode = kHistUniform;
-    if (std::strstr(tune, "hist=peel")) c.hist_mode = kHistPeel;
-    if (std::strstr(tune, "hist=match")) c.hist_mode = kHistMatchAny;
-  }
-  return cache.emplace(std::make_pair(dev, S), c).first->second;
+  // Defaults are the variants measured fastest on GB300; a tuning cache (written by the
+  // autotuner) and then REINDEX_TUNE override them.
+  apply_tuning(c, tuning_from_cache(dev, c.sms, S).c_str());
+  apply_tuning(c, std::getenv("REINDEX_TUNE"));
+  return g_cfg.emplace(std::make_pair(dev, S), c).first->second;
+}
+
+const LaunchCfg& launch_cfg(int S) {
+  std::lock_guard<std::mutex> g(g_cfg_mu);
+  return launch_cfg_locked(S);
+}
+
+void set_launch_cfg(int S, const LaunchCfg& c) {
+  std::lock_guard<std::mutex> g(g_cfg_mu);
+  launch_cfg_locked(S) = c;
 }
 
 // ---------------------------------------------------------------------------------------------

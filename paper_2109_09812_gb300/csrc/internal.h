@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace reindex {
@@ -21,8 +23,13 @@ struct LaunchCfg {
   int grid_per_tile = 0;        // 1: one CTA per tile; 0: persistent CTAs (SMs x occupancy)
 };
 
-// Per-device launch configuration (computed once per device, thread-safe).
+// Per-device launch configuration (computed once per device and stride, thread-safe).
 const LaunchCfg& launch_cfg(int S);
+void set_launch_cfg(int S, const LaunchCfg& c);
+void apply_tuning(LaunchCfg& c, const char* spec);
+std::string describe_tuning(const LaunchCfg& c);
+// Tuning cache file (REINDEX_TUNE_CACHE): the spec stored for this device and stride, or "".
+std::string tuning_from_cache(int dev, int sms, int S);
 
 cudaError_t launch_clear(void* p, size_t bytes, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_used_flags(const int32_t* idx, int64_t M, int64_t nVtx, WsPtrs ws, const LaunchCfg& c,

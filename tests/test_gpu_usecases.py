@@ -91,3 +91,44 @@ def test_submesh_bad_element_id(rx):
     out_v, out_n, out_i = rx.reindex_submesh(dev(m.vtx.view(np.int32)), dev(m.idx), dev(sel))
     assert rx.reindex_stream_status() == rx.REINDEX_ERR_INDEX_RANGE
     assert int(out_n.item()) == -rx.REINDEX_ERR_INDEX_RANGE
+
+
+# ------------------------------------------------------------------------------------ autotuner
+
+
+def test_autotune_keeps_results_exact_and_persists(rx, tmp_path):
+    import os
+    import subprocess
+    import sys
+
+    m = synth.heightfield_soup(400, 300, 0.05, seed=21)
+    v, i = dev(m.vtx.view(np.int32)), dev(m.idx)
+    cache = tmp_path / "tune.txt"
+    os.environ["REINDEX_TUNE_CACHE"] = str(cache)
+    try:
+        chosen = rx.reindex_autotune(v, i, reps=2)
+    finally:
+        del os.environ["REINDEX_TUNE_CACHE"]
+    assert chosen.startswith("sort=") and "grid=" in chosen
+    assert rx.reindex_tuning_get(12) == chosen
+    ov, oi = oracle.reindex_sort(m.vtx, m.idx)
+    out_v, out_n, out_i = rx.reindex_mesh(v, i)
+    torch.cuda.synchronize()
+    D = int(out_n.item())
+    np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+    # explicit settings round-trip, and every variant stays exact
+    for spec in ["sort=pipe,rank=match,hist=peel,grid=tile", "sort=regs,rank=ballot,hist=match,grid=persist"]:
+        rx.reindex_tuning_set(12, spec)
+        assert rx.reindex_tuning_get(12) == spec
+        out_v, out_n, out_i = rx.reindex_mesh(v, i)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+    rx.reindex_tuning_set(12, chosen)
+    # a new process starts from the cached choice
+    assert cache.read_text().strip().endswith("|12|" + chosen)
+    code = ("import paper_2109_09812_gb300 as rx, torch; torch.zeros(1, device='cuda'); "
+            "print(rx.reindex_tuning_get(12))")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+                       env=dict(os.environ, REINDEX_TUNE_CACHE=str(cache)), cwd=os.path.dirname(os.path.dirname(__file__)))
+    assert r.stdout.strip().splitlines()[-1] == chosen, r.stderr[-2000:]
