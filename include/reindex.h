@@ -255,6 +255,12 @@ reindex_status reindex_server_drain(reindex_server* s, int timeout_ms);
 reindex_status reindex_server_get_stats(reindex_server* s, reindex_server_stats* out);
 /* Drops requests not yet started, waits for running batches, frees everything. */
 void reindex_server_destroy(reindex_server* s);
+/* Test hook for failure detection: while tile >= 0, the compaction kernel's tile `tile` (of 2048
+ * vertices) never publishes its decoupled look-back status, so the bounded waits of the tiles
+ * after it run out (about a second) and the call reports REINDEX_ERR_TIMEOUT through *out_nVtx
+ * and reindex_stream_status, leaving the CUDA context usable.  -1 turns it off (the default). */
+void reindex_debug_stall_tile(int64_t tile);
+
 /* Host-only self-check of the server's arena allocator against a brute-force model; returns the
  * number of inconsistencies (0 = correct).  Needs no GPU. */
 int reindex_debug_arena_check(uint64_t seed, int ops, size_t size);

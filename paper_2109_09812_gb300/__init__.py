@@ -40,7 +40,8 @@ EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "
             "reindex_server_create", "reindex_server_submit", "reindex_server_poll", "reindex_server_release",
             "reindex_server_drain", "reindex_server_get_stats", "reindex_server_destroy", "reindex_debug_arena_check",
             "reindex_merge_workspace_size", "reindex_merge_meshes", "reindex_submesh_workspace_size",
-            "reindex_submesh", "reindex_autotune", "reindex_tuning_get", "reindex_tuning_set"]
+            "reindex_submesh", "reindex_autotune", "reindex_tuning_get", "reindex_tuning_set",
+            "reindex_debug_stall_tile"]
 
 _lock = threading.Lock()
 _lib = None
@@ -140,6 +141,8 @@ def lib() -> ctypes.CDLL:
             L.reindex_tuning_get.restype = ci
             L.reindex_tuning_set.argtypes = [ci, ctypes.c_char_p]
             L.reindex_tuning_set.restype = ci
+            L.reindex_debug_stall_tile.argtypes = [i64]
+            L.reindex_debug_stall_tile.restype = None
             L.reindex_debug_arena_check.argtypes = [ctypes.c_uint64, ci, ctypes.c_size_t]
             L.reindex_debug_arena_check.restype = ci
             _lib = L

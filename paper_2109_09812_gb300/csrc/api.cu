@@ -1,6 +1,7 @@
 // C ABI of the re-indexing library (include/reindex.h): argument checks, workspace layout,
 // the launch sequence of the pipeline, the pool-allocating and host-buffer variants, the
 // sticky error query and the per-launch timing facility.
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <functional>
@@ -124,6 +125,9 @@ static uint8_t* skip_buffer(const Plan* plan, cudaStream_t st) {
   return h;
 }
 }  // namespace prof
+
+static std::atomic<int64_t> g_stall_tile{-1};
+int64_t debug_stall_tile() { return g_stall_tile.load(); }
 
 static reindex_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return REINDEX_OK;
@@ -597,6 +601,8 @@ int reindex_profile_collect(reindex_profile_record* out, int maxRecords) {
   for (uint8_t* h : pins) cudaFreeHost(h);
   return bad ? -1 : (int)recs.size();
 }
+
+void reindex_debug_stall_tile(int64_t tile) { g_stall_tile.store(tile < 0 ? -1 : tile); }
 
 const char* reindex_kernel_name(int kernel) {
   static const char* names[REINDEX_K_COUNT] = {"clear",     "used_flags", "compact_hist", "sort_plan",

@@ -43,7 +43,7 @@ constexpr int64_t kMaxCount = (int64_t)kValMask;  // largest count a status word
 
 // Bounded spin: every wait on another CTA gives up after this many polls, records
 // REINDEX_ERR_TIMEOUT and publishes a (meaningless) prefix so that no successor waits forever.
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kSpinLimit = 1u << 20;
 constexpr int kLookWindow = 16;  // predecessor status words fetched per look-back round (sort)
 
 // Device-side error codes (same numbers as reindex_status).

@@ -58,6 +58,9 @@ cudaError_t launch_gather_elements(const int32_t* idx, int k, int64_t nElem, con
                                   int32_t* out, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_set_count(int64_t* out_nVtx, int64_t value, cudaStream_t st);
 
+// Test hook: compaction tile that withholds its look-back status (-1: none).
+int64_t debug_stall_tile();
+
 // Occupancy queries for the persistent kernels (per template instantiation).
 int occupancy_compact(int S);
 int occupancy_sort(int S);

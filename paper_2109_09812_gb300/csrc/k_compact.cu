@@ -15,9 +15,11 @@ namespace reindex {
 
 // S is the vertex stride.  In batched mode (kSeg) the item key is the owning mesh's id followed
 // by the vertex words (SI = S + 4 bytes), so that one sort groups the items by mesh.
+// stall_tile >= 0 (a test hook, -1 otherwise): that tile never publishes its look-back status, so
+// its successors' bounded waits run out and the call ends with REINDEX_ERR_TIMEOUT.
 template <int S, int kHist, bool kSeg>
 __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ vtx, int64_t nVtx, WsPtrs ws,
-                                                       int64_t tilesV, SegArgs seg) {
+                                                       int64_t tilesV, SegArgs seg, int64_t stall_tile) {
   constexpr int SI = kSeg ? S + 4 : S;  // item key bytes
   constexpr int K = SI / 4;
   constexpr int P = SI;  // byte digits per key
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
       woff += (q < w) ? c : 0u;
       total += c;
     }
-    if (w == 0) {
+    if (w == 0 && tile != stall_tile) {
       uint32_t prefix = 0;
       uint32_t* my = ws.lb_compact + tile;
       if (tile == 0) {
@@ -89,6 +91,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
         if (tile == tilesV - 1) ctrl->U = prefix + total;
       }
     }
+    if (tile == stall_tile && t == 0) s_prefix = 0;  // the stalled tile writes at [0, total): in bounds
     __syncthreads();
     const int64_t obase = (int64_t)s_prefix + woff;
 
@@ -166,12 +169,13 @@ int occupancy_compact(int S) {
 template <int S, bool kSeg>
 static void launch_s(int g, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, int mode, const SegArgs& seg,
                      cudaStream_t st) {
+  const int64_t stall = debug_stall_tile();
   if (kSeg || mode == kHistUniform)
-    k_compact<S, kHistUniform, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg);
+    k_compact<S, kHistUniform, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg, stall);
   else if (mode == kHistMatchAny)
-    k_compact<S, kHistMatchAny, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg);
+    k_compact<S, kHistMatchAny, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg, stall);
   else
-    k_compact<S, kHistPeel, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg);
+    k_compact<S, kHistPeel, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg, stall);
 }
 
 cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,

@@ -244,3 +244,25 @@ def test_profile_records_every_kernel(rx):
     # x and y are integers 0..256 as float32: their lowest byte is always zero -> skipped passes
     sk = {r["digit"]: r["skipped"] for r in recs if r["name"] == "onesweep"}
     assert sk[8] and sk[4] and not sk[0]
+
+
+def test_lookback_wait_runs_out_and_reports_timeout(rx):
+    """A compaction tile that never publishes its status (test hook): the waits after it give up
+    after their iteration limit, the call reports REINDEX_ERR_TIMEOUT, and the next call works."""
+    import time
+
+    m = synth.heightfield_soup(64, 64, 0.05, seed=31)  # 25,805 vertices: 13 compaction tiles
+    v, i = to_dev(m.vtx, m.idx)
+    rx.reindex_stream_status()
+    rx.lib().reindex_debug_stall_tile(5)
+    try:
+        t0 = time.time()
+        out_v, out_n, out_i = rx.reindex_mesh(v, i)
+        status = rx.reindex_stream_status()
+        elapsed = time.time() - t0
+    finally:
+        rx.lib().reindex_debug_stall_tile(-1)
+    assert status == rx.REINDEX_ERR_TIMEOUT
+    assert int(out_n.item()) == -rx.REINDEX_ERR_TIMEOUT
+    assert elapsed < 60
+    assert assert_parity(rx, m.vtx, m.idx.reshape(-1), 3) == 65 * 65
