@@ -494,6 +494,14 @@ def build_mesh(workload):
     return synth.config_mesh(cfg), None
 
 
+def step_model_bytes(N, S, M, U, D):
+    """Bytes a re-indexing step must move under a fixed model: 8-bit digits, all S radix passes
+    (no credit for skipped ones), items of W = S + 4 bytes.  Used-flag scatter 4M + N/8; compaction
+    N*S + N/8 + U*W; sort 2*S*U*W; run heads, scan, scatter and gather U*W + 4U + D*S; remap 12M."""
+    W = S + 4
+    return (4 * M + N / 8) + (N * S + N / 8 + U * W) + 2 * S * U * W + (U * W + 4 * U + D * S) + 12 * M
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -566,6 +574,12 @@ def run_ours(args, world, rank, local):
                 "traffic": ncu_traffic(args.workload), "algorithmic_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": avg_ms, "passes_per_step": len(sweeps) / args.steps}
 
+    # the whole step against the fixed byte model (8-bit digits, all S passes, W-byte items)
+    model = step_model_bytes(n_vtx, S, M, U, D)
+    step_model = {"bytes": model, "achieved": model / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                  "frac": model / (ms / 1e3) / 1e9 / peak,
+                  "compulsory_frac": (n_vtx * S + 8 * M + D * S) / (ms / 1e3) / 1e9 / peak}
+
     # ---- end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -587,7 +601,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": WORKLOADS[args.workload][0], "n_vtx": n_vtx, "n_elem": n_elem, "stride_bytes": S,
                    "idx_per_elem": k, "unique_out": D, "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 ({(n_vtx * S + M * 4) / 1e6:.0f} MB read per step)"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "tuning": tuning,
+        "roofline": roofline, "step_model": step_model, "cpu_baseline": cpu, "e2e": e2e, "tuning": tuning,
         "gpu_launches": len(recs),
         "kernels": {k_: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k_, v in sorted(per_kernel.items())},
         "clocks": clocks.summary(),
