@@ -21,26 +21,33 @@ namespace reindex {
 static std::mutex g_cfg_mu;
 static std::map<std::pair<int, int>, LaunchCfg> g_cfg;
 
-// Applies "sort=regs|pipe,rank=ballot|match,hist=uniform|peel|match,grid=persist|tile" (any
-// subset, in any order).  Every variant computes the same result.
+// Applies "sort=regs|pipe|tiles|auto,rank=ballot|match,hist=uniform|peel|match,grid=persist|tile,
+// swaves=tile|1|4" (any subset, in any order).  Every variant computes the same result.
 void apply_tuning(LaunchCfg& c, const char* spec) {
   if (!spec) return;
   if (std::strstr(spec, "grid=tile")) c.grid_per_tile = 1;
   if (std::strstr(spec, "grid=persist")) c.grid_per_tile = 0;
   if (std::strstr(spec, "sort=regs")) c.sort_kernel = kSortRegs;
   if (std::strstr(spec, "sort=pipe") && c.occ_sort_pipe > 0) c.sort_kernel = kSortPipe;
+  if (std::strstr(spec, "sort=tiles")) c.sort_kernel = kSortTiles;
+  if (std::strstr(spec, "sort=auto")) c.sort_kernel = kSortAuto;
   if (std::strstr(spec, "rank=match")) c.rank_mode = kRankMatchAny;
   if (std::strstr(spec, "rank=ballot")) c.rank_mode = kRankBallot;
   if (std::strstr(spec, "hist=uniform")) c.hist_mode = kHistUniform;
   if (std::strstr(spec, "hist=peel")) c.hist_mode = kHistPeel;
   if (std::strstr(spec, "hist=match")) c.hist_mode = kHistMatchAny;
+  if (std::strstr(spec, "swaves=tile")) c.scatter_waves = 0;
+  if (std::strstr(spec, "swaves=1")) c.scatter_waves = 1;
+  if (std::strstr(spec, "swaves=4")) c.scatter_waves = 4;
 }
 
 std::string describe_tuning(const LaunchCfg& c) {
-  std::string d = c.sort_kernel == kSortPipe ? "sort=pipe" : "sort=regs";
+  const char* sorts[] = {"sort=regs", "sort=pipe", "sort=tiles", "sort=auto"};
+  std::string d = sorts[c.sort_kernel];
   d += c.rank_mode == kRankMatchAny ? ",rank=match" : ",rank=ballot";
   d += c.hist_mode == kHistMatchAny ? ",hist=match" : (c.hist_mode == kHistPeel ? ",hist=peel" : ",hist=uniform");
   d += c.grid_per_tile ? ",grid=tile" : ",grid=persist";
+  d += c.scatter_waves ? ",swaves=" + std::to_string(c.scatter_waves) : std::string(",swaves=tile");
   return d;
 }
 
@@ -56,7 +63,8 @@ static LaunchCfg& launch_cfg_locked(int S) {
   c.occ_sort = occupancy_sort(S);
   c.occ_head = occupancy_head(S);
   c.occ_sort_pipe = occupancy_sort_pipe(S);
-  if (c.occ_sort_pipe < 1) c.sort_kernel = kSortRegs;  // shared memory too small on this device
+  c.occ_tiles = occupancy_tiles(S);
+  if (c.occ_sort_pipe < 1 && c.sort_kernel == kSortPipe) c.sort_kernel = kSortRegs;  // too little shared memory
   // Defaults are the variants measured fastest on GB300; a tuning cache (written by the
   // autotuner) and then REINDEX_TUNE override them.
   apply_tuning(c, tuning_from_cache(dev, c.sms, S).c_str());
@@ -64,9 +72,9 @@ static LaunchCfg& launch_cfg_locked(int S) {
   return g_cfg.emplace(std::make_pair(dev, S), c).first->second;
 }
 
-const LaunchCfg& launch_cfg(int S) {
+LaunchCfg launch_cfg(int S) {
   std::lock_guard<std::mutex> g(g_cfg_mu);
-  return launch_cfg_locked(S);
+  return launch_cfg_locked(S);  // copied under the lock
 }
 
 void set_launch_cfg(int S, const LaunchCfg& c) {
@@ -173,11 +181,32 @@ struct PipeExtras {
   bool flags_done = false;
 };
 
+// One radix pass (digit d) with the configured kernel variant.
+static cudaError_t sort_pass(int S, int d, const WsPtrs& p, const LaunchCfg& c, cudaStream_t st,
+                             const uint8_t* skip) {
+  if (c.sort_kernel == kSortTiles) {
+    {
+      prof::Scope s(REINDEX_K_TILE_COUNT, d, st, skip);
+      cudaError_t e = launch_tile_count(S, d, p, c, st);
+      if (e != cudaSuccess) return e;
+    }
+    {
+      prof::Scope s(REINDEX_K_TILE_OFFSETS, d, st, skip);
+      cudaError_t e = launch_tile_offsets(d, p, st);
+      if (e != cudaSuccess) return e;
+    }
+    prof::Scope s(REINDEX_K_TILE_SCATTER, d, st, skip);
+    return launch_tile_scatter(S, d, p, c, st);
+  }
+  prof::Scope s(REINDEX_K_ONESWEEP, d, st, skip);
+  return c.sort_kernel == kSortPipe ? launch_onesweep_pipe(S, d, p, c, st) : launch_onesweep(S, d, p, c, st);
+}
+
 // The launch sequence (all on `st`, no host synchronisation).
 static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t M,
                                    void* out_vtx, int64_t* out_nVtx, int32_t* out_idx, void* ws,
                                    const WsLayout& L, cudaStream_t st, const PipeExtras* extra = nullptr) {
-  const LaunchCfg& c = launch_cfg(S);
+  const LaunchCfg c = resolve_cfg(launch_cfg(S), S, L.Umax);  // one configuration for the whole call
   const WsPtrs p = ws_ptrs(ws, L);
   {
     prof::Scope s(REINDEX_K_CLEAR, -1, st);
@@ -197,13 +226,10 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
   }
   {
     prof::Scope s(REINDEX_K_SORT_PLAN, -1, st);
-    REINDEX_TRY(launch_sort_plan(S, p, st));
+    REINDEX_TRY(launch_sort_plan(S, p, c.sort_kernel == kSortTiles, st));
   }
   const uint8_t* skip = prof::skip_buffer(p.plan, st);
-  for (int d = 0; d < L.P; ++d) {
-    prof::Scope s(REINDEX_K_ONESWEEP, d, st, skip);
-    REINDEX_TRY(c.sort_kernel == kSortPipe ? launch_onesweep_pipe(S, d, p, c, st) : launch_onesweep(S, d, p, c, st));
-  }
+  for (int d = 0; d < L.P; ++d) REINDEX_TRY(sort_pass(S, d, p, c, st, skip));
   {
     prof::Scope s(REINDEX_K_HEAD_SCAN, -1, st);
     REINDEX_TRY(launch_head_scan(S, p, out_vtx, out_nVtx, (uint32_t)nVtx, c, nullptr, st));
@@ -239,8 +265,8 @@ static reindex_status run_batched(const void* vtx, int64_t nVtx, int S, const in
                                   const int64_t* vtxOff, const int64_t* elemOff, int nMeshes, void* out_vtx,
                                   int64_t* outOff, int32_t* out_idx, void* ws, const SegLayout& SL,
                                   cudaStream_t st) {
-  const LaunchCfg& cS = launch_cfg(S);
-  const LaunchCfg& c = launch_cfg(S + 4);
+  const LaunchCfg cS = launch_cfg(S);
+  const LaunchCfg c = resolve_cfg(launch_cfg(S + 4), S + 4, SL.L.Umax);
   const WsPtrs p = ws_ptrs(ws, SL.L);
   unsigned char* b = static_cast<unsigned char*>(ws);
   SegArgs seg;
@@ -267,18 +293,16 @@ static reindex_status run_batched(const void* vtx, int64_t nVtx, int S, const in
   }
   {
     prof::Scope sc(REINDEX_K_COMPACT, -1, st);
-    REINDEX_TRY(launch_compact(S, vtx, nVtx, p, SL.L.tilesV, cS, &seg, st));
+    LaunchCfg cc = cS;  // the sort (configured for S + 4) decides whether histograms are taken
+    cc.sort_kernel = c.sort_kernel;
+    REINDEX_TRY(launch_compact(S, vtx, nVtx, p, SL.L.tilesV, cc, &seg, st));
   }
   {
     prof::Scope sc(REINDEX_K_SORT_PLAN, -1, st);
-    REINDEX_TRY(launch_sort_plan(S + 4, p, st));
+    REINDEX_TRY(launch_sort_plan(S + 4, p, c.sort_kernel == kSortTiles, st));
   }
   const uint8_t* skip = prof::skip_buffer(p.plan, st);
-  for (int d = 0; d < S + 4; ++d) {
-    prof::Scope sc(REINDEX_K_ONESWEEP, d, st, skip);
-    REINDEX_TRY(c.sort_kernel == kSortPipe ? launch_onesweep_pipe(S + 4, d, p, c, st)
-                                           : launch_onesweep(S + 4, d, p, c, st));
-  }
+  for (int d = 0; d < S + 4; ++d) REINDEX_TRY(sort_pass(S + 4, d, p, c, st, skip));
   {
     prof::Scope sc(REINDEX_K_HEAD_SCAN, -1, st);
     REINDEX_TRY(launch_head_scan(S + 4, p, out_vtx, total, (uint32_t)nVtx, c, &seg, st));
@@ -607,7 +631,8 @@ void reindex_debug_stall_tile(int64_t tile) { g_stall_tile.store(tile < 0 ? -1 :
 const char* reindex_kernel_name(int kernel) {
   static const char* names[REINDEX_K_COUNT] = {"clear",     "used_flags", "compact_hist", "sort_plan",
                                                "onesweep",  "head_scan",  "remap",        "finalize",
-                                               "seg_prepare", "seg_offsets"};
+                                               "seg_prepare", "seg_offsets", "tile_count", "tile_offsets",
+                                               "tile_scatter"};
   return (kernel >= 0 && kernel < REINDEX_K_COUNT) ? names[kernel] : "unknown";
 }
 

@@ -28,11 +28,17 @@ constexpr int kMaxDigits = 20;             // 20-byte keys (16-byte vertices + a
 // Kernel variants (chosen per device by launch_cfg; see REINDEX_TUNE in api.cu).
 constexpr int kSortRegs = 0;      // radix pass with items in registers (k_onesweep)
 constexpr int kSortPipe = 1;      // radix pass pipelined through shared memory (k_onesweep_pipe)
+constexpr int kSortTiles = 2;     // radix pass with precounted tile offsets (k_radix_tiles.cu)
+constexpr int kSortAuto = 3;      // per call: kSortTiles for large meshes with keys of <= 12 bytes,
+                                  // else kSortRegs (the faster of the two there on GB300)
+constexpr int64_t kTilesMinItems = 1 << 21;  // below this, launch count favours kSortRegs
 constexpr int kRankBallot = 0;    // digit peers from 8 ballots
 constexpr int kRankMatchAny = 1;  // digit peers from match.any
 constexpr int kHistUniform = 0;   // histogram: one atomic per warp when the digit is warp-uniform
 constexpr int kHistPeel = 1;      // histogram: the first lane's digit group counted with one atomic
 constexpr int kHistMatchAny = 2;  // histogram: one atomic per distinct digit (match.any)
+constexpr int kHistNone = 3;      // no histograms: key bit masks and the low-16-bit plane instead
+                                  // (the "tiles" sort counts digits per pass itself)
 
 // Look-back status word: 2-bit flag + 30-bit count.
 constexpr uint32_t kFlagAgg = 1u << 30;    // tile aggregate only
@@ -58,7 +64,9 @@ struct Control {             // zeroed at the start of every call
   uint32_t U;                // number of used vertices (written by the last compaction tile)
   uint32_t ctr[32];          // atomic tile counters: [0] compaction, [1 + d] sort digit d,
                              // [1 + kMaxDigits] head scan
-  uint32_t pad[30];
+  uint32_t kor[kMaxDigits / 4];   // OR of key word q over the used vertices (compaction, kHistNone)
+  uint32_t knand[kMaxDigits / 4]; // OR of the complement: bit b varies iff set in both masks
+  uint32_t pad[20];
 };
 static_assert(sizeof(Control) == 256, "Control block is one 256-byte line");
 
@@ -68,7 +76,9 @@ struct Plan {                // written by the sort-plan kernel
   uint8_t skip[kMaxDigits];  // 1: digit d is constant over all items; its pass moves nothing
   uint8_t src[kMaxDigits];   // buffer the pass for digit d reads (0 = A, 1 = B)
   uint8_t area[kMaxDigits];  // which of the two look-back areas the pass uses
-  uint8_t pad[16];
+  int8_t next[kMaxDigits];   // the next non-trivial digit after d, or -1
+  int8_t first;              // the first non-trivial digit, or -1
+  uint8_t pad[11];
   uint32_t base[kMaxDigits][kRadix];  // exclusive prefix of the digit histogram
 };
 
@@ -80,7 +90,8 @@ struct WsLayout {
   int64_t tilesV = 0, tilesS = 0, tilesH = 0;
   size_t off_ctrl = 0, off_hist = 0, off_lb_compact = 0, off_lb_head = 0, off_lb_sort = 0,
          off_bitmask = 0, zero_bytes = 0;
-  size_t off_plan = 0, off_itemsA = 0, off_itemsB = 0, items_bytes = 0, idoff = 0, off_old2new = 0, total = 0;
+  size_t off_plan = 0, off_itemsA = 0, off_itemsB = 0, items_bytes = 0, idoff = 0, off_old2new = 0, off_digits = 0,
+         total = 0;
 
   void compute(int64_t n, int s, int64_t m) {
     S = s; K = s / 4; P = s; nVtx = n; M = m;
@@ -105,6 +116,7 @@ struct WsLayout {
     off_itemsA = o;      o += items_bytes;
     off_itemsB = o;      o += items_bytes;
     off_old2new = o;     o = align_up(o + (size_t)n * 4, 256);
+    off_digits = o;      o = align_up(o + 2 * (size_t)align_up((size_t)Umax, kSortTile), 256);  // whole tiles
     total = o;
   }
 };
@@ -121,6 +133,8 @@ struct WsPtrs {
   unsigned char* itemsA;
   unsigned char* itemsB;
   uint32_t* old2new;     // [nVtx]
+  uint8_t* digits;       // [Umax rounded up to whole sort tiles]: digit of the next radix pass; before
+                         // the first pass, viewed as uint16: low 16 bits of the last key word
   int64_t tilesS;        // capacity of the sort look-back table, in tiles
   int64_t Umax;          // capacity of each item buffer, in items
   int64_t idoff;         // byte offset of the id plane inside an item buffer (S = 8, 16)
@@ -139,6 +153,7 @@ inline WsPtrs ws_ptrs(void* ws, const WsLayout& L) {
   p.itemsA = b + L.off_itemsA;
   p.itemsB = b + L.off_itemsB;
   p.old2new = reinterpret_cast<uint32_t*>(b + L.off_old2new);
+  p.digits = b + L.off_digits;
   p.tilesS = L.tilesS;
   p.Umax = L.Umax;
   p.idoff = (int64_t)L.idoff;
@@ -395,23 +410,43 @@ __device__ __forceinline__ uint32_t wait_status(const uint32_t* p, Control* c) {
 }
 
 // Decoupled look-back over one counter per tile, done by one full warp: returns the exclusive
-// prefix of tile `tile` (> 0) in every lane.  Each round inspects the 32 predecessors
-// tile-1 .. tile-32 at once, stops at the nearest one carrying an inclusive prefix.
+// prefix of tile `tile` (> 0) in every lane.  Each round inspects the 32*W nearest predecessors
+// not yet accumulated (lane l: W consecutive ones), all loads in flight together, and stops at
+// the nearest one carrying an inclusive prefix.  (The nearest prefix is usually within 32
+// tiles: windows of 256 and 1024 measured slower, since every round waits for all of them.)
+template <int W = 1>
 __device__ __forceinline__ uint32_t warp_lookback(const uint32_t* lb, int64_t tile, Control* c) {
   const int lane = threadIdx.x & 31;
   uint32_t excl = 0;
   int64_t hi = tile - 1;  // newest predecessor not yet accumulated
   while (true) {
-    const int64_t t = hi - lane;
-    uint32_t s = (t >= 0) ? wait_status(lb + t, c) : kFlagPre;  // before tile 0: prefix 0
-    const uint32_t pre_mask = __ballot_sync(0xffffffffu, (s & kFlagMask) == kFlagPre);
-    const int stop = __ffs(pre_mask) - 1;  // nearest predecessor with an inclusive prefix
-    uint32_t v = (pre_mask != 0 && lane > stop) ? 0u : (s & kValMask);
+    uint32_t s[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const int64_t q = hi - (int64_t)lane * W - i;
+      s[i] = q >= 0 ? ld_relaxed(lb + q) : kFlagPre;  // before tile 0: prefix 0
+    }
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const int64_t q = hi - (int64_t)lane * W - i;
+      if (q >= 0 && (s[i] & kFlagMask) == 0) s[i] = wait_status(lb + q, c);
+    }
+    int stop = W;  // nearest predecessor of this lane carrying an inclusive prefix
+#pragma unroll
+    for (int i = W - 1; i >= 0; --i)
+      if ((s[i] & kFlagMask) == kFlagPre) stop = i;
+    uint32_t part = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+      if (i <= stop) part += s[i] & kValMask;
+    const uint32_t pre_mask = __ballot_sync(0xffffffffu, stop < W);
+    const int first = pre_mask ? __ffs(pre_mask) - 1 : 32;  // nearest lane with a prefix
+    uint32_t v = lane <= first ? part : 0u;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     excl += v;
     if (pre_mask != 0) break;
-    hi -= 32;
+    hi -= 32 * W;
   }
   return excl;
 }

@@ -17,14 +17,22 @@ struct LaunchCfg {
   int occ_sort = 0;
   int occ_head = 0;
   int occ_sort_pipe = 0;
-  int sort_kernel = kSortRegs;  // kSortRegs (k_onesweep) or kSortPipe (k_onesweep_pipe)
+  int occ_tiles = 0;
+  int sort_kernel = kSortAuto;  // kSortRegs (k_onesweep), kSortPipe (k_onesweep_pipe), kSortTiles, kSortAuto
   int rank_mode = kRankBallot;  // onesweep digit matching (kRank*)
   int hist_mode = kHistUniform; // compaction histogram method (kHist*)
   int grid_per_tile = 0;        // 1: one CTA per tile; 0: persistent CTAs (SMs x occupancy)
+  int scatter_waves = 0;        // "tiles" scatter: 0 one CTA per tile, else CTAs = waves x SMs x occupancy
 };
 
+// The configuration for one call: kSortAuto resolved for S-byte keys and up to Umax items.
+inline LaunchCfg resolve_cfg(LaunchCfg c, int S, int64_t Umax) {
+  if (c.sort_kernel == kSortAuto) c.sort_kernel = (S <= 12 && Umax >= kTilesMinItems) ? kSortTiles : kSortRegs;
+  return c;
+}
+
 // Per-device launch configuration (computed once per device and stride, thread-safe).
-const LaunchCfg& launch_cfg(int S);
+LaunchCfg launch_cfg(int S);
 void set_launch_cfg(int S, const LaunchCfg& c);
 void apply_tuning(LaunchCfg& c, const char* spec);
 std::string describe_tuning(const LaunchCfg& c);
@@ -37,9 +45,14 @@ cudaError_t launch_used_flags(const int32_t* idx, int64_t M, int64_t nVtx, WsPtr
 // seg == nullptr: single mesh; otherwise batched, S being the vertex stride (items carry S + 4 bytes).
 cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
                            const SegArgs* seg, cudaStream_t st);
-cudaError_t launch_sort_plan(int S, WsPtrs ws, cudaStream_t st);
+// from_masks: trivial passes from the key bit masks (the "tiles" sort takes no upfront histograms).
+cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, cudaStream_t st);
 cudaError_t launch_onesweep(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_onesweep_pipe(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
+// The "tiles" radix pass (k_radix_tiles.cu): per-tile digit counts, their scan, the scatter.
+cudaError_t launch_tile_count(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_tile_offsets(int digit, WsPtrs ws, cudaStream_t st);
+cudaError_t launch_tile_scatter(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 // seg != nullptr: batched, S being the item key size (vertex stride + 4); writes seg->outOff.
 cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx,
                              const LaunchCfg& c, const SegArgs* seg, cudaStream_t st);
@@ -65,6 +78,7 @@ int64_t debug_stall_tile();
 int occupancy_compact(int S);
 int occupancy_sort(int S);
 int occupancy_sort_pipe(int S);
+int occupancy_tiles(int S);
 int occupancy_head(int S);
 
 // Device-wide sticky error word (read and cleared by reindex_stream_status).

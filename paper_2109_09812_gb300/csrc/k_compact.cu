@@ -8,7 +8,9 @@
 //
 // Tiles of 2048 vertices (8 warps x 8 rows x 32 lanes); a tile's output offset comes from a
 // decoupled look-back over per-tile used counts, so items keep vertex order.  The same pass
-// counts, per byte digit d of the key, how many used vertices have each digit value.
+// counts, per byte digit d of the key, how many used vertices have each digit value; or, for the
+// "tiles" sort (kHistNone), it records which key bits vary (OR of each key word and of its
+// complement) and the low 16 bits of each item's last key word, at the item's position.
 #include "internal.h"
 
 namespace reindex {
@@ -23,13 +25,19 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
   constexpr int SI = kSeg ? S + 4 : S;  // item key bytes
   constexpr int K = SI / 4;
   constexpr int P = SI;  // byte digits per key
-  __shared__ uint32_t s_hist[P * kRadix];
+  constexpr bool kCount = kHist != kHistNone;
+  __shared__ uint32_t s_hist[kCount ? P * kRadix : 1];
   __shared__ uint32_t s_warp[kWarps];
   __shared__ uint32_t s_tile, s_prefix;
   Control* ctrl = ws.ctrl;
   if (block_error(ctrl)) return;  // an invalid index was seen: nothing downstream is meaningful
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  for (int i = t; i < P * kRadix; i += kThreads) s_hist[i] = 0;
+  if constexpr (kCount)
+    for (int i = t; i < P * kRadix; i += kThreads) s_hist[i] = 0;
+  uint32_t kor[K], knand[K];  // this thread's OR of each key word and of its complement
+#pragma unroll
+  for (int q = 0; q < K; ++q) kor[q] = knand[q] = 0;
+  uint16_t* low16 = reinterpret_cast<uint16_t*>(ws.digits);
 
   for (;;) {
     if (t == 0) s_tile = atomicAdd(&ctrl->ctr[0], 1u);
@@ -106,7 +114,16 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
         for (int q = 0; q < K; ++q) it.k[q] = k[r][q];
         it.id = (uint32_t)(vbase + r * 32 + lane);
         ItemIO<SI>::store(ws.itemsA, ws.idoff, obase + pos[r], it);
+        if constexpr (!kCount) {
+          low16[obase + pos[r]] = (uint16_t)k[r][K - 1];
+#pragma unroll
+          for (int q = 0; q < K; ++q) {
+            kor[q] |= k[r][q];
+            knand[q] |= ~k[r][q];
+          }
+        }
       }
+      if constexpr (!kCount) continue;
       // Histograms.  Many key bytes are heavily skewed (exponent bytes, the zero low bytes of
       // small integers), and lanes adding to the same bin in one instruction serialise, so the
       // lanes that share a digit are combined first (three variants, chosen per device).
@@ -136,9 +153,20 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
     __syncthreads();  // s_tile, s_warp and s_prefix are rewritten by the next tile
   }
   __syncthreads();
-  for (int i = t; i < P * kRadix; i += kThreads) {
-    const uint32_t c = s_hist[i];
-    if (c) atomicAdd(ws.hist + i, c);
+  if constexpr (kCount) {
+    for (int i = t; i < P * kRadix; i += kThreads) {
+      const uint32_t c = s_hist[i];
+      if (c) atomicAdd(ws.hist + i, c);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const uint32_t a = __reduce_or_sync(0xffffffffu, kor[q]), b = __reduce_or_sync(0xffffffffu, knand[q]);
+      if (lane == 0) {
+        if (a) atomicOr(&ctrl->kor[q], a);
+        if (b) atomicOr(&ctrl->knand[q], b);
+      }
+    }
   }
 }
 
@@ -149,9 +177,12 @@ static int occ() {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistPeel, false>, kThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_compact<S, kHistMatchAny, false>, kThreads, 0);
   int n = min(a, min(b, c));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistNone, false>, kThreads, 0);
+  n = min(n, a);
   if constexpr (S <= 16) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistUniform, true>, kThreads, 0);
-    n = min(n, a);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistNone, true>, kThreads, 0);
+    n = min(n, min(a, b));
   }
   return n < 1 ? 1 : n;
 }
@@ -170,7 +201,9 @@ template <int S, bool kSeg>
 static void launch_s(int g, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, int mode, const SegArgs& seg,
                      cudaStream_t st) {
   const int64_t stall = debug_stall_tile();
-  if (kSeg || mode == kHistUniform)
+  if (mode == kHistNone)
+    k_compact<S, kHistNone, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg, stall);
+  else if (kSeg || mode == kHistUniform)
     k_compact<S, kHistUniform, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg, stall);
   else if (mode == kHistMatchAny)
     k_compact<S, kHistMatchAny, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg, stall);
@@ -184,20 +217,22 @@ cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int6
   int64_t g = c.grid_per_tile ? tilesV : (int64_t)c.sms * c.occ_compact;
   if (g > tilesV) g = tilesV;
   const SegArgs none{};
+  // the "tiles" sort counts digits per pass and needs no upfront histograms
+  const int mode = c.sort_kernel == kSortTiles ? kHistNone : c.hist_mode;
   if (seg) {
     switch (S) {
-      case 4: launch_s<4, true>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, *seg, st); break;
-      case 8: launch_s<8, true>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, *seg, st); break;
-      case 12: launch_s<12, true>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, *seg, st); break;
-      default: launch_s<16, true>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, *seg, st); break;
+      case 4: launch_s<4, true>((int)g, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
+      case 8: launch_s<8, true>((int)g, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
+      case 12: launch_s<12, true>((int)g, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
+      default: launch_s<16, true>((int)g, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
     }
   } else {
     switch (S) {
-      case 4: launch_s<4, false>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, none, st); break;
-      case 8: launch_s<8, false>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, none, st); break;
-      case 12: launch_s<12, false>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, none, st); break;
-      case 16: launch_s<16, false>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, none, st); break;
-      default: launch_s<20, false>((int)g, vtx, nVtx, ws, tilesV, c.hist_mode, none, st); break;
+      case 4: launch_s<4, false>((int)g, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      case 8: launch_s<8, false>((int)g, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      case 12: launch_s<12, false>((int)g, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      case 16: launch_s<16, false>((int)g, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      default: launch_s<20, false>((int)g, vtx, nVtx, ws, tilesV, mode, none, st); break;
     }
   }
   return cudaGetLastError();

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int
 }
 
 // Digit offsets and pass plan (one CTA of 256 threads; thread t owns digit value t).
-__global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P) {
+// from_masks: trivial digits come from the key bit masks (no upfront histograms were taken).
+__global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from_masks) {
   __shared__ uint32_t s_warp[kRadix / 32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const uint32_t U = ws.ctrl->U;
@@ -73,7 +74,14 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P) {
   for (int d = 0; d < P; ++d) {
     const uint32_t c = ws.hist[d * kRadix + t];
     // A digit whose value is the same for all U items: that pass is the identity.
-    const int trivial = __syncthreads_or(c == U);
+    int trivial;
+    if (from_masks) {
+      const int q = P / 4 - 1 - (d >> 2);
+      trivial = (((ws.ctrl->kor[q] & ws.ctrl->knand[q]) >> ((d & 3) * 8)) & 0xFFu) == 0;
+      __syncthreads();
+    } else {
+      trivial = __syncthreads_or(c == U);
+    }
     const uint32_t incl = warp_incl_scan(c);
     if (lane == 31) s_warp[w] = incl;
     __syncthreads();
@@ -93,6 +101,12 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P) {
   }
   if (t == 0) {
     for (int d = P; d < kMaxDigits; ++d) plan->skip[d] = 1;
+    int nxt = -1;
+    for (int d = kMaxDigits - 1; d >= 0; --d) {
+      plan->next[d] = (int8_t)nxt;
+      if (!plan->skip[d]) nxt = d;
+    }
+    plan->first = (int8_t)nxt;
     plan->U = U;
     plan->final_sel = sel;
   }
@@ -193,8 +207,8 @@ cudaError_t launch_used_flags(const int32_t* idx, int64_t M, int64_t nVtx, WsPtr
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort_plan(int S, WsPtrs ws, cudaStream_t st) {
-  k_sort_plan<<<1, kRadix, 0, st>>>(ws, S);
+cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, cudaStream_t st) {
+  k_sort_plan<<<1, kRadix, 0, st>>>(ws, S, from_masks ? 1 : 0);
   return cudaGetLastError();
 }
 

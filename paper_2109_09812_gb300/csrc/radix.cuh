@@ -1,0 +1,107 @@
+// Pieces shared by the radix-pass kernels (k_onesweep.cu, k_radix_tiles.cu): shared-memory
+// staging of a tile in digit order, the per-CTA shared-memory budget and the warp-level digit
+// matching used to rank items stably.
+#pragma once
+
+#include "internal.h"
+
+namespace reindex {
+
+// Shared-memory staging of one tile: a vector per item (the key words, plus the old index for
+// the array-of-structures layouts) and, for S = 8 and 16, a separate old-index plane.
+template <int S>
+struct Stage;
+
+template <>
+struct Stage<4> {
+  static constexpr size_t bytes = (size_t)kSortTile * 8;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<4>& it) {
+    reinterpret_cast<uint2*>(sm)[p] = make_uint2(it.k[0], it.id);
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<4>& it) {
+    const uint2 v = reinterpret_cast<const uint2*>(sm)[p];
+    it.k[0] = v.x; it.id = v.y;
+  }
+};
+template <>
+struct Stage<12> {
+  static constexpr size_t bytes = (size_t)kSortTile * 16;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<12>& it) {
+    reinterpret_cast<uint4*>(sm)[p] = make_uint4(it.k[0], it.k[1], it.k[2], it.id);
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<12>& it) {
+    const uint4 v = reinterpret_cast<const uint4*>(sm)[p];
+    it.k[0] = v.x; it.k[1] = v.y; it.k[2] = v.z; it.id = v.w;
+  }
+};
+template <>
+struct Stage<8> {
+  static constexpr size_t bytes = (size_t)kSortTile * 12;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<8>& it) {
+    reinterpret_cast<uint2*>(sm)[p] = make_uint2(it.k[0], it.k[1]);
+    reinterpret_cast<uint32_t*>(sm + (size_t)kSortTile * 8)[p] = it.id;
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<8>& it) {
+    const uint2 v = reinterpret_cast<const uint2*>(sm)[p];
+    it.k[0] = v.x; it.k[1] = v.y;
+    it.id = reinterpret_cast<const uint32_t*>(sm + (size_t)kSortTile * 8)[p];
+  }
+};
+template <>
+struct Stage<16> {
+  static constexpr size_t bytes = (size_t)kSortTile * 20;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<16>& it) {
+    reinterpret_cast<uint4*>(sm)[p] = make_uint4(it.k[0], it.k[1], it.k[2], it.k[3]);
+    reinterpret_cast<uint32_t*>(sm + (size_t)kSortTile * 16)[p] = it.id;
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<16>& it) {
+    const uint4 v = reinterpret_cast<const uint4*>(sm)[p];
+    it.k[0] = v.x; it.k[1] = v.y; it.k[2] = v.z; it.k[3] = v.w;
+    it.id = reinterpret_cast<const uint32_t*>(sm + (size_t)kSortTile * 16)[p];
+  }
+};
+
+template <>
+struct Stage<20> {
+  static constexpr size_t bytes = (size_t)kSortTile * 24;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<20>& it) {
+    uint2* q = reinterpret_cast<uint2*>(sm) + 3 * p;
+    q[0] = make_uint2(it.k[0], it.k[1]);
+    q[1] = make_uint2(it.k[2], it.k[3]);
+    q[2] = make_uint2(it.k[4], it.id);
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<20>& it) {
+    const uint2* q = reinterpret_cast<const uint2*>(sm) + 3 * p;
+    const uint2 a = q[0], b = q[1], c = q[2];
+    it.k[0] = a.x; it.k[1] = a.y; it.k[2] = b.x; it.k[3] = b.y; it.k[4] = c.x; it.id = c.y;
+  }
+};
+
+constexpr int kSortWarps = kSortThreads / 32;
+
+template <int S>
+struct SortSmem {
+  static constexpr size_t stage = Stage<S>::bytes;
+  static constexpr size_t whist = (size_t)kSortWarps * kRadix * 4;
+  static constexpr size_t bytes = stage + whist + 2 * kRadix * 4 + 32 * 4;
+};
+
+// Mask of the lanes whose 8-bit digit equals this lane's (and whose validity matches).
+template <int kMode>
+__device__ __forceinline__ uint32_t match_digit(uint32_t dig, bool valid) {
+  if (kMode == kRankMatchAny) {
+    return __match_any_sync(0xffffffffu, valid ? dig : 0x100u);
+  } else {
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    if (!valid) peers = ~peers;
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const bool bit = (dig >> b) & 1u;
+      const uint32_t vote = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? vote : ~vote;
+    }
+    return peers;
+  }
+}
+
+}  // namespace reindex

@@ -1,8 +1,9 @@
 // Autotuner: picks, per device and vertex stride, the fastest of the library's kernel variants
 // for the caller's own mesh, by timing whole reindex_mesh_ws runs with CUDA events.
-//   knobs: radix-pass kernel (register-tiled, 4096-item tiles | TMA-pipelined through shared
-//          memory, 2048-4096-item tiles), digit matching (8 ballots | match.any), histogram
-//          method (uniform check | peel | match.any), grid shape (persistent | one CTA per tile)
+//   knobs: radix-pass kernel (register-tiled onesweep, 4096-item tiles | TMA-pipelined through
+//          shared memory, 2048-4096-item tiles | precounted tile offsets), digit matching (8 ballots | match.any), histogram
+//          method (uniform check | peel | match.any), grid shape (persistent | one CTA per tile),
+//          CTAs of the "tiles" scatter (one per tile | 1 or 4 waves striding over the tiles)
 // Coordinate descent: each knob in turn takes the value with the lowest median time while the
 // others stay fixed.  The choice applies to every later call on the device and, if the
 // environment variable REINDEX_TUNE_CACHE names a file, is appended to it so that a later
@@ -98,10 +99,11 @@ reindex_status reindex_autotune(const void* vtx, int64_t nVtx, int S, const int3
   LaunchCfg best = start;
   float best_ms = 0.f;
   reindex_status rs = timed(&best_ms);
-  const char* knobs[][3] = {{"sort=regs", "sort=pipe", nullptr},
-                            {"rank=ballot", "rank=match", nullptr},
-                            {"hist=uniform", "hist=peel", "hist=match"},
-                            {"grid=persist", "grid=tile", nullptr}};
+  const char* knobs[][4] = {{"sort=regs", "sort=pipe", "sort=tiles", nullptr},
+                            {"rank=ballot", "rank=match", nullptr, nullptr},
+                            {"hist=uniform", "hist=peel", "hist=match", nullptr},
+                            {"grid=persist", "grid=tile", nullptr, nullptr},
+                            {"swaves=tile", "swaves=1", "swaves=4", nullptr}};
   for (auto& knob : knobs) {
     if (rs != REINDEX_OK) break;
     for (const char* v : knob) {

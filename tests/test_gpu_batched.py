@@ -74,6 +74,21 @@ def test_batched_equals_oracle_per_mesh(rx, S):
     check_against_oracle(meshes, out_v, out_off, out_i)
 
 
+@pytest.mark.parametrize("spec", ["sort=regs,grid=persist", "sort=tiles,swaves=1", "sort=tiles,swaves=tile"])
+@pytest.mark.parametrize("S", [4, 16])
+def test_batched_sort_variants(rx, spec, S):
+    """The batched path sorts (S + 4)-byte keys with the variant configured for that key size."""
+    saved = rx.reindex_tuning_get(S + 4)
+    rx.reindex_tuning_set(S + 4, spec)
+    try:
+        rng = np.random.default_rng(300 + S)
+        meshes = random_meshes(rng, 29, S // 4, 3)
+        out_v, out_off, out_i = run_batched(rx, *concat(meshes))
+        check_against_oracle(meshes, out_v, out_off, out_i)
+    finally:
+        rx.reindex_tuning_set(S + 4, saved)
+
+
 def test_batched_equals_single_calls(rx):
     meshes = [(m.vtx, m.idx) for m in synth.batched_heightfield(24, seed=9, min_tris=64, max_tris=20_000)]
     out_v, out_off, out_i = run_batched(rx, *concat(meshes))

@@ -227,9 +227,15 @@ def test_host_buffer_variant(rx):
     np.testing.assert_array_equal(out_i.numpy().reshape(-1), oi)
 
 
-def test_profile_records_every_kernel(rx):
+SORT_KERNELS = {"regs": ["onesweep"], "tiles": ["tile_count", "tile_offsets", "tile_scatter"]}
+
+
+@pytest.mark.parametrize("sort", ["regs", "tiles"])
+def test_profile_records_every_kernel(rx, sort):
     m = synth.config_mesh(1)
     v, i = to_dev(m.vtx, m.idx)
+    saved = rx.reindex_tuning_get(12)
+    rx.reindex_tuning_set(12, f"sort={sort}")
     rx.profile_collect()
     rx.profile_enable(True)
     try:
@@ -237,13 +243,40 @@ def test_profile_records_every_kernel(rx):
         torch.cuda.synchronize()
     finally:
         rx.profile_enable(False)
+        rx.reindex_tuning_set(12, saved)
     recs = rx.profile_collect()
     names = [r["name"] for r in recs]
-    assert names.count("onesweep") == 12
-    assert set(names) == set(rx.KERNEL_NAMES) - {"seg_prepare", "seg_offsets"}
+    mine = SORT_KERNELS[sort]
+    for k in mine:
+        assert names.count(k) == 12
+    others = {k for ks in SORT_KERNELS.values() for k in ks} - set(mine)
+    assert set(names) == set(rx.KERNEL_NAMES) - {"seg_prepare", "seg_offsets"} - others
     # x and y are integers 0..256 as float32: their lowest byte is always zero -> skipped passes
-    sk = {r["digit"]: r["skipped"] for r in recs if r["name"] == "onesweep"}
+    sk = {r["digit"]: r["skipped"] for r in recs if r["name"] == mine[-1]}
     assert sk[8] and sk[4] and not sk[0]
+
+
+# Every radix-pass variant (and grid shape) must give the same bit-exact result.
+SORT_VARIANTS = ["sort=regs,rank=ballot,grid=persist", "sort=regs,rank=match,grid=tile",
+                 "sort=pipe,rank=ballot,grid=persist", "sort=tiles,rank=ballot,swaves=1",
+                 "sort=tiles,rank=match,swaves=tile", "sort=tiles,rank=ballot,swaves=4"]
+
+
+@pytest.mark.parametrize("spec", SORT_VARIANTS)
+@pytest.mark.parametrize("S", [4, 8, 12, 16, 20])
+def test_sort_variants_bit_exact(rx, spec, S):
+    saved = rx.reindex_tuning_get(S)
+    rx.reindex_tuning_set(S, spec)
+    try:
+        rng = np.random.default_rng(7000 + S + 100 * SORT_VARIANTS.index(spec))
+        for mode in ["random", "dups", "const"]:
+            for n, m in SIZES:
+                assert_parity(rx, *random_mesh(rng, n, m, S // 4, mode))
+        if S == 12:
+            mesh = synth.config_mesh(1)
+            assert assert_parity(rx, mesh.vtx, mesh.idx, 3) == mesh.expected_unique
+    finally:
+        rx.reindex_tuning_set(S, saved)
 
 
 def test_lookback_wait_runs_out_and_reports_timeout(rx):
