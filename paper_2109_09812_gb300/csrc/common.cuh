@@ -50,7 +50,10 @@ constexpr int64_t kMaxCount = (int64_t)kValMask;  // largest count a status word
 // Bounded spin: every wait on another CTA gives up after this many polls, records
 // REINDEX_ERR_TIMEOUT and publishes a (meaningless) prefix so that no successor waits forever.
 constexpr uint32_t kSpinLimit = 1u << 20;
-constexpr int kLookWindow = 16;  // predecessor status words fetched per look-back round (sort)
+// Single-counter look-back tables (compaction, head scan) keep each tile's status word in its own
+// kLbPad-word slot (one 128-byte line), so that the hundreds of CTAs polling recent tiles do not
+// all hit one L2 line (packed status words made both kernels about 1.5x slower).
+constexpr int kLbPad = 32;
 
 // Device-side error codes (same numbers as reindex_status).
 constexpr uint32_t kErrIndexRange = 4;
@@ -102,8 +105,8 @@ struct WsLayout {
     size_t o = 0;
     off_ctrl = o;        o += sizeof(Control);
     off_hist = o;        o = align_up(o + (size_t)P * kRadix * 4, 256);
-    off_lb_compact = o;  o = align_up(o + (size_t)tilesV * 4, 256);
-    off_lb_head = o;     o = align_up(o + (size_t)tilesH * 4, 256);
+    off_lb_compact = o;  o = align_up(o + (size_t)tilesV * 4 * kLbPad, 256);
+    off_lb_head = o;     o = align_up(o + (size_t)tilesH * 4 * kLbPad, 256);
     off_lb_sort = o;     o = align_up(o + (size_t)2 * tilesS * kRadix * 4, 256);
     off_bitmask = o;     o = align_up(o + (size_t)((n + 31) / 32) * 4, 256);
     zero_bytes = o;
@@ -125,8 +128,8 @@ struct WsLayout {
 struct WsPtrs {
   Control* ctrl;
   uint32_t* hist;        // [P][256]
-  uint32_t* lb_compact;  // [tilesV]
-  uint32_t* lb_head;     // [tilesH]
+  uint32_t* lb_compact;  // [tilesV * kLbPad]: status of tile q at q * kLbPad
+  uint32_t* lb_head;     // [tilesH * kLbPad]
   uint32_t* lb_sort;     // [2][tilesS][256]
   uint32_t* bitmask;     // [ceil(nVtx/32)]
   Plan* plan;
@@ -409,7 +412,8 @@ __device__ __forceinline__ uint32_t wait_status(const uint32_t* p, Control* c) {
   return s;
 }
 
-// Decoupled look-back over one counter per tile, done by one full warp: returns the exclusive
+// Decoupled look-back over one counter per tile (status of tile q at lb[q * kLbPad]), done by one
+// full warp: returns the exclusive
 // prefix of tile `tile` (> 0) in every lane.  Each round inspects the 32*W nearest predecessors
 // not yet accumulated (lane l: W consecutive ones), all loads in flight together, and stops at
 // the nearest one carrying an inclusive prefix.  (The nearest prefix is usually within 32
@@ -424,12 +428,12 @@ __device__ __forceinline__ uint32_t warp_lookback(const uint32_t* lb, int64_t ti
 #pragma unroll
     for (int i = 0; i < W; ++i) {
       const int64_t q = hi - (int64_t)lane * W - i;
-      s[i] = q >= 0 ? ld_relaxed(lb + q) : kFlagPre;  // before tile 0: prefix 0
+      s[i] = q >= 0 ? ld_relaxed(lb + q * kLbPad) : kFlagPre;  // before tile 0: prefix 0
     }
 #pragma unroll
     for (int i = 0; i < W; ++i) {
       const int64_t q = hi - (int64_t)lane * W - i;
-      if (q >= 0 && (s[i] & kFlagMask) == 0) s[i] = wait_status(lb + q, c);
+      if (q >= 0 && (s[i] & kFlagMask) == 0) s[i] = wait_status(lb + q * kLbPad, c);
     }
     int stop = W;  // nearest predecessor of this lane carrying an inclusive prefix
 #pragma unroll

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
     }
     if (w == 0 && tile != stall_tile) {
       uint32_t prefix = 0;
-      uint32_t* my = ws.lb_compact + tile;
+      uint32_t* my = ws.lb_compact + tile * kLbPad;
       if (tile == 0) {
         if (lane == 0) st_relaxed(my, kFlagPre | total);
       } else {

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsP
     }
     if (w == 0) {
       uint32_t prefix = 0;
-      uint32_t* my = ws.lb_head + tile;
+      uint32_t* my = ws.lb_head + tile * kLbPad;
       if (tile == 0) {
         if (lane == 0) st_relaxed(my, kFlagPre | total);
       } else {
