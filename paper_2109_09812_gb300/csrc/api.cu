@@ -21,7 +21,7 @@ namespace reindex {
 static std::mutex g_cfg_mu;
 static std::map<std::pair<int, int>, LaunchCfg> g_cfg;
 
-// Applies "sort=regs|pipe|tiles|auto,rank=ballot|match,hist=uniform|peel|match,grid=persist|tile,
+// Applies "sort=regs|pipe|tiles|auto,rank=ballot|match|vary,hist=uniform|peel|match,grid=persist|tile,
 // swaves=tile|1|4" (any subset, in any order).  Every variant computes the same result.
 void apply_tuning(LaunchCfg& c, const char* spec) {
   if (!spec) return;
@@ -33,6 +33,7 @@ void apply_tuning(LaunchCfg& c, const char* spec) {
   if (std::strstr(spec, "sort=auto")) c.sort_kernel = kSortAuto;
   if (std::strstr(spec, "rank=match")) c.rank_mode = kRankMatchAny;
   if (std::strstr(spec, "rank=ballot")) c.rank_mode = kRankBallot;
+  if (std::strstr(spec, "rank=vary")) c.rank_mode = kRankBallotVary;
   if (std::strstr(spec, "hist=uniform")) c.hist_mode = kHistUniform;
   if (std::strstr(spec, "hist=peel")) c.hist_mode = kHistPeel;
   if (std::strstr(spec, "hist=match")) c.hist_mode = kHistMatchAny;
@@ -44,7 +45,7 @@ void apply_tuning(LaunchCfg& c, const char* spec) {
 std::string describe_tuning(const LaunchCfg& c) {
   const char* sorts[] = {"sort=regs", "sort=pipe", "sort=tiles", "sort=auto"};
   std::string d = sorts[c.sort_kernel];
-  d += c.rank_mode == kRankMatchAny ? ",rank=match" : ",rank=ballot";
+  d += c.rank_mode == kRankMatchAny ? ",rank=match" : (c.rank_mode == kRankBallotVary ? ",rank=vary" : ",rank=ballot");
   d += c.hist_mode == kHistMatchAny ? ",hist=match" : (c.hist_mode == kHistPeel ? ",hist=peel" : ",hist=uniform");
   d += c.grid_per_tile ? ",grid=tile" : ",grid=persist";
   d += c.scatter_waves ? ",swaves=" + std::to_string(c.scatter_waves) : std::string(",swaves=tile");
@@ -65,6 +66,9 @@ static LaunchCfg& launch_cfg_locked(int S) {
   c.occ_sort_pipe = occupancy_sort_pipe(S);
   c.occ_tiles = occupancy_tiles(S);
   if (c.occ_sort_pipe < 1 && c.sort_kernel == kSortPipe) c.sort_kernel = kSortRegs;  // too little shared memory
+  // 16- and 20-byte keys rank faster without the ballots of constant digit bits (register pressure
+  // of the wider items); 4- to 12-byte keys with all eight (measured on GB300)
+  if (S >= 16) c.rank_mode = kRankBallotVary;
   // Defaults are the variants measured fastest on GB300; a tuning cache (written by the
   // autotuner) and then REINDEX_TUNE override them.
   apply_tuning(c, tuning_from_cache(dev, c.sms, S).c_str());

@@ -29,11 +29,12 @@ constexpr int kMaxDigits = 20;             // 20-byte keys (16-byte vertices + a
 constexpr int kSortRegs = 0;      // radix pass with items in registers (k_onesweep)
 constexpr int kSortPipe = 1;      // radix pass pipelined through shared memory (k_onesweep_pipe)
 constexpr int kSortTiles = 2;     // radix pass with precounted tile offsets (k_radix_tiles.cu)
-constexpr int kSortAuto = 3;      // per call: kSortTiles for large meshes with keys of <= 12 bytes,
-                                  // else kSortRegs (the faster of the two there on GB300)
+constexpr int kSortAuto = 3;      // per call: kSortTiles for large meshes, else kSortRegs (the faster
+                                  // of the two on GB300 for each)
 constexpr int64_t kTilesMinItems = 1 << 21;  // below this, launch count favours kSortRegs
 constexpr int kRankBallot = 0;    // digit peers from 8 ballots
 constexpr int kRankMatchAny = 1;  // digit peers from match.any
+constexpr int kRankBallotVary = 2;  // ballots on the digit bits that vary only
 constexpr int kHistUniform = 0;   // histogram: one atomic per warp when the digit is warp-uniform
 constexpr int kHistPeel = 1;      // histogram: the first lane's digit group counted with one atomic
 constexpr int kHistMatchAny = 2;  // histogram: one atomic per distinct digit (match.any)
@@ -82,6 +83,8 @@ struct Plan {                // written by the sort-plan kernel
   int8_t next[kMaxDigits];   // the next non-trivial digit after d, or -1
   int8_t first;              // the first non-trivial digit, or -1
   uint8_t pad[11];
+  uint8_t vary[kMaxDigits];  // bits of digit d that differ between items (the others are constant)
+  uint8_t pad2[12];
   uint32_t base[kMaxDigits][kRadix];  // exclusive prefix of the digit histogram
 };
 

@@ -19,15 +19,15 @@ struct LaunchCfg {
   int occ_sort_pipe = 0;
   int occ_tiles = 0;
   int sort_kernel = kSortAuto;  // kSortRegs (k_onesweep), kSortPipe (k_onesweep_pipe), kSortTiles, kSortAuto
-  int rank_mode = kRankBallot;  // onesweep digit matching (kRank*)
+  int rank_mode = kRankBallot;  // digit matching of the radix passes (kRank*; onesweep: ballot or match)
   int hist_mode = kHistUniform; // compaction histogram method (kHist*)
   int grid_per_tile = 0;        // 1: one CTA per tile; 0: persistent CTAs (SMs x occupancy)
   int scatter_waves = 0;        // "tiles" scatter: 0 one CTA per tile, else CTAs = waves x SMs x occupancy
 };
 
 // The configuration for one call: kSortAuto resolved for S-byte keys and up to Umax items.
-inline LaunchCfg resolve_cfg(LaunchCfg c, int S, int64_t Umax) {
-  if (c.sort_kernel == kSortAuto) c.sort_kernel = (S <= 12 && Umax >= kTilesMinItems) ? kSortTiles : kSortRegs;
+inline LaunchCfg resolve_cfg(LaunchCfg c, int /*S*/, int64_t Umax) {
+  if (c.sort_kernel == kSortAuto) c.sort_kernel = Umax >= kTilesMinItems ? kSortTiles : kSortRegs;
   return c;
 }
 

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(kSortThreads, S >= 20 ? 1 : 2) k_onesweep(WsPt
   const bool digit_thread = t < kRadix;  // threads 0..255 own digit value t
   if (digit_thread) gbase[t] = plan->base[d][t];
   const int shift = (d & 3) * 8;
+  const uint32_t vary = plan->vary[d];
   uint32_t* wh = whist + w * kRadix;
   const int wbase = w * 32 * kSortIpt;
 
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(kSortThreads, S >= 20 ? 1 : 2) k_onesweep(WsPt
     for (int r = 0; r < kSortIpt; ++r) {
       const bool valid = wbase + r * 32 + lane < n;
       const uint32_t dig = (it[r].k[kWord] >> shift) & 0xFFu;
-      const uint32_t peers = match_digit<kMode>(dig, valid);
+      const uint32_t peers = match_digit<kMode>(dig, valid, vary);
       const uint32_t lt = peers & lanemask_lt();
       const int leader = __ffs(peers) - 1;
       uint32_t old = 0;

@@ -31,11 +31,14 @@ constexpr uint32_t kSrcPlane8 = 0, kSrcPlane16 = 1, kSrcKeys = 2;  // where k_ti
 // Per-pass values of the plan, read once by thread 0 and shared, together with the error word
 // (so that every thread of the CTA takes the same early exit).
 struct PassInfo {
-  uint32_t U, run, src, next, count_src;
+  uint32_t U, run, src, next, count_src, vary;
 };
 
+// A skipped pass exits without a barrier: every thread reads the skip flag through the read-only
+// cache (written by an earlier kernel), so the CTAs of a skipped pass cost almost nothing.
 __device__ __forceinline__ PassInfo pass_info(const WsPtrs& ws, int d) {
   __shared__ PassInfo s_pi;
+  if (__ldg(ws.plan->skip + d)) return PassInfo{0, 0, 0, 0, 0, 0};
   if (threadIdx.x == 0) {
     const Plan* plan = ws.plan;
     const uint32_t skip = plan->skip[d], U = plan->U, src = plan->src[d];
@@ -46,6 +49,7 @@ __device__ __forceinline__ PassInfo pass_info(const WsPtrs& ws, int d) {
     s_pi.src = src;
     s_pi.next = (uint32_t)(int32_t)next;
     s_pi.count_src = d != first ? kSrcPlane8 : (d <= 1 ? kSrcPlane16 : kSrcKeys);
+    s_pi.vary = plan->vary[d];
   }
   __syncthreads();
   const PassInfo pi = s_pi;
@@ -154,37 +158,26 @@ constexpr int kOffRegs = 8;   // counts a thread keeps in registers between the 
 constexpr int kOffBatch = 8;  // loads issued together per thread (columns longer than 8192 tiles)
 
 // One CTA per digit value v: cnt[v][tile] -> (items with a digit below v) + sum of
-// cnt[v][0 .. tile).
+// cnt[v][0 .. tile).  The column and the digit totals are loaded together, then one barrier.
 __global__ void __launch_bounds__(kOffThreads) k_tile_offsets(WsPtrs ws, int d) {
   __shared__ uint32_t s_warp[kOffThreads / 32];
-  __shared__ uint32_t s_base;
+  __shared__ uint32_t s_below[kRadix / 32];
   const PassInfo pi = pass_info(ws, d);
   if (!pi.run) return;
   const uint32_t ntiles = (pi.U + kSortTile - 1) / kSortTile;
   const int v = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
   uint32_t* col = tile_counts(ws, v);
-  // digit start: the totals of the smaller digit values (threads 0..255 hold one each)
-  {
-    uint32_t x = (t < v) ? ws.hist[d * kRadix + t] : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) s_warp[w] = x;
-    __syncthreads();
-    if (t == 0) {
-      uint32_t b = 0;
-      for (int q = 0; q < kRadix / 32; ++q) b += s_warp[q];
-      s_base = b;
-    }
-    __syncthreads();
-  }
   const uint32_t chunk = (ntiles + kOffThreads - 1) / kOffThreads;
   const uint32_t lo = min((uint32_t)t * chunk, ntiles), hi = min(lo + chunk, ntiles);
-  uint32_t a[kOffRegs];
-  uint32_t sum = 0;
   const bool in_regs = chunk <= kOffRegs;
+  uint32_t a[kOffRegs];
   if (in_regs) {
 #pragma unroll
     for (int i = 0; i < kOffRegs; ++i) a[i] = lo + i < hi ? col[lo + i] : 0u;
+  }
+  uint32_t below = (t < v) ? ws.hist[d * kRadix + t] : 0u;  // items whose digit is smaller than v
+  uint32_t sum = 0;
+  if (in_regs) {
 #pragma unroll
     for (int i = 0; i < kOffRegs; ++i) sum += a[i];
   } else {
@@ -196,11 +189,15 @@ __global__ void __launch_bounds__(kOffThreads) k_tile_offsets(WsPtrs ws, int d) 
       for (int i = 0; i < kOffBatch; ++i) sum += b[i];
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
   const uint32_t incl = warp_incl_scan(sum);
-  __syncthreads();  // s_warp is reused
   if (lane == 31) s_warp[w] = incl;
+  if (lane == 0 && w < kRadix / 32) s_below[w] = below;
   __syncthreads();
-  uint32_t run = s_base + incl - sum;
+  uint32_t run = incl - sum;
+#pragma unroll
+  for (int q = 0; q < kRadix / 32; ++q) run += s_below[q];
   for (int q = 0; q < w; ++q) run += s_warp[q];
   if (in_regs) {
 #pragma unroll
@@ -279,7 +276,7 @@ __global__ void __launch_bounds__(kSortThreads, S >= 20 ? 1 : 2) k_tile_scatter(
     for (int r = 0; r < kSortIpt; ++r) {
       const bool valid = wbase + r * 32 + lane < n;
       const uint32_t dig = (it[r].k[kWord] >> shift) & 0xFFu;
-      const uint32_t peers = match_digit<kMode>(dig, valid);
+      const uint32_t peers = match_digit<kMode>(dig, valid, pi.vary);
       const uint32_t lt = peers & lanemask_lt();
       const int leader = __ffs(peers) - 1;
       uint32_t old = 0;
@@ -370,7 +367,7 @@ static int occ_mode() {
 
 template <int S>
 static int occ() {
-  return min(occ_mode<S, kRankBallot>(), occ_mode<S, kRankMatchAny>());
+  return min(occ_mode<S, kRankBallot>(), min(occ_mode<S, kRankMatchAny>(), occ_mode<S, kRankBallotVary>()));
 }
 
 int occupancy_tiles(int S) {
@@ -420,6 +417,8 @@ template <int S>
 static void scatter_s(int g, int digit, WsPtrs ws, int mode, cudaStream_t st) {
   if (mode == kRankMatchAny)
     scatter_mode<S, kRankMatchAny>(g, digit, ws, st);
+  else if (mode == kRankBallotVary)
+    scatter_mode<S, kRankBallotVary>(g, digit, ws, st);
   else
     scatter_mode<S, kRankBallot>(g, digit, ws, st);
 }

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int
 // from_masks: trivial digits come from the key bit masks (no upfront histograms were taken).
 __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from_masks) {
   __shared__ uint32_t s_warp[kRadix / 32];
+  __shared__ uint32_t s_or[kRadix / 32], s_and[kRadix / 32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const uint32_t U = ws.ctrl->U;
   Plan* plan = ws.plan;
@@ -75,12 +76,22 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from
     const uint32_t c = ws.hist[d * kRadix + t];
     // A digit whose value is the same for all U items: that pass is the identity.
     int trivial;
+    uint32_t vary;  // digit bits that are not the same in every item
     if (from_masks) {
       const int q = P / 4 - 1 - (d >> 2);
-      trivial = (((ws.ctrl->kor[q] & ws.ctrl->knand[q]) >> ((d & 3) * 8)) & 0xFFu) == 0;
+      vary = ((ws.ctrl->kor[q] & ws.ctrl->knand[q]) >> ((d & 3) * 8)) & 0xFFu;
+      trivial = vary == 0;
       __syncthreads();
     } else {
+      // from the histogram: OR and AND over the digit values that occur
+      const uint32_t o = __reduce_or_sync(0xffffffffu, c ? (uint32_t)t : 0u);
+      const uint32_t a = __reduce_and_sync(0xffffffffu, c ? (uint32_t)t : 0xFFu);
+      if (lane == 0) s_or[w] = o, s_and[w] = a;
       trivial = __syncthreads_or(c == U);
+      uint32_t oo = 0, aa = 0xFFu;
+      for (int k = 0; k < kRadix / 32; ++k) oo |= s_or[k], aa &= s_and[k];
+      vary = (oo ^ aa) & 0xFFu;
+      __syncthreads();  // s_or / s_and are rewritten for the next digit
     }
     const uint32_t incl = warp_incl_scan(c);
     if (lane == 31) s_warp[w] = incl;
@@ -93,6 +104,7 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from
       plan->skip[d] = (uint8_t)trivial;
       plan->src[d] = (uint8_t)sel;
       plan->area[d] = (uint8_t)(q & 1u);
+      plan->vary[d] = (uint8_t)vary;
     }
     if (!trivial) {
       sel ^= 1u;

@@ -86,9 +86,12 @@ struct SortSmem {
   static constexpr size_t bytes = stage + whist + 2 * kRadix * 4 + 32 * 4;
 };
 
-// Mask of the lanes whose 8-bit digit equals this lane's (and whose validity matches).
+// Mask of the lanes whose 8-bit digit equals this lane's (and whose validity matches), from
+// match.any, from 8 ballots (one per digit bit), or (kRankBallotVary) from ballots on the bits in
+// `vary` only: the digit bits that differ between items anywhere in the array (the others are
+// equal in every valid lane; the branches are warp-uniform).
 template <int kMode>
-__device__ __forceinline__ uint32_t match_digit(uint32_t dig, bool valid) {
+__device__ __forceinline__ uint32_t match_digit(uint32_t dig, bool valid, uint32_t vary) {
   if (kMode == kRankMatchAny) {
     return __match_any_sync(0xffffffffu, valid ? dig : 0x100u);
   } else {
@@ -96,6 +99,7 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t dig, bool valid) {
     if (!valid) peers = ~peers;
 #pragma unroll
     for (int b = 0; b < kRadixBits; ++b) {
+      if (kMode == kRankBallotVary && !((vary >> b) & 1u)) continue;
       const bool bit = (dig >> b) & 1u;
       const uint32_t vote = __ballot_sync(0xffffffffu, bit);
       peers &= bit ? vote : ~vote;

@@ -100,7 +100,7 @@ reindex_status reindex_autotune(const void* vtx, int64_t nVtx, int S, const int3
   float best_ms = 0.f;
   reindex_status rs = timed(&best_ms);
   const char* knobs[][4] = {{"sort=regs", "sort=pipe", "sort=tiles", nullptr},
-                            {"rank=ballot", "rank=match", nullptr, nullptr},
+                            {"rank=ballot", "rank=match", "rank=vary", nullptr},
                             {"hist=uniform", "hist=peel", "hist=match", nullptr},
                             {"grid=persist", "grid=tile", nullptr, nullptr},
                             {"swaves=tile", "swaves=1", "swaves=4", nullptr}};
