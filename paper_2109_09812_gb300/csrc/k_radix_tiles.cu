@@ -153,68 +153,63 @@ __global__ void __launch_bounds__(kThreads, 4) k_tile_count(WsPtrs ws, int d) {
   if (total) atomicAdd(ws.hist + d * kRadix + t, total);
 }
 
-constexpr int kOffThreads = 1024;
-constexpr int kOffRegs = 8;   // counts a thread keeps in registers between the two sweeps
-constexpr int kOffBatch = 8;  // loads issued together per thread (columns longer than 8192 tiles)
+constexpr int kOffThreads = 512;
+constexpr int kOffWarps = kOffThreads / 32;
+constexpr int kOffBatch = 8;  // rows of 32 counts loaded together per warp
 
 // One CTA per digit value v: cnt[v][tile] -> (items with a digit below v) + sum of
-// cnt[v][0 .. tile).  The column and the digit totals are loaded together, then one barrier.
-__global__ void __launch_bounds__(kOffThreads) k_tile_offsets(WsPtrs ws, int d) {
-  __shared__ uint32_t s_warp[kOffThreads / 32];
+// cnt[v][0 .. tile).  Warp w owns a contiguous segment of the column and walks it in rows of 32
+// consecutive tiles (coalesced): a first sweep sums the segment, one barrier gives the segment
+// starts, and a second sweep scans each row and writes the offsets.
+__global__ void __launch_bounds__(kOffThreads, 2) k_tile_offsets(WsPtrs ws, int d) {
+  __shared__ uint32_t s_seg[kOffWarps];
   __shared__ uint32_t s_below[kRadix / 32];
   const PassInfo pi = pass_info(ws, d);
   if (!pi.run) return;
   const uint32_t ntiles = (pi.U + kSortTile - 1) / kSortTile;
   const int v = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
   uint32_t* col = tile_counts(ws, v);
-  const uint32_t chunk = (ntiles + kOffThreads - 1) / kOffThreads;
-  const uint32_t lo = min((uint32_t)t * chunk, ntiles), hi = min(lo + chunk, ntiles);
-  const bool in_regs = chunk <= kOffRegs;
-  uint32_t a[kOffRegs];
-  if (in_regs) {
-#pragma unroll
-    for (int i = 0; i < kOffRegs; ++i) a[i] = lo + i < hi ? col[lo + i] : 0u;
-  }
+  const uint32_t rows = (ntiles + 32 * kOffWarps - 1) / (32 * kOffWarps);  // rows of 32 per warp
+  const uint32_t seg0 = (uint32_t)w * rows * 32;
   uint32_t below = (t < v) ? ws.hist[d * kRadix + t] : 0u;  // items whose digit is smaller than v
-  uint32_t sum = 0;
-  if (in_regs) {
+  uint32_t acc = 0;
+  for (uint32_t r0 = 0; r0 < rows; r0 += kOffBatch) {
+    uint32_t x[kOffBatch];
 #pragma unroll
-    for (int i = 0; i < kOffRegs; ++i) sum += a[i];
-  } else {
-    for (uint32_t q0 = lo; q0 < hi; q0 += kOffBatch) {
-      uint32_t b[kOffBatch];
-#pragma unroll
-      for (int i = 0; i < kOffBatch; ++i) b[i] = q0 + i < hi ? col[q0 + i] : 0u;
-#pragma unroll
-      for (int i = 0; i < kOffBatch; ++i) sum += b[i];
+    for (int i = 0; i < kOffBatch; ++i) {
+      const uint32_t q = seg0 + (r0 + i) * 32 + lane;
+      x[i] = (r0 + i < rows && q < ntiles) ? col[q] : 0u;
     }
+#pragma unroll
+    for (int i = 0; i < kOffBatch; ++i) acc += x[i];
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
-  const uint32_t incl = warp_incl_scan(sum);
-  if (lane == 31) s_warp[w] = incl;
-  if (lane == 0 && w < kRadix / 32) s_below[w] = below;
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    below += __shfl_xor_sync(0xffffffffu, below, o);
+  }
+  if (lane == 0) {
+    s_seg[w] = acc;
+    if (w < kRadix / 32) s_below[w] = below;
+  }
   __syncthreads();
-  uint32_t run = incl - sum;
+  uint32_t carry = 0;
 #pragma unroll
-  for (int q = 0; q < kRadix / 32; ++q) run += s_below[q];
-  for (int q = 0; q < w; ++q) run += s_warp[q];
-  if (in_regs) {
+  for (int q = 0; q < kRadix / 32; ++q) carry += s_below[q];
+  for (int q = 0; q < w; ++q) carry += s_seg[q];
+  for (uint32_t r0 = 0; r0 < rows; r0 += kOffBatch) {
+    uint32_t x[kOffBatch];
 #pragma unroll
-    for (int i = 0; i < kOffRegs; ++i) {
-      if (lo + i < hi) col[lo + i] = run;
-      run += a[i];
+    for (int i = 0; i < kOffBatch; ++i) {
+      const uint32_t q = seg0 + (r0 + i) * 32 + lane;
+      x[i] = (r0 + i < rows && q < ntiles) ? col[q] : 0u;
     }
-  } else {
-    for (uint32_t q0 = lo; q0 < hi; q0 += kOffBatch) {
-      uint32_t b[kOffBatch];
 #pragma unroll
-      for (int i = 0; i < kOffBatch; ++i) b[i] = q0 + i < hi ? col[q0 + i] : 0u;
-#pragma unroll
-      for (int i = 0; i < kOffBatch; ++i) {
-        if (q0 + i < hi) col[q0 + i] = run;
-        run += b[i];
-      }
+    for (int i = 0; i < kOffBatch; ++i) {
+      const uint32_t q = seg0 + (r0 + i) * 32 + lane;
+      const uint32_t incl = warp_incl_scan(x[i]);
+      if (r0 + i < rows && q < ntiles) col[q] = carry + incl - x[i];
+      carry += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
 }
