@@ -582,7 +582,12 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = load_peaks()
     avg_ms = sum(sweeps) / len(sweeps) if sweeps else float("nan")
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    per_pass = {}
+    for r in recs:
+        if r["name"] == kname and not r["skipped"]:
+            per_pass.setdefault(r["digit"], []).append(r["ms"])
     roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "per_pass_ms": {d: round(sum(v) / len(v), 4) for d, v in sorted(per_pass.items())},
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                 "traffic": ncu_traffic(kname, args.workload), "algorithmic_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": avg_ms, "passes_per_step": len(sweeps) / args.steps}

@@ -82,7 +82,7 @@ const char* reindex_status_string(reindex_status s);
 
 /* Bytes of device workspace reindex_mesh_ws needs for a mesh of this size (Section 3.6 notes
  * the method needs temporary memory comparable to the data: here two copies of the (key,
- * old index) items, two bytes per item for radix digits, one uint32 per input vertex, a bit
+ * old index) items, one byte per item for radix digits, one uint32 per input vertex, a bit
  * per input vertex and small look-back and histogram tables).  Returns 0 for unsupported
  * arguments. */
 size_t reindex_workspace_size(int64_t nVtx, int vtxStrideBytes, int64_t nElem, int idxPerElem);
@@ -317,7 +317,8 @@ typedef enum {
   REINDEX_K_TILE_COUNT = 10,   /* step 3, "tiles" variant: per-tile digit counts */
   REINDEX_K_TILE_OFFSETS = 11, /* step 3, "tiles" variant: tile offsets per digit */
   REINDEX_K_TILE_SCATTER = 12, /* step 3, "tiles" variant: the pass's data movement */
-  REINDEX_K_COUNT = 13
+  REINDEX_K_KEY_MASKS = 13,    /* "tiles" variant: which key bits vary over the used vertices */
+  REINDEX_K_COUNT = 14
 } reindex_kernel_id;
 
 void reindex_profile_enable(int on);

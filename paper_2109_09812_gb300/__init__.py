@@ -31,7 +31,7 @@ REINDEX_ERR_CUDA = 6
 REINDEX_ERR_INTERNAL = 7
 
 KERNEL_NAMES = ["clear", "used_flags", "compact_hist", "sort_plan", "onesweep", "head_scan", "remap", "finalize",
-                "seg_prepare", "seg_offsets", "tile_count", "tile_offsets", "tile_scatter"]
+                "seg_prepare", "seg_offsets", "tile_count", "tile_offsets", "tile_scatter", "key_masks"]
 
 # Symbols declared in include/reindex.h (checked by the ABI test).
 EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "reindex_mesh_ws",

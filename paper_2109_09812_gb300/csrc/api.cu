@@ -22,7 +22,7 @@ static std::mutex g_cfg_mu;
 static std::map<std::pair<int, int>, LaunchCfg> g_cfg;
 
 // Applies "sort=regs|pipe|tiles|auto,rank=ballot|match|vary,hist=uniform|peel|match,grid=persist|tile,
-// swaves=tile|1|4" (any subset, in any order).  Every variant computes the same result.
+// swaves=tile|1|4,pack=auto|on|off" (any subset, in any order).  Every variant computes the same result.
 void apply_tuning(LaunchCfg& c, const char* spec) {
   if (!spec) return;
   if (std::strstr(spec, "grid=tile")) c.grid_per_tile = 1;
@@ -40,6 +40,9 @@ void apply_tuning(LaunchCfg& c, const char* spec) {
   if (std::strstr(spec, "swaves=tile")) c.scatter_waves = 0;
   if (std::strstr(spec, "swaves=1")) c.scatter_waves = 1;
   if (std::strstr(spec, "swaves=4")) c.scatter_waves = 4;
+  if (std::strstr(spec, "pack=on")) c.pack_keys = 1;
+  if (std::strstr(spec, "pack=off")) c.pack_keys = 0;
+  if (std::strstr(spec, "pack=auto")) c.pack_keys = -1;
 }
 
 std::string describe_tuning(const LaunchCfg& c) {
@@ -49,6 +52,7 @@ std::string describe_tuning(const LaunchCfg& c) {
   d += c.hist_mode == kHistMatchAny ? ",hist=match" : (c.hist_mode == kHistPeel ? ",hist=peel" : ",hist=uniform");
   d += c.grid_per_tile ? ",grid=tile" : ",grid=persist";
   d += c.scatter_waves ? ",swaves=" + std::to_string(c.scatter_waves) : std::string(",swaves=tile");
+  d += c.pack_keys < 0 ? ",pack=auto" : (c.pack_keys ? ",pack=on" : ",pack=off");
   return d;
 }
 
@@ -224,13 +228,24 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
     prof::Scope s(REINDEX_K_USED_FLAGS, -1, st);
     REINDEX_TRY(launch_used_flags(idx, M, nVtx, p, c, st));
   }
-  {
+  if (c.sort_kernel == kSortTiles && c.pack_keys) {  // bit masks -> plan (key packing) -> compaction
+    {
+      prof::Scope s(REINDEX_K_KEY_MASKS, -1, st);
+      REINDEX_TRY(launch_key_masks(S, vtx, nVtx, p, c, nullptr, st));
+    }
+    {
+      prof::Scope s(REINDEX_K_SORT_PLAN, -1, st);
+      REINDEX_TRY(launch_sort_plan(S, p, true, true, st));
+    }
     prof::Scope s(REINDEX_K_COMPACT, -1, st);
     REINDEX_TRY(launch_compact(S, vtx, nVtx, p, L.tilesV, c, nullptr, st));
-  }
-  {
+  } else {  // compaction (upfront histograms, or key bit masks) -> plan
+    {
+      prof::Scope s(REINDEX_K_COMPACT, -1, st);
+      REINDEX_TRY(launch_compact(S, vtx, nVtx, p, L.tilesV, c, nullptr, st));
+    }
     prof::Scope s(REINDEX_K_SORT_PLAN, -1, st);
-    REINDEX_TRY(launch_sort_plan(S, p, c.sort_kernel == kSortTiles, st));
+    REINDEX_TRY(launch_sort_plan(S, p, c.sort_kernel == kSortTiles, false, st));
   }
   const uint8_t* skip = prof::skip_buffer(p.plan, st);
   for (int d = 0; d < L.P; ++d) REINDEX_TRY(sort_pass(S, d, p, c, st, skip));
@@ -270,7 +285,7 @@ static reindex_status run_batched(const void* vtx, int64_t nVtx, int S, const in
                                   int64_t* outOff, int32_t* out_idx, void* ws, const SegLayout& SL,
                                   cudaStream_t st) {
   const LaunchCfg cS = launch_cfg(S);
-  const LaunchCfg c = resolve_cfg(launch_cfg(S + 4), S + 4, SL.L.Umax);
+  const LaunchCfg c = resolve_cfg(launch_cfg(S + 4), S + 4, SL.L.Umax, true);
   const WsPtrs p = ws_ptrs(ws, SL.L);
   unsigned char* b = static_cast<unsigned char*>(ws);
   SegArgs seg;
@@ -295,15 +310,27 @@ static reindex_status run_batched(const void* vtx, int64_t nVtx, int S, const in
     prof::Scope sc(REINDEX_K_USED_FLAGS, -1, st);
     REINDEX_TRY(launch_seg_flags(idx, out_idx, M, seg, p, c, st));
   }
-  {
+  LaunchCfg cc = cS;  // the sort (configured for S + 4) decides whether histograms are taken
+  cc.sort_kernel = c.sort_kernel;
+  cc.pack_keys = c.pack_keys;
+  if (c.sort_kernel == kSortTiles && c.pack_keys) {  // bit masks -> plan (key packing) -> compaction
+    {
+      prof::Scope sc(REINDEX_K_KEY_MASKS, -1, st);
+      REINDEX_TRY(launch_key_masks(S, vtx, nVtx, p, cc, &seg, st));
+    }
+    {
+      prof::Scope sc(REINDEX_K_SORT_PLAN, -1, st);
+      REINDEX_TRY(launch_sort_plan(S + 4, p, true, true, st));
+    }
     prof::Scope sc(REINDEX_K_COMPACT, -1, st);
-    LaunchCfg cc = cS;  // the sort (configured for S + 4) decides whether histograms are taken
-    cc.sort_kernel = c.sort_kernel;
     REINDEX_TRY(launch_compact(S, vtx, nVtx, p, SL.L.tilesV, cc, &seg, st));
-  }
-  {
+  } else {  // compaction (upfront histograms, or key bit masks) -> plan
+    {
+      prof::Scope sc(REINDEX_K_COMPACT, -1, st);
+      REINDEX_TRY(launch_compact(S, vtx, nVtx, p, SL.L.tilesV, cc, &seg, st));
+    }
     prof::Scope sc(REINDEX_K_SORT_PLAN, -1, st);
-    REINDEX_TRY(launch_sort_plan(S + 4, p, c.sort_kernel == kSortTiles, st));
+    REINDEX_TRY(launch_sort_plan(S + 4, p, c.sort_kernel == kSortTiles, false, st));
   }
   const uint8_t* skip = prof::skip_buffer(p.plan, st);
   for (int d = 0; d < S + 4; ++d) REINDEX_TRY(sort_pass(S + 4, d, p, c, st, skip));
@@ -636,7 +663,7 @@ const char* reindex_kernel_name(int kernel) {
   static const char* names[REINDEX_K_COUNT] = {"clear",     "used_flags", "compact_hist", "sort_plan",
                                                "onesweep",  "head_scan",  "remap",        "finalize",
                                                "seg_prepare", "seg_offsets", "tile_count", "tile_offsets",
-                                               "tile_scatter"};
+                                               "tile_scatter", "key_masks"};
   return (kernel >= 0 && kernel < REINDEX_K_COUNT) ? names[kernel] : "unknown";
 }
 

@@ -38,7 +38,8 @@ constexpr int kRankBallotVary = 2;  // ballots on the digit bits that vary only
 constexpr int kHistUniform = 0;   // histogram: one atomic per warp when the digit is warp-uniform
 constexpr int kHistPeel = 1;      // histogram: the first lane's digit group counted with one atomic
 constexpr int kHistMatchAny = 2;  // histogram: one atomic per distinct digit (match.any)
-constexpr int kHistNone = 3;      // no histograms: key bit masks and the low-16-bit plane instead
+constexpr int kHistNone = 3;      // no histograms: packed keys and the first pass's digit plane instead
+constexpr int kHistMasks = 4;     // no histograms: key bit masks and the plane of key byte 0 instead
                                   // (the "tiles" sort counts digits per pass itself)
 
 // Look-back status word: 2-bit flag + 30-bit count.
@@ -74,6 +75,28 @@ struct Control {             // zeroed at the start of every call
 };
 static_assert(sizeof(Control) == 256, "Control block is one 256-byte line");
 
+// Key packing for the "tiles" sort.  Bits that are equal in every item do not affect the order,
+// so the compaction can pack the varying bits of each key (runs of consecutive bits, least
+// significant first) into the low bits of the key, and the radix passes sort byte digits of that
+// packed key: fewer passes when many bits are constant (integer coordinates, exponent bits, the
+// high bytes of a mesh id).  Packed keys are equal exactly when the keys are; the head scan
+// restores the keys it writes out.
+constexpr int kMaxPackRuns = 16;
+struct KeyPack {
+  uint8_t on;                      // 1: the keys are packed
+  uint8_t nbits;                   // varying bits in all
+  uint8_t nruns;                   // runs, least significant first
+  uint8_t word[kMaxPackRuns];      // key word of run r (word 0 is the most significant)
+  uint8_t shift[kMaxPackRuns];     // lowest bit of the run within that word
+  uint8_t len[kMaxPackRuns];       // run length in bits
+  uint8_t pos[kMaxPackRuns];       // where the run starts in the packed key
+  uint8_t simple;                  // 1: at most one run per word (wshift / wlen describe them)
+  uint8_t wshift[kMaxDigits / 4];  // word q's run: lowest bit
+  uint8_t wlen[kMaxDigits / 4];    //               and length (0: no varying bit)
+  uint8_t pad[2];
+};
+static_assert(sizeof(KeyPack) == 80, "KeyPack layout");
+
 struct Plan {                // written by the sort-plan kernel
   uint32_t U;
   uint32_t final_sel;        // 0: sorted items end in buffer A, 1: in buffer B
@@ -82,9 +105,13 @@ struct Plan {                // written by the sort-plan kernel
   uint8_t area[kMaxDigits];  // which of the two look-back areas the pass uses
   int8_t next[kMaxDigits];   // the next non-trivial digit after d, or -1
   int8_t first;              // the first non-trivial digit, or -1
-  uint8_t pad[11];
+  uint8_t plane_first;       // tiles sort: the compaction's digit plane holds the first pass's digit
+                             // (else key byte 0)
+  uint8_t pad[10];
   uint8_t vary[kMaxDigits];  // bits of digit d that differ between items (the others are constant)
   uint8_t pad2[12];
+  KeyPack pack;                      // packing of the keys (pack.on == 0: not packed)
+  uint32_t kconst[kMaxDigits / 4];   // values of the constant key bits (to restore packed keys)
   uint32_t base[kMaxDigits][kRadix];  // exclusive prefix of the digit histogram
 };
 
@@ -122,7 +149,7 @@ struct WsLayout {
     off_itemsA = o;      o += items_bytes;
     off_itemsB = o;      o += items_bytes;
     off_old2new = o;     o = align_up(o + (size_t)n * 4, 256);
-    off_digits = o;      o = align_up(o + 2 * (size_t)align_up((size_t)Umax, kSortTile), 256);  // whole tiles
+    off_digits = o;      o = align_up(o + (size_t)align_up((size_t)Umax, kSortTile), 256);  // whole tiles
     total = o;
   }
 };
@@ -139,8 +166,8 @@ struct WsPtrs {
   unsigned char* itemsA;
   unsigned char* itemsB;
   uint32_t* old2new;     // [nVtx]
-  uint8_t* digits;       // [Umax rounded up to whole sort tiles]: digit of the next radix pass; before
-                         // the first pass, viewed as uint16: low 16 bits of the last key word
+  uint8_t* digits;       // [Umax rounded up to whole sort tiles]: each item's digit of the next radix
+                         // pass (of the first one: written by the compaction)
   int64_t tilesS;        // capacity of the sort look-back table, in tiles
   int64_t Umax;          // capacity of each item buffer, in items
   int64_t idoff;         // byte offset of the id plane inside an item buffer (S = 8, 16)
@@ -365,6 +392,107 @@ __device__ __forceinline__ uint32_t key_digit(const uint32_t (&k)[K], int d) {
   for (int q = 1; q < K; ++q)
     if (q == w) word = k[q];
   return (word >> ((d & 3) * 8)) & 0xFFu;
+}
+
+// Word `w` (run time) of a key held in registers, and OR into it (select chains: a run-time index
+// into a register array would move the array to local memory).
+template <int K>
+__device__ __forceinline__ uint32_t key_word(const uint32_t (&k)[K], int w) {
+  uint32_t x = k[0];
+#pragma unroll
+  for (int q = 1; q < K; ++q)
+    if (q == w) x = k[q];
+  return x;
+}
+template <int K>
+__device__ __forceinline__ void key_word_or(uint32_t (&k)[K], int w, uint32_t v) {
+#pragma unroll
+  for (int q = 0; q < K; ++q)
+    if (q == w) k[q] |= v;
+}
+
+// Packs the varying bits of a key into its low bits (KeyPack runs, least significant first).
+template <int K>
+__device__ __forceinline__ void pack_key(uint32_t (&k)[K], const KeyPack& P) {
+  uint32_t out[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) out[q] = 0;
+  uint64_t acc = 0;
+  uint32_t nacc = 0;
+  int ow = K - 1;  // packed word being filled
+  for (int r = 0; r < P.nruns; ++r) {
+    const uint32_t len = P.len[r];
+    const uint32_t v = (key_word<K>(k, P.word[r]) >> P.shift[r]) & (len >= 32 ? ~0u : (1u << len) - 1u);
+    acc |= (uint64_t)v << nacc;
+    nacc += len;
+    if (nacc >= 32) {
+      key_word_or<K>(out, ow, (uint32_t)acc);
+      --ow;
+      acc >>= 32;
+      nacc -= 32;
+    }
+  }
+  if (nacc) key_word_or<K>(out, ow, (uint32_t)acc);
+#pragma unroll
+  for (int q = 0; q < K; ++q) k[q] = out[q];
+}
+
+// pack_key for keys with at most one run of varying bits per word (KeyPack::simple): the words
+// are visited in a fixed order with their run's shift and length, no per-run loop.
+template <int K>
+__device__ __forceinline__ void pack_key_simple(uint32_t (&k)[K], const KeyPack& P) {
+  uint32_t out[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) out[q] = 0;
+  uint64_t acc = 0;
+  uint32_t nacc = 0;
+  int ow = K - 1;
+#pragma unroll
+  for (int q = K - 1; q >= 0; --q) {
+    const uint32_t len = P.wlen[q];
+    const uint32_t v = (k[q] >> P.wshift[q]) & (len >= 32 ? ~0u : (1u << len) - 1u);
+    acc |= (uint64_t)v << nacc;
+    nacc += len;
+    if (nacc >= 32) {
+      key_word_or<K>(out, ow, (uint32_t)acc);
+      --ow;
+      acc >>= 32;
+      nacc -= 32;
+    }
+  }
+  if (nacc) key_word_or<K>(out, ow, (uint32_t)acc);
+#pragma unroll
+  for (int q = 0; q < K; ++q) k[q] = out[q];
+}
+
+// Bits [pos, pos + len) of a packed key (len <= 32).
+template <int K>
+__device__ __forceinline__ uint32_t packed_bits(const uint32_t (&k)[K], uint32_t pos, uint32_t len) {
+  const int cw = K - 1 - (int)(pos >> 5), cb = pos & 31;
+  uint32_t v = key_word<K>(k, cw) >> cb;
+  if (cb + len > 32) v |= key_word<K>(k, cw - 1) << (32 - cb);
+  return v & (len >= 32 ? ~0u : (1u << len) - 1u);
+}
+
+// Inverse of pack_key: every run back in place, the constant bits from kconst.
+template <int K>
+__device__ __forceinline__ void unpack_key(uint32_t (&k)[K], const KeyPack& P, const uint32_t* kconst) {
+  uint32_t out[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) out[q] = kconst[q];
+  for (int r = 0; r < P.nruns; ++r)
+    key_word_or<K>(out, P.word[r], packed_bits<K>(k, P.pos[r], P.len[r]) << P.shift[r]);
+#pragma unroll
+  for (int q = 0; q < K; ++q) k[q] = out[q];
+}
+
+// Key word 0 (the mesh id in batched mode) of a packed key.
+template <int K>
+__device__ __forceinline__ uint32_t unpacked_word0(const uint32_t (&k)[K], const KeyPack& P, uint32_t kconst0) {
+  uint32_t v = kconst0;
+  for (int r = 0; r < P.nruns; ++r)
+    if (P.word[r] == 0) v |= packed_bits<K>(k, P.pos[r], P.len[r]) << P.shift[r];
+  return v;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -23,11 +23,15 @@ struct LaunchCfg {
   int hist_mode = kHistUniform; // compaction histogram method (kHist*)
   int grid_per_tile = 0;        // 1: one CTA per tile; 0: persistent CTAs (SMs x occupancy)
   int scatter_waves = 0;        // "tiles" scatter: 0 one CTA per tile, else CTAs = waves x SMs x occupancy
+  int pack_keys = -1;           // "tiles" sort: pack the varying key bits when that saves a pass
+                                // (1 on, 0 off, -1 auto: keys of up to 8 bytes and batched calls)
 };
 
 // The configuration for one call: kSortAuto resolved for S-byte keys and up to Umax items.
-inline LaunchCfg resolve_cfg(LaunchCfg c, int /*S*/, int64_t Umax) {
+// batched: the call sorts (mesh id, vertex) keys, whose mesh-id bytes are mostly constant.
+inline LaunchCfg resolve_cfg(LaunchCfg c, int S, int64_t Umax, bool batched = false) {
   if (c.sort_kernel == kSortAuto) c.sort_kernel = Umax >= kTilesMinItems ? kSortTiles : kSortRegs;
+  if (c.pack_keys < 0) c.pack_keys = (batched || S <= 8) ? 1 : 0;
   return c;
 }
 
@@ -46,7 +50,10 @@ cudaError_t launch_used_flags(const int32_t* idx, int64_t M, int64_t nVtx, WsPtr
 cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
                            const SegArgs* seg, cudaStream_t st);
 // from_masks: trivial passes from the key bit masks (the "tiles" sort takes no upfront histograms).
-cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, cudaStream_t st);
+cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, bool allow_pack, cudaStream_t st);
+// Key bit masks over the used vertices (tiles sort; S is the vertex stride, seg as for the compaction).
+cudaError_t launch_key_masks(int S, const void* vtx, int64_t nVtx, WsPtrs ws, const LaunchCfg& c, const SegArgs* seg,
+                             cudaStream_t st);
 cudaError_t launch_onesweep(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_onesweep_pipe(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 // The "tiles" radix pass (k_radix_tiles.cu): per-tile digit counts, their scan, the scatter.

@@ -9,8 +9,14 @@
 // Tiles of 2048 vertices (8 warps x 8 rows x 32 lanes); a tile's output offset comes from a
 // decoupled look-back over per-tile used counts, so items keep vertex order.  The same pass
 // counts, per byte digit d of the key, how many used vertices have each digit value; or, for the
-// "tiles" sort (kHistNone), it records which key bits vary (OR of each key word and of its
-// complement) and the low 16 bits of each item's last key word, at the item's position.
+// "tiles" sort (kHistNone, after k_key_masks and the plan), it packs each key's varying bits when
+// the plan packs them and writes each item's digit of the first radix pass into the digit plane.
+//
+// k_key_masks (tiles sort, before the plan): the OR of every key word over the used vertices and
+// the OR of its complement; a bit varies between used vertices iff it is set in both.
+#include <algorithm>
+#include <atomic>
+
 #include "internal.h"
 
 namespace reindex {
@@ -25,19 +31,30 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
   constexpr int SI = kSeg ? S + 4 : S;  // item key bytes
   constexpr int K = SI / 4;
   constexpr int P = SI;  // byte digits per key
-  constexpr bool kCount = kHist != kHistNone;
+  constexpr bool kCount = kHist != kHistNone && kHist != kHistMasks;
+  constexpr bool kMasks = kHist == kHistMasks;  // tiles sort without packing: the plan comes after
   __shared__ uint32_t s_hist[kCount ? P * kRadix : 1];
   __shared__ uint32_t s_warp[kWarps];
   __shared__ uint32_t s_tile, s_prefix;
+  __shared__ KeyPack s_pack;
+  __shared__ int s_first;
   Control* ctrl = ws.ctrl;
+  if (kHist == kHistNone && threadIdx.x == 0) {
+    s_pack = ws.plan->pack;
+    s_first = ws.plan->first;
+  }
   if (block_error(ctrl)) return;  // an invalid index was seen: nothing downstream is meaningful
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   if constexpr (kCount)
     for (int i = t; i < P * kRadix; i += kThreads) s_hist[i] = 0;
-  uint32_t kor[K], knand[K];  // this thread's OR of each key word and of its complement
+  // digit of the first radix pass (tiles sort): byte 0 of the packed key, or a byte of the key
+  // (kHistMasks: key byte 0, the first pass's digit unless that byte is constant)
+  const bool packed = kHist == kHistNone && s_pack.on;
+  const int first = kMasks ? 0 : (kCount ? -1 : s_first);
+  const int fword = packed ? K - 1 : K - 1 - (first >> 2), fshift = packed ? 0 : (first & 3) * 8;
+  uint32_t kor[K], knand[K];  // kHistMasks: this thread's OR of each key word and of its complement
 #pragma unroll
   for (int q = 0; q < K; ++q) kor[q] = knand[q] = 0;
-  uint16_t* low16 = reinterpret_cast<uint16_t*>(ws.digits);
 
   for (;;) {
     if (t == 0) s_tile = atomicAdd(&ctrl->ctr[0], 1u);
@@ -96,7 +113,10 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
       }
       if (lane == 0) {
         s_prefix = prefix;
-        if (tile == tilesV - 1) ctrl->U = prefix + total;
+        if (tile == tilesV - 1) {
+          ctrl->U = prefix + total;
+          if (kHist == kHistNone) ws.plan->U = prefix + total;  // the plan ran before the compaction
+        }
       }
     }
     if (tile == stall_tile && t == 0) s_prefix = 0;  // the stalled tile writes at [0, total): in bounds
@@ -113,15 +133,23 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
 #pragma unroll
         for (int q = 0; q < K; ++q) it.k[q] = k[r][q];
         it.id = (uint32_t)(vbase + r * 32 + lane);
-        ItemIO<SI>::store(ws.itemsA, ws.idoff, obase + pos[r], it);
         if constexpr (!kCount) {
-          low16[obase + pos[r]] = (uint16_t)k[r][K - 1];
+          if (packed) {
+            if (s_pack.simple)
+              pack_key_simple<K>(it.k, s_pack);
+            else
+              pack_key<K>(it.k, s_pack);
+          }
+          if (first >= 0) ws.digits[obase + pos[r]] = (uint8_t)(key_word<K>(it.k, fword) >> fshift);
+        }
+        if constexpr (kMasks) {
 #pragma unroll
           for (int q = 0; q < K; ++q) {
-            kor[q] |= k[r][q];
-            knand[q] |= ~k[r][q];
+            kor[q] |= it.k[q];
+            knand[q] |= ~it.k[q];
           }
         }
+        ItemIO<SI>::store(ws.itemsA, ws.idoff, obase + pos[r], it);
       }
       if constexpr (!kCount) continue;
       // Histograms.  Many key bytes are heavily skewed (exponent bytes, the zero low bytes of
@@ -158,7 +186,8 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
       const uint32_t c = s_hist[i];
       if (c) atomicAdd(ws.hist + i, c);
     }
-  } else {
+  }
+  if constexpr (kMasks) {
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const uint32_t a = __reduce_or_sync(0xffffffffu, kor[q]), b = __reduce_or_sync(0xffffffffu, knand[q]);
@@ -166,6 +195,80 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
         if (a) atomicOr(&ctrl->kor[q], a);
         if (b) atomicOr(&ctrl->knand[q], b);
       }
+    }
+  }
+}
+
+// kVec: the vertex array is 16-byte aligned, so a thread reads 4 consecutive vertices (S words of
+// 16 bytes) with vector loads; the tail and unaligned arrays go one vertex at a time.
+template <int S, bool kSeg, bool kVec>
+__global__ void __launch_bounds__(kThreads) k_key_masks(const void* __restrict__ vtx, int64_t nVtx, WsPtrs ws,
+                                                         SegArgs seg) {
+  constexpr int K = kSeg ? S / 4 + 1 : S / 4;
+  constexpr int KV = S / 4;  // words per vertex
+  if (block_error(ws.ctrl)) return;
+  uint32_t kor[K], knand[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) kor[q] = knand[q] = 0;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  int64_t done = 0;
+  if constexpr (kVec) {
+    const uint4* v4 = reinterpret_cast<const uint4*>(vtx);
+    const int64_t n4 = nVtx >> 2;  // groups of 4 vertices = KV vectors
+    for (int64_t g = blockIdx.x * (int64_t)kThreads + threadIdx.x; g < n4; g += stride) {
+      // vertex loads first (independent of the used bits, so both are in flight together)
+      uint32_t wds[4 * KV];
+#pragma unroll
+      for (int i = 0; i < KV; ++i) {
+        const uint4 x = __ldcs(v4 + g * KV + i);
+        wds[4 * i] = x.x; wds[4 * i + 1] = x.y; wds[4 * i + 2] = x.z; wds[4 * i + 3] = x.w;
+      }
+      const uint32_t bits = (__ldg(ws.bitmask + (g >> 3)) >> ((g & 7) * 4)) & 0xFu;  // used bits of the 4
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!((bits >> j) & 1u)) continue;
+        uint32_t k[K];
+        if constexpr (kSeg) {
+          k[0] = seg_mesh(g * 4 + j, seg.vtxOff, 1, seg.blkV, seg.nMeshes);
+#pragma unroll
+          for (int q = 0; q < KV; ++q) k[1 + q] = wds[j * KV + q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < KV; ++q) k[q] = wds[j * KV + q];
+        }
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          kor[q] |= k[q];
+          knand[q] |= ~k[q];
+        }
+      }
+    }
+    done = n4 << 2;
+  }
+  for (int64_t v = done + blockIdx.x * (int64_t)kThreads + threadIdx.x; v < nVtx; v += stride) {
+    if (!((__ldg(ws.bitmask + (v >> 5)) >> (v & 31)) & 1u)) continue;
+    uint32_t k[K];
+    if constexpr (kSeg) {
+      uint32_t kv[S / 4];
+      load_key<S>(vtx, v, kv);
+      k[0] = seg_mesh(v, seg.vtxOff, 1, seg.blkV, seg.nMeshes);
+#pragma unroll
+      for (int q = 0; q < S / 4; ++q) k[1 + q] = kv[q];
+    } else {
+      load_key<S>(vtx, v, k);
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      kor[q] |= k[q];
+      knand[q] |= ~k[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const uint32_t a = __reduce_or_sync(0xffffffffu, kor[q]), b = __reduce_or_sync(0xffffffffu, knand[q]);
+    if ((threadIdx.x & 31) == 0) {
+      if (a) atomicOr(&ws.ctrl->kor[q], a);
+      if (b) atomicOr(&ws.ctrl->knand[q], b);
     }
   }
 }
@@ -178,11 +281,13 @@ static int occ() {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_compact<S, kHistMatchAny, false>, kThreads, 0);
   int n = min(a, min(b, c));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistNone, false>, kThreads, 0);
-  n = min(n, a);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistMasks, false>, kThreads, 0);
+  n = min(n, min(a, b));
   if constexpr (S <= 16) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistUniform, true>, kThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistNone, true>, kThreads, 0);
-    n = min(n, min(a, b));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_compact<S, kHistMasks, true>, kThreads, 0);
+    n = min(n, min(a, min(b, c)));
   }
   return n < 1 ? 1 : n;
 }
@@ -197,44 +302,96 @@ int occupancy_compact(int S) {
   }
 }
 
+// Resident CTAs per SM of one compaction variant (queried once; persistent grids are sized by it).
+template <int S, int kHist, bool kSeg>
+static int occ_variant() {
+  static std::atomic<int> cached{0};
+  int n = cached.load(std::memory_order_relaxed);
+  if (n == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_compact<S, kHist, kSeg>, kThreads, 0);
+    if (n < 1) n = 1;
+    cached.store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+
+template <int S, int kHist, bool kSeg>
+static void launch_v(int64_t g, int sms, bool persistent, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV,
+                     const SegArgs& seg, cudaStream_t st) {
+  if (persistent) g = std::min<int64_t>(g, (int64_t)sms * occ_variant<S, kHist, kSeg>());
+  k_compact<S, kHist, kSeg><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg, debug_stall_tile());
+}
+
 template <int S, bool kSeg>
-static void launch_s(int g, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, int mode, const SegArgs& seg,
-                     cudaStream_t st) {
-  const int64_t stall = debug_stall_tile();
+static void launch_s(int64_t g, int sms, bool persistent, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV,
+                     int mode, const SegArgs& seg, cudaStream_t st) {
   if (mode == kHistNone)
-    k_compact<S, kHistNone, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg, stall);
+    launch_v<S, kHistNone, kSeg>(g, sms, persistent, vtx, nVtx, ws, tilesV, seg, st);
+  else if (mode == kHistMasks)
+    launch_v<S, kHistMasks, kSeg>(g, sms, persistent, vtx, nVtx, ws, tilesV, seg, st);
   else if (kSeg || mode == kHistUniform)
-    k_compact<S, kHistUniform, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg, stall);
+    launch_v<S, kHistUniform, kSeg>(g, sms, persistent, vtx, nVtx, ws, tilesV, seg, st);
   else if (mode == kHistMatchAny)
-    k_compact<S, kHistMatchAny, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg, stall);
+    launch_v<S, kHistMatchAny, kSeg>(g, sms, persistent, vtx, nVtx, ws, tilesV, seg, st);
   else
-    k_compact<S, kHistPeel, kSeg><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, tilesV, seg, stall);
+    launch_v<S, kHistPeel, kSeg>(g, sms, persistent, vtx, nVtx, ws, tilesV, seg, st);
 }
 
 cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
                            const SegArgs* seg, cudaStream_t st) {
   if (tilesV == 0) return cudaSuccess;
-  int64_t g = c.grid_per_tile ? tilesV : (int64_t)c.sms * c.occ_compact;
-  if (g > tilesV) g = tilesV;
+  const int64_t g = tilesV;  // capped at SMs x the variant's occupancy unless one CTA per tile
+  const bool persistent = !c.grid_per_tile;
   const SegArgs none{};
   // the "tiles" sort counts digits per pass and needs no upfront histograms
-  const int mode = c.sort_kernel == kSortTiles ? kHistNone : c.hist_mode;
+  const int mode = c.sort_kernel == kSortTiles ? (c.pack_keys ? kHistNone : kHistMasks) : c.hist_mode;
   if (seg) {
     switch (S) {
-      case 4: launch_s<4, true>((int)g, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
-      case 8: launch_s<8, true>((int)g, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
-      case 12: launch_s<12, true>((int)g, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
-      default: launch_s<16, true>((int)g, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
+      case 4: launch_s<4, true>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
+      case 8: launch_s<8, true>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
+      case 12: launch_s<12, true>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
+      default: launch_s<16, true>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, *seg, st); break;
     }
   } else {
     switch (S) {
-      case 4: launch_s<4, false>((int)g, vtx, nVtx, ws, tilesV, mode, none, st); break;
-      case 8: launch_s<8, false>((int)g, vtx, nVtx, ws, tilesV, mode, none, st); break;
-      case 12: launch_s<12, false>((int)g, vtx, nVtx, ws, tilesV, mode, none, st); break;
-      case 16: launch_s<16, false>((int)g, vtx, nVtx, ws, tilesV, mode, none, st); break;
-      default: launch_s<20, false>((int)g, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      case 4: launch_s<4, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      case 8: launch_s<8, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      case 12: launch_s<12, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      case 16: launch_s<16, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      default: launch_s<20, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
     }
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_key_masks(int S, const void* vtx, int64_t nVtx, WsPtrs ws, const LaunchCfg& c,
+                             const SegArgs* seg, cudaStream_t st) {
+  if (nVtx == 0) return cudaSuccess;
+  int64_t g = (nVtx + kThreads - 1) / kThreads;
+  if (g > (int64_t)c.sms * 8) g = (int64_t)c.sms * 8;
+  const bool vec = (reinterpret_cast<uintptr_t>(vtx) & 15) == 0;
+  const SegArgs none{};
+  const SegArgs& sg = seg ? *seg : none;
+#define REINDEX_KM(SS, SEG)                                                                 \
+  (vec ? k_key_masks<SS, SEG, true><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, ws, sg)       \
+       : k_key_masks<SS, SEG, false><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, ws, sg))
+  if (seg) {
+    switch (S) {
+      case 4: REINDEX_KM(4, true); break;
+      case 8: REINDEX_KM(8, true); break;
+      case 12: REINDEX_KM(12, true); break;
+      default: REINDEX_KM(16, true); break;
+    }
+  } else {
+    switch (S) {
+      case 4: REINDEX_KM(4, false); break;
+      case 8: REINDEX_KM(8, false); break;
+      case 12: REINDEX_KM(12, false); break;
+      case 16: REINDEX_KM(16, false); break;
+      default: REINDEX_KM(20, false); break;
+    }
+  }
+#undef REINDEX_KM
   return cudaGetLastError();
 }
 

@@ -7,7 +7,9 @@
 //   *out_nVtx = total number of heads                        (Section 2.3, newN)
 // The prefix sum is a decoupled look-back scan over tiles of 2048 items (256 threads x 8; four
 // CTAs per SM, so that the others keep working while one waits in its look-back);
-// neither nodup nor newIdx is materialised.
+// neither nodup nor newIdx is materialised.  If the radix sort packed the keys (their varying
+// bits only), run heads are found on the packed keys (equal exactly when the keys are) and only
+// the keys written out are restored; a mesh id (batched mode) is read from its packed bits.
 #include "internal.h"
 
 namespace reindex {
@@ -23,9 +25,17 @@ __global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsP
   constexpr int K = S / 4;
   __shared__ uint32_t s_warp[kHeadWarps];
   __shared__ uint32_t s_tile, s_prefix;
+  __shared__ KeyPack s_pack;
+  __shared__ uint32_t s_kconst[K];
   Control* ctrl = ws.ctrl;
-  if (block_error(ctrl)) return;
   const Plan* plan = ws.plan;
+  if (threadIdx.x == 0) {
+    s_pack = plan->pack;
+#pragma unroll
+    for (int q = 0; q < K; ++q) s_kconst[q] = plan->kconst[q];
+  }
+  if (block_error(ctrl)) return;  // (its barriers also publish s_pack and s_kconst)
+  const bool packed = s_pack.on != 0;
   const uint32_t U = plan->U;
   const int64_t ntiles = ((int64_t)U + kHeadTile - 1) / kHeadTile;
   const unsigned char* buf = plan->final_sel ? ws.itemsB : ws.itemsA;
@@ -65,6 +75,7 @@ __global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsP
     for (int r = 0; r < kHeadIpt; ++r) {
       const int64_t j = wbase + r * 32 + lane;
       bool diff = false, mesh_diff = false;
+      uint32_t pks[K];  // the preceding item's key
 #pragma unroll
       for (int q = 0; q < K; ++q) {
         const uint32_t up = __shfl_up_sync(0xffffffffu, it[r].k[q], 1);
@@ -76,7 +87,11 @@ __global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsP
           pk = lane ? up : last;
         }
         diff |= it[r].k[q] != pk;
-        if (q == 0) mesh_diff = it[r].k[0] != pk;
+        pks[q] = pk;
+      }
+      if constexpr (kSeg) {  // the mesh id is key word 0 (restored from its packed bits when packed)
+        mesh_diff = packed ? unpacked_word0<K>(it[r].k, s_pack, 0u) != unpacked_word0<K>(pks, s_pack, 0u)
+                           : it[r].k[0] != pks[0];
       }
       const bool head = (j < U) && (j == 0 || diff);
       const uint32_t m = __ballot_sync(0xffffffffu, head);
@@ -120,16 +135,22 @@ __global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsP
         const uint32_t nid = head ? e : e - 1u;
         if (it[r].id < nVtx) {
           st_u32_hint(ws.old2new + it[r].id, nid, keep);
-          if constexpr (kSeg) {
-            if (head) {
-              uint32_t v[K - 1];
+          if (head || (kSeg && ((firsts >> r) & 1u))) {
+            uint32_t key[K];
 #pragma unroll
-              for (int q = 1; q < K; ++q) v[q - 1] = it[r].k[q];
-              store_key<S - 4>(out_vtx, nid, v);
+            for (int q = 0; q < K; ++q) key[q] = it[r].k[q];
+            if (packed) unpack_key<K>(key, s_pack, s_kconst);
+            if constexpr (kSeg) {
+              if (head) {
+                uint32_t v[K - 1];
+#pragma unroll
+                for (int q = 1; q < K; ++q) v[q - 1] = key[q];
+                store_key<S - 4>(out_vtx, nid, v);
+              }
+              if ((firsts >> r) & 1u) seg.outOff[key[0]] = (int64_t)nid;
+            } else {
+              store_key<S>(out_vtx, nid, key);
             }
-            if ((firsts >> r) & 1u) seg.outOff[it[r].k[0]] = (int64_t)nid;
-          } else {
-            if (head) store_key<S>(out_vtx, nid, it[r].k);
           }
         } else {
           record_error(ctrl, kErrInternal);  // corrupted item: never write out of range

@@ -3,17 +3,17 @@
 // tile waits for another (the "tiles" sort variant).  Three launches per digit position d:
 //   k_tile_count    per tile of 4096 items, how many carry each digit value, and the pass's
 //                   digit totals.  It reads a byte plane holding each item's digit d at the
-//                   item's position, written by the previous pass (before the first pass, the
-//                   compaction's plane of the low 16 bits of the last key word serves digits 0
-//                   and 1; a first pass on a higher digit reads the key words themselves);
+//                   item's position, written by the previous pass (for the first pass, by the
+//                   compaction);
 //   k_tile_offsets  per digit value v, the exclusive scan of its counts over the tiles plus the
 //                   number of items whose digit is below v;
 //   k_tile_scatter  loads a tile, ranks its digits inside each warp (stable), stages the tile in
 //                   digit order in shared memory and writes it out in runs; every item also
 //                   writes its digit of the next non-trivial pass into the byte plane.
 // Every pass is the same stable pass as k_onesweep, so the result is identical.  No upfront
-// histograms are needed: trivial passes are known from the key bit masks.  Extra traffic per
-// item and pass: one byte written and one read.
+// histograms are needed: trivial passes are known from the key bit masks, and when many key bits
+// are constant the compaction packs the varying ones (KeyPack), so the passes sort fewer bytes.
+// Extra traffic per item and pass: one byte written and one read.
 #include <algorithm>
 
 #include "radix.cuh"
@@ -26,12 +26,12 @@ __device__ __forceinline__ uint32_t* tile_counts(const WsPtrs& ws, int v) {
   return ws.lb_sort + (size_t)v * (size_t)ws.tilesS;
 }
 
-constexpr uint32_t kSrcPlane8 = 0, kSrcPlane16 = 1, kSrcKeys = 2;  // where k_tile_count finds digit d
-
 // Per-pass values of the plan, read once by thread 0 and shared, together with the error word
 // (so that every thread of the CTA takes the same early exit).
 struct PassInfo {
-  uint32_t U, run, src, next, count_src, vary;
+  uint32_t U, run, src, next, vary;
+  uint32_t keys;  // k_tile_count reads digit d from the keys: a first pass whose digit is not in the
+                  // compaction's plane (unpacked keys whose byte 0 is constant)
 };
 
 // A skipped pass exits without a barrier: every thread reads the skip flag through the read-only
@@ -42,14 +42,14 @@ __device__ __forceinline__ PassInfo pass_info(const WsPtrs& ws, int d) {
   if (threadIdx.x == 0) {
     const Plan* plan = ws.plan;
     const uint32_t skip = plan->skip[d], U = plan->U, src = plan->src[d];
-    const int first = plan->first, next = plan->next[d];
+    const int next = plan->next[d], first = plan->first;
     const uint32_t err = *(volatile const uint32_t*)&ws.ctrl->err;
     s_pi.U = U;
     s_pi.run = (!skip && err == 0) ? 1u : 0u;
     s_pi.src = src;
     s_pi.next = (uint32_t)(int32_t)next;
-    s_pi.count_src = d != first ? kSrcPlane8 : (d <= 1 ? kSrcPlane16 : kSrcKeys);
     s_pi.vary = plan->vary[d];
+    s_pi.keys = (d == first && d != 0 && !plan->plane_first) ? 1u : 0u;
   }
   __syncthreads();
   const PassInfo pi = s_pi;
@@ -72,20 +72,6 @@ constexpr int kHPad = kRadix + 1;
 constexpr int kLaneDigits = kSortTile / 32;  // 128 digits of a tile per lane
 static_assert(kCntTiles == 2 * kWarps, "two tiles per warp");
 
-// 16 digits at positions j .. j+15 (j a multiple of 16, j < U), packed 4 per word, from the
-// byte plane or (src == kSrcPlane16) from byte d of the 16-bit plane.
-__device__ __forceinline__ uint4 load16(const WsPtrs& ws, uint32_t src, int d, uint32_t j) {
-  if (src == kSrcPlane8) return __ldcs(reinterpret_cast<const uint4*>(ws.digits + j));
-  const uint4* p = reinterpret_cast<const uint4*>(ws.digits + 2 * (size_t)j);
-  const uint4 a = __ldcs(p), b = __ldcs(p + 1);
-  const uint32_t h[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-  const int sh = d * 8;
-  uint32_t q[4] = {0, 0, 0, 0};
-#pragma unroll
-  for (int i = 0; i < 16; ++i) q[i >> 2] |= ((h[i >> 1] >> ((i & 1) * 16 + sh)) & 0xFFu) << ((i & 3) * 8);
-  return make_uint4(q[0], q[1], q[2], q[3]);
-}
-
 template <int S>
 __global__ void __launch_bounds__(kThreads, 4) k_tile_count(WsPtrs ws, int d) {
   __shared__ uint32_t h[kCntTiles * kHPad];
@@ -107,28 +93,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_tile_count(WsPtrs ws, int d) {
     const uint32_t base = tile * kSortTile;
     const int n = (int)min((uint32_t)kSortTile, U - base);
     uint32_t* hr = h + tl * kHPad;
-    if (pi.count_src == kSrcKeys) {  // first pass on a digit above the 16-bit plane: read the keys
+    if (pi.keys) {
       const int word = S / 4 - 1 - (d >> 2), sh = (d & 3) * 8;
-      for (int i = lane; i < n; i += 32) atomicAdd(hr + ((item_key_word<S>(items, (int64_t)base + i, word) >> sh) & 0xFFu), 1u);
+      for (int i = lane; i < n; i += 32)
+        atomicAdd(hr + ((item_key_word<S>(items, (int64_t)base + i, word) >> sh) & 0xFFu), 1u);
       continue;
     }
     // lane's 128 digits: 8 chunks of 16, chunk c at c*512 + lane*16; all loads issued first
     uint4 v[kLaneDigits / 16];
-    if (pi.count_src == kSrcPlane8) {
 #pragma unroll
-      for (int c = 0; c < kLaneDigits / 16; ++c) {
-        const int p = c * 512 + lane * 16;
-        v[c] = p < n ? __ldcs(reinterpret_cast<const uint4*>(ws.digits + base + p)) : make_uint4(0, 0, 0, 0);
-      }
-    } else {
-#pragma unroll 1
-      for (int c = 0; c < kLaneDigits / 16; ++c) {
-        const int p = c * 512 + lane * 16;
-        const uint4 x = p < n ? load16(ws, pi.count_src, d, base + p) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-        for (int q = 0; q < kLaneDigits / 16; ++q)
-          if (q == c) v[q] = x;
-      }
+    for (int c = 0; c < kLaneDigits / 16; ++c) {
+      const int p = c * 512 + lane * 16;
+      v[c] = p < n ? __ldcs(reinterpret_cast<const uint4*>(ws.digits + base + p)) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int c = 0; c < kLaneDigits / 16; ++c) {

@@ -64,20 +64,80 @@ __global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int
 }
 
 // Digit offsets and pass plan (one CTA of 256 threads; thread t owns digit value t).
-// from_masks: trivial digits come from the key bit masks (no upfront histograms were taken).
-__global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from_masks) {
+// The radix-sort plan for the P byte positions of a P-byte key.  With upfront histograms
+// (onesweep sort): a byte is trivial if one value holds all U items; exclusive digit offsets from
+// the histogram.  From the key bit masks (tiles sort, no histograms): if packing the varying bits
+// (KeyPack) saves at least one pass, the passes sort the bytes of the packed key and the positions
+// past its last byte are trivial; otherwise the raw bytes without a varying bit are trivial.
+__global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from_masks, int allow_pack) {
   __shared__ uint32_t s_warp[kRadix / 32];
   __shared__ uint32_t s_or[kRadix / 32], s_and[kRadix / 32];
+  __shared__ int s_np;  // bytes of the packed key, or -1 (keys not packed)
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const uint32_t U = ws.ctrl->U;
   Plan* plan = ws.plan;
+  const int K = P / 4;
+  if (t == 0) {
+    int np = -1;
+    plan->pack.on = 0;
+    if (from_masks) {
+      KeyPack kp{};
+      int pos = 0, nraw = 0;
+      bool fits = true;
+      kp.simple = 1;
+      for (int wd = K - 1; wd >= 0; --wd) {  // least significant word first
+        const uint32_t m = ws.ctrl->kor[wd] & ws.ctrl->knand[wd];
+        plan->kconst[wd] = ws.ctrl->kor[wd] & ~m;
+        const int first_run = kp.nruns;
+        for (int i = 0; i < 4; ++i) nraw += ((m >> (8 * i)) & 0xFFu) != 0;
+        for (int b = 0; b < 32;) {  // runs of varying bits
+          if (!((m >> b) & 1u)) {
+            ++b;
+            continue;
+          }
+          int e = b;
+          while (e < 32 && ((m >> e) & 1u)) ++e;
+          if (kp.nruns == kMaxPackRuns) {
+            fits = false;
+          } else {
+            kp.word[kp.nruns] = (uint8_t)wd;
+            kp.shift[kp.nruns] = (uint8_t)b;
+            kp.len[kp.nruns] = (uint8_t)(e - b);
+            kp.pos[kp.nruns] = (uint8_t)pos;
+            ++kp.nruns;
+          }
+          pos += e - b;
+          b = e;
+        }
+        const int runs_here = kp.nruns - first_run;
+        if (runs_here > 1) kp.simple = 0;
+        kp.wshift[wd] = runs_here == 1 ? kp.shift[first_run] : 0;
+        kp.wlen[wd] = runs_here == 1 ? kp.len[first_run] : 0;
+      }
+      kp.nbits = (uint8_t)pos;
+      const int packed = (pos + 7) / 8;
+      if (allow_pack && fits && packed < nraw) {  // packing saves at least one pass
+        kp.on = 1;
+        plan->pack = kp;
+        np = packed;
+      }
+    }
+    s_np = np;
+  }
+  __syncthreads();
+  const int np = s_np;
+  const uint32_t nbits = np >= 0 ? plan->pack.nbits : 0u;
   uint32_t sel = 0, q = 0;  // identical in every thread
   for (int d = 0; d < P; ++d) {
     const uint32_t c = ws.hist[d * kRadix + t];
     // A digit whose value is the same for all U items: that pass is the identity.
     int trivial;
     uint32_t vary;  // digit bits that are not the same in every item
-    if (from_masks) {
+    if (from_masks && np >= 0) {
+      trivial = d >= np;
+      vary = trivial ? 0u : ((d == np - 1 && (nbits & 7u)) ? (1u << (nbits & 7u)) - 1u : 0xFFu);
+      __syncthreads();
+    } else if (from_masks) {
       const int q = P / 4 - 1 - (d >> 2);
       vary = ((ws.ctrl->kor[q] & ws.ctrl->knand[q]) >> ((d & 3) * 8)) & 0xFFu;
       trivial = vary == 0;
@@ -119,7 +179,8 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from
       if (!plan->skip[d]) nxt = d;
     }
     plan->first = (int8_t)nxt;
-    plan->U = U;
+    plan->U = allow_pack ? 0u : U;  // packing: the plan runs first and the compaction writes U
+    plan->plane_first = allow_pack ? 1 : 0;
     plan->final_sel = sel;
   }
 }
@@ -219,8 +280,8 @@ cudaError_t launch_used_flags(const int32_t* idx, int64_t M, int64_t nVtx, WsPtr
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, cudaStream_t st) {
-  k_sort_plan<<<1, kRadix, 0, st>>>(ws, S, from_masks ? 1 : 0);
+cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, bool allow_pack, cudaStream_t st) {
+  k_sort_plan<<<1, kRadix, 0, st>>>(ws, S, from_masks ? 1 : 0, allow_pack ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -103,7 +103,8 @@ reindex_status reindex_autotune(const void* vtx, int64_t nVtx, int S, const int3
                             {"rank=ballot", "rank=match", "rank=vary", nullptr},
                             {"hist=uniform", "hist=peel", "hist=match", nullptr},
                             {"grid=persist", "grid=tile", nullptr, nullptr},
-                            {"swaves=tile", "swaves=1", "swaves=4", nullptr}};
+                            {"swaves=tile", "swaves=1", "swaves=4", nullptr},
+                            {"pack=auto", "pack=on", "pack=off", nullptr}};
   for (auto& knob : knobs) {
     if (rs != REINDEX_OK) break;
     for (const char* v : knob) {

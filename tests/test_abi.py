@@ -43,12 +43,12 @@ def test_status_strings(L):
 
 
 def test_workspace_size_model(L):
-    # two item buffers of (S+4) bytes per potentially used vertex + a 2-byte digit plane per item
+    # two item buffers of (S+4) bytes per potentially used vertex + a 1-byte digit plane per item
     # + oldToNew + bitmask + tables
     n, S, ne, k = 26_424_115, 12, 8_388_608, 3
     b = rx.reindex_workspace_size(n, S, ne, k)
     U = min(n, ne * k)
-    assert 2 * U * (S + 4) + 2 * U + 4 * n <= b <= 2 * U * (S + 4) + 2 * U + 4 * n + 64 * 2**20
+    assert 2 * U * (S + 4) + U + 4 * n <= b <= 2 * U * (S + 4) + U + 4 * n + 64 * 2**20
     assert rx.reindex_workspace_size(n, 5, ne, k) == 0  # unsupported stride
     assert rx.reindex_workspace_size(-1, 12, ne, k) == 0
     assert rx.reindex_workspace_size(10, 12, 0, 3) > 0

@@ -60,6 +60,9 @@ def random_mesh(rng, n, m, K, mode):
         pool = np.array([0x00000000, 0x80000000, 0x7FC00000, 0x7FC00001, 0xBF800000, 0x3F800000, 0x40400000],
                         dtype=np.uint32)
         vtx = pool[rng.integers(0, len(pool), size=(n, K))]
+    elif mode == "hibyte":  # lowest key byte constant, varying bits in several runs per word
+        vtx = (rng.integers(0, 2**32, size=(n, K), dtype=np.uint64).astype(np.uint32) & np.uint32(0xF0F0FF00))
+        vtx |= np.uint32(0x00000A05)
     else:  # "const": a few constant words -> trivial radix passes get skipped
         vtx = np.zeros((n, K), dtype=np.uint32)
         vtx[:, -1] = rng.integers(0, 300, size=n).astype(np.uint32)
@@ -227,10 +230,11 @@ def test_host_buffer_variant(rx):
     np.testing.assert_array_equal(out_i.numpy().reshape(-1), oi)
 
 
-SORT_KERNELS = {"regs": ["onesweep"], "tiles": ["tile_count", "tile_offsets", "tile_scatter"]}
+SORT_KERNELS = {"regs": ["onesweep"], "tiles,pack=off": ["tile_count", "tile_offsets", "tile_scatter"],
+                "tiles,pack=on": ["tile_count", "tile_offsets", "tile_scatter", "key_masks"]}
 
 
-@pytest.mark.parametrize("sort", ["regs", "tiles"])
+@pytest.mark.parametrize("sort", ["regs", "tiles,pack=off", "tiles,pack=on"])
 def test_profile_records_every_kernel(rx, sort):
     m = synth.config_mesh(1)
     v, i = to_dev(m.vtx, m.idx)
@@ -248,18 +252,22 @@ def test_profile_records_every_kernel(rx, sort):
     names = [r["name"] for r in recs]
     mine = SORT_KERNELS[sort]
     for k in mine:
-        assert names.count(k) == 12
+        assert names.count(k) == (1 if k == "key_masks" else 12)
     others = {k for ks in SORT_KERNELS.values() for k in ks} - set(mine)
     assert set(names) == set(rx.KERNEL_NAMES) - {"seg_prepare", "seg_offsets"} - others
     # x and y are integers 0..256 as float32: their lowest byte is always zero -> skipped passes
-    sk = {r["digit"]: r["skipped"] for r in recs if r["name"] == mine[-1]}
-    assert sk[8] and sk[4] and not sk[0]
+    # (packed keys: the skipped passes are the top digit positions instead)
+    sk = {r["digit"]: r["skipped"] for r in recs if r["name"] == mine[0]}
+    assert sum(sk.values()) >= 2 and not sk[0]
+    if not sort.endswith("pack=on"):
+        assert sk[8] and sk[4]
 
 
 # Every radix-pass variant (and grid shape) must give the same bit-exact result.
 SORT_VARIANTS = ["sort=regs,rank=ballot,grid=persist", "sort=regs,rank=match,grid=tile",
-                 "sort=pipe,rank=ballot,grid=persist", "sort=tiles,rank=ballot,swaves=1",
-                 "sort=tiles,rank=match,swaves=tile", "sort=tiles,rank=ballot,swaves=4"]
+                 "sort=pipe,rank=ballot,grid=persist", "sort=tiles,rank=ballot,swaves=1,pack=on",
+                 "sort=tiles,rank=match,swaves=tile,pack=off", "sort=tiles,rank=ballot,swaves=4,pack=off",
+                 "sort=tiles,rank=vary,swaves=tile,pack=on", "sort=tiles,rank=ballot,pack=auto"]
 
 
 @pytest.mark.parametrize("spec", SORT_VARIANTS)
@@ -269,7 +277,7 @@ def test_sort_variants_bit_exact(rx, spec, S):
     rx.reindex_tuning_set(S, spec)
     try:
         rng = np.random.default_rng(7000 + S + 100 * SORT_VARIANTS.index(spec))
-        for mode in ["random", "dups", "const"]:
+        for mode in ["random", "dups", "const", "hibyte"]:
             for n, m in SIZES:
                 assert_parity(rx, *random_mesh(rng, n, m, S // 4, mode))
         if S == 12:
