@@ -18,7 +18,8 @@ constexpr int kHeadWarps = kHeadThreads / 32;
 
 // S is the item key size.  In batched mode (kSeg) key word 0 is the mesh id: only words 1.. are
 // written to out_vtx, and the first item of each mesh records that mesh's first output vertex.
-template <int S, bool kSeg>
+// kMayPack: the sort may have packed the keys (the call allows packing); else they are never packed.
+template <int S, bool kSeg, bool kMayPack>
 __global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsPtrs ws, void* __restrict__ out_vtx,
                                                          int64_t* __restrict__ out_nVtx, uint32_t nVtx,
                                                          SegArgs seg) {
@@ -29,13 +30,13 @@ __global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsP
   __shared__ uint32_t s_kconst[K];
   Control* ctrl = ws.ctrl;
   const Plan* plan = ws.plan;
-  if (threadIdx.x == 0) {
+  if (kMayPack && threadIdx.x == 0) {
     s_pack = plan->pack;
 #pragma unroll
     for (int q = 0; q < K; ++q) s_kconst[q] = plan->kconst[q];
   }
   if (block_error(ctrl)) return;  // (its barriers also publish s_pack and s_kconst)
-  const bool packed = s_pack.on != 0;
+  const bool packed = kMayPack && s_pack.on != 0;
   const uint32_t U = plan->U;
   const int64_t ntiles = ((int64_t)U + kHeadTile - 1) / kHeadTile;
   const unsigned char* buf = plan->final_sel ? ws.itemsB : ws.itemsA;
@@ -163,8 +164,10 @@ __global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsP
 
 template <int S>
 static int occ() {
-  int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_head_scan<S, false>, kHeadThreads, 0);
+  int n = 0, m = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_head_scan<S, false, false>, kHeadThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_head_scan<S, false, true>, kHeadThreads, 0);
+  n = min(n, m);
   return n < 1 ? 1 : n;
 }
 
@@ -180,8 +183,11 @@ int occupancy_head(int S) {
 
 template <int S, bool kSeg>
 static void launch_s(int g, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx, const SegArgs& seg,
-                     cudaStream_t st) {
-  k_head_scan<S, kSeg><<<g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx, seg);
+                     bool may_pack, cudaStream_t st) {
+  if (may_pack)
+    k_head_scan<S, kSeg, true><<<g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx, seg);
+  else
+    k_head_scan<S, kSeg, false><<<g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx, seg);
 }
 
 cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx,
@@ -191,20 +197,21 @@ cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx,
   if (g > tiles) g = tiles;
   if (g < 1) g = 1;
   const SegArgs none{};
+  const bool may_pack = c.sort_kernel == kSortTiles && c.pack_keys != 0;
   if (seg) {
     switch (S) {
-      case 8: launch_s<8, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, st); break;
-      case 12: launch_s<12, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, st); break;
-      case 16: launch_s<16, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, st); break;
-      default: launch_s<20, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, st); break;
+      case 8: launch_s<8, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, may_pack, st); break;
+      case 12: launch_s<12, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, may_pack, st); break;
+      case 16: launch_s<16, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, may_pack, st); break;
+      default: launch_s<20, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, may_pack, st); break;
     }
   } else {
     switch (S) {
-      case 4: launch_s<4, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, st); break;
-      case 8: launch_s<8, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, st); break;
-      case 12: launch_s<12, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, st); break;
-      case 16: launch_s<16, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, st); break;
-      default: launch_s<20, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, st); break;
+      case 4: launch_s<4, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
+      case 8: launch_s<8, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
+      case 12: launch_s<12, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
+      case 16: launch_s<16, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
+      default: launch_s<20, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
     }
   }
   return cudaGetLastError();

@@ -36,20 +36,24 @@ struct PassInfo {
 
 // A skipped pass exits without a barrier: every thread reads the skip flag through the read-only
 // cache (written by an earlier kernel), so the CTAs of a skipped pass cost almost nothing.
+template <bool kCount = false>
 __device__ __forceinline__ PassInfo pass_info(const WsPtrs& ws, int d) {
   __shared__ PassInfo s_pi;
   if (__ldg(ws.plan->skip + d)) return PassInfo{0, 0, 0, 0, 0, 0};
   if (threadIdx.x == 0) {
     const Plan* plan = ws.plan;
     const uint32_t skip = plan->skip[d], U = plan->U, src = plan->src[d];
-    const int next = plan->next[d], first = plan->first;
+    const int next = plan->next[d];
     const uint32_t err = *(volatile const uint32_t*)&ws.ctrl->err;
     s_pi.U = U;
     s_pi.run = (!skip && err == 0) ? 1u : 0u;
     s_pi.src = src;
     s_pi.next = (uint32_t)(int32_t)next;
     s_pi.vary = plan->vary[d];
-    s_pi.keys = (d == first && d != 0 && !plan->plane_first) ? 1u : 0u;
+    if (kCount) {
+      const int first = plan->first;
+      s_pi.keys = (d == first && d != 0 && !plan->plane_first) ? 1u : 0u;
+    }
   }
   __syncthreads();
   const PassInfo pi = s_pi;
@@ -75,7 +79,7 @@ static_assert(kCntTiles == 2 * kWarps, "two tiles per warp");
 template <int S>
 __global__ void __launch_bounds__(kThreads, 4) k_tile_count(WsPtrs ws, int d) {
   __shared__ uint32_t h[kCntTiles * kHPad];
-  const PassInfo pi = pass_info(ws, d);
+  const PassInfo pi = pass_info<true>(ws, d);
   if (!pi.run) return;
   const uint32_t U = pi.U;
   const uint32_t ntiles = (U + kSortTile - 1) / kSortTile;

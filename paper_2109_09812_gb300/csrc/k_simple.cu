@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from
   if (t == 0) {
     int np = -1;
     plan->pack.on = 0;
-    if (from_masks) {
+    if (from_masks && allow_pack) {
       KeyPack kp{};
       int pos = 0, nraw = 0;
       bool fits = true;
