@@ -495,6 +495,12 @@ __device__ __forceinline__ uint32_t unpacked_word0(const uint32_t (&k)[K], const
   return v;
 }
 
+// Programmatic dependent launch: wait until the previous kernel on the stream has completed and
+// its writes are visible (returns at once for a kernel launched without the attribute), and let
+// the next kernel be scheduled once every CTA of this one has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // ---------------------------------------------------------------------------------------------
 // Memory-model helpers for decoupled look-back.
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {

@@ -35,6 +35,24 @@ inline LaunchCfg resolve_cfg(LaunchCfg c, int S, int64_t Umax, bool batched = fa
   return c;
 }
 
+// Launch with programmatic dependent launch: the kernel may be scheduled while the previous kernel
+// on the stream finishes; it must call pdl_wait() before reading anything that kernel wrote.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Per-device launch configuration (computed once per device and stride, thread-safe).
 LaunchCfg launch_cfg(int S);
 void set_launch_cfg(int S, const LaunchCfg& c);

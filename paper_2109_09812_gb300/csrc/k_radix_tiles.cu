@@ -79,6 +79,8 @@ static_assert(kCntTiles == 2 * kWarps, "two tiles per warp");
 template <int S>
 __global__ void __launch_bounds__(kThreads, 4) k_tile_count(WsPtrs ws, int d) {
   __shared__ uint32_t h[kCntTiles * kHPad];
+  pdl_wait();
+  pdl_trigger();
   const PassInfo pi = pass_info<true>(ws, d);
   if (!pi.run) return;
   const uint32_t U = pi.U;
@@ -144,6 +146,8 @@ constexpr int kOffBatch = 8;  // rows of 32 counts loaded together per warp
 __global__ void __launch_bounds__(kOffThreads, 2) k_tile_offsets(WsPtrs ws, int d) {
   __shared__ uint32_t s_seg[kOffWarps];
   __shared__ uint32_t s_below[kRadix / 32];
+  pdl_wait();
+  pdl_trigger();
   const PassInfo pi = pass_info(ws, d);
   if (!pi.run) return;
   const uint32_t ntiles = (pi.U + kSortTile - 1) / kSortTile;
@@ -213,6 +217,8 @@ __global__ void __launch_bounds__(kSortThreads, S >= 20 ? 1 : 2) k_tile_scatter(
   int32_t* goff = reinterpret_cast<int32_t*>(whist + kSortWarps * kRadix);     // [256] global - local pos
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(goff + 2 * kRadix);          // [32]
 
+  pdl_wait();
+  pdl_trigger();
   const PassInfo pi = pass_info(ws, d);
   if (!pi.run) return;
   Control* ctrl = ws.ctrl;
@@ -360,42 +366,39 @@ cudaError_t launch_tile_count(int S, int digit, WsPtrs ws, const LaunchCfg& c, c
   if (tiles < 1) return cudaSuccess;
   const int g = (int)((tiles + kCntTiles - 1) / kCntTiles);
   switch (S) {
-    case 4: k_tile_count<4><<<g, kThreads, 0, st>>>(ws, digit); break;
-    case 8: k_tile_count<8><<<g, kThreads, 0, st>>>(ws, digit); break;
-    case 12: k_tile_count<12><<<g, kThreads, 0, st>>>(ws, digit); break;
-    case 16: k_tile_count<16><<<g, kThreads, 0, st>>>(ws, digit); break;
-    default: k_tile_count<20><<<g, kThreads, 0, st>>>(ws, digit); break;
+    case 4: return launch_pdl(k_tile_count<4>, g, kThreads, 0, st, ws, digit);
+    case 8: return launch_pdl(k_tile_count<8>, g, kThreads, 0, st, ws, digit);
+    case 12: return launch_pdl(k_tile_count<12>, g, kThreads, 0, st, ws, digit);
+    case 16: return launch_pdl(k_tile_count<16>, g, kThreads, 0, st, ws, digit);
+    default: return launch_pdl(k_tile_count<20>, g, kThreads, 0, st, ws, digit);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_tile_offsets(int digit, WsPtrs ws, cudaStream_t st) {
   if (ws.Umax < 1) return cudaSuccess;
-  k_tile_offsets<<<kRadix, kOffThreads, 0, st>>>(ws, digit);
-  return cudaGetLastError();
+  return launch_pdl(k_tile_offsets, kRadix, kOffThreads, 0, st, ws, digit);
 }
 
 template <int S, int kMode>
-static void scatter_mode(int g, int digit, WsPtrs ws, cudaStream_t st) {
+static cudaError_t scatter_mode(int g, int digit, WsPtrs ws, cudaStream_t st) {
   const int word = S / 4 - 1 - (digit >> 2);  // word 0 is the most significant
   constexpr size_t sm = SortSmem<S>::bytes;
+  cudaError_t e = cudaSuccess;
   switch (word) {
-    case 0: k_tile_scatter<S, 0, kMode><<<g, kSortThreads, sm, st>>>(ws, digit); break;
-    case 1: if constexpr (S >= 8) k_tile_scatter<S, 1, kMode><<<g, kSortThreads, sm, st>>>(ws, digit); break;
-    case 2: if constexpr (S >= 12) k_tile_scatter<S, 2, kMode><<<g, kSortThreads, sm, st>>>(ws, digit); break;
-    case 3: if constexpr (S >= 16) k_tile_scatter<S, 3, kMode><<<g, kSortThreads, sm, st>>>(ws, digit); break;
-    default: if constexpr (S >= 20) k_tile_scatter<S, 4, kMode><<<g, kSortThreads, sm, st>>>(ws, digit); break;
+    case 0: e = launch_pdl(k_tile_scatter<S, 0, kMode>, g, kSortThreads, sm, st, ws, digit); break;
+    case 1: if constexpr (S >= 8) e = launch_pdl(k_tile_scatter<S, 1, kMode>, g, kSortThreads, sm, st, ws, digit); break;
+    case 2: if constexpr (S >= 12) e = launch_pdl(k_tile_scatter<S, 2, kMode>, g, kSortThreads, sm, st, ws, digit); break;
+    case 3: if constexpr (S >= 16) e = launch_pdl(k_tile_scatter<S, 3, kMode>, g, kSortThreads, sm, st, ws, digit); break;
+    default: if constexpr (S >= 20) e = launch_pdl(k_tile_scatter<S, 4, kMode>, g, kSortThreads, sm, st, ws, digit); break;
   }
+  return e;
 }
 
 template <int S>
-static void scatter_s(int g, int digit, WsPtrs ws, int mode, cudaStream_t st) {
-  if (mode == kRankMatchAny)
-    scatter_mode<S, kRankMatchAny>(g, digit, ws, st);
-  else if (mode == kRankBallotVary)
-    scatter_mode<S, kRankBallotVary>(g, digit, ws, st);
-  else
-    scatter_mode<S, kRankBallot>(g, digit, ws, st);
+static cudaError_t scatter_s(int g, int digit, WsPtrs ws, int mode, cudaStream_t st) {
+  if (mode == kRankMatchAny) return scatter_mode<S, kRankMatchAny>(g, digit, ws, st);
+  if (mode == kRankBallotVary) return scatter_mode<S, kRankBallotVary>(g, digit, ws, st);
+  return scatter_mode<S, kRankBallot>(g, digit, ws, st);
 }
 
 cudaError_t launch_tile_scatter(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st) {
@@ -405,13 +408,12 @@ cudaError_t launch_tile_scatter(int S, int digit, WsPtrs ws, const LaunchCfg& c,
   // CTAs that stride over the tiles
   const int g = (int)std::min<int64_t>(tiles, c.scatter_waves ? (int64_t)c.scatter_waves * c.sms * c.occ_tiles : tiles);
   switch (S) {
-    case 4: scatter_s<4>(g, digit, ws, c.rank_mode, st); break;
-    case 8: scatter_s<8>(g, digit, ws, c.rank_mode, st); break;
-    case 12: scatter_s<12>(g, digit, ws, c.rank_mode, st); break;
-    case 16: scatter_s<16>(g, digit, ws, c.rank_mode, st); break;
-    default: scatter_s<20>(g, digit, ws, c.rank_mode, st); break;
+    case 4: return scatter_s<4>(g, digit, ws, c.rank_mode, st);
+    case 8: return scatter_s<8>(g, digit, ws, c.rank_mode, st);
+    case 12: return scatter_s<12>(g, digit, ws, c.rank_mode, st);
+    case 16: return scatter_s<16>(g, digit, ws, c.rank_mode, st);
+    default: return scatter_s<20>(g, digit, ws, c.rank_mode, st);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace reindex
