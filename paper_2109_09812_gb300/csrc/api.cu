@@ -187,6 +187,8 @@ static reindex_status check_ptrs(const void* vtx, int64_t nVtx, int S, const int
 struct PipeExtras {
   std::function<cudaError_t(const WsPtrs&, const LaunchCfg&)> pre;
   bool flags_done = false;
+  cudaEvent_t vtx_ready = nullptr;   // the vertex array is complete once this event has fired
+  cudaEvent_t heads_done = nullptr;  // recorded once the unique vertices and *out_nVtx are written
 };
 
 // One radix pass (digit d) with the configured kernel variant.
@@ -228,6 +230,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
     prof::Scope s(REINDEX_K_USED_FLAGS, -1, st);
     REINDEX_TRY(launch_used_flags(idx, M, nVtx, p, c, st));
   }
+  if (extra && extra->vtx_ready) REINDEX_TRY(cudaStreamWaitEvent(st, extra->vtx_ready, 0));
   if (c.sort_kernel == kSortTiles && c.pack_keys) {  // bit masks -> plan (key packing) -> compaction
     {
       prof::Scope s(REINDEX_K_KEY_MASKS, -1, st);
@@ -253,6 +256,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
     prof::Scope s(REINDEX_K_HEAD_SCAN, -1, st);
     REINDEX_TRY(launch_head_scan(S, p, out_vtx, out_nVtx, (uint32_t)nVtx, c, nullptr, st));
   }
+  if (extra && extra->heads_done) REINDEX_TRY(cudaEventRecord(extra->heads_done, st));
   {
     prof::Scope s(REINDEX_K_REMAP, -1, st);
     REINDEX_TRY(launch_remap(idx, out_idx, M, p, c, st));
@@ -453,34 +457,62 @@ reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int S, cons
   const size_t b_out = align_up((size_t)L.Umax * S, 256);
   const size_t total = b_vtx + 2 * b_idx + b_out + 256 + L.total;
   set_pool_threshold();
+  // A second stream carries the vertex upload (while the used flags are set from the indices) and
+  // the download of the unique vertices (while the indices are remapped).
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_alloc = nullptr, ev_vtx = nullptr, ev_heads = nullptr, ev_cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  for (cudaEvent_t* ev : {&ev_alloc, &ev_vtx, &ev_heads, &ev_cs})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   unsigned char* d = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), total, st);
-  if (e != cudaSuccess) return cuda_status(e);
-  void* d_vtx = d;
-  int32_t* d_idx = reinterpret_cast<int32_t*>(d + b_vtx);
-  int32_t* d_oidx = reinterpret_cast<int32_t*>(d + b_vtx + b_idx);
-  void* d_ovtx = d + b_vtx + 2 * b_idx;
-  int64_t* d_n = reinterpret_cast<int64_t*>(d + b_vtx + 2 * b_idx + b_out);
-  void* d_ws = d + b_vtx + 2 * b_idx + b_out + 256;
-  int64_t D = -1;
-  do {
-    if ((e = cudaMemcpyAsync(d_vtx, host_vtx, (size_t)nVtx * S, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
-    if ((e = cudaMemcpyAsync(d_idx, host_idx, (size_t)M * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
-    r = run_pipeline(d_vtx, nVtx, S, d_idx, M, d_ovtx, d_n, d_oidx, d_ws, L, st);
-    if (r != REINDEX_OK) break;
-    if ((e = cudaMemcpyAsync(host_out_idx, d_oidx, (size_t)M * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
-    if ((e = cudaMemcpyAsync(&D, d_n, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
-    if (D > 0 &&
-        (e = cudaMemcpyAsync(host_out_vtx, d_ovtx, (size_t)D * S, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-      break;
-  } while (0);
-  cudaError_t ef = cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d), total, st);
+  int64_t D = -1, Dfinal = -1;
+  bool allocated = e == cudaSuccess;
+  if (allocated) {
+    void* d_vtx = d;
+    int32_t* d_idx = reinterpret_cast<int32_t*>(d + b_vtx);
+    int32_t* d_oidx = reinterpret_cast<int32_t*>(d + b_vtx + b_idx);
+    void* d_ovtx = d + b_vtx + 2 * b_idx;
+    int64_t* d_n = reinterpret_cast<int64_t*>(d + b_vtx + 2 * b_idx + b_out);
+    void* d_ws = d + b_vtx + 2 * b_idx + b_out + 256;
+    PipeExtras ex;
+    ex.vtx_ready = ev_vtx;
+    ex.heads_done = ev_heads;
+    do {
+      if ((e = cudaEventRecord(ev_alloc, st)) != cudaSuccess) break;
+      if ((e = cudaStreamWaitEvent(cs, ev_alloc, 0)) != cudaSuccess) break;
+      if ((e = cudaMemcpyAsync(d_vtx, host_vtx, (size_t)nVtx * S, cudaMemcpyHostToDevice, cs)) != cudaSuccess) break;
+      if ((e = cudaEventRecord(ev_vtx, cs)) != cudaSuccess) break;
+      if ((e = cudaMemcpyAsync(d_idx, host_idx, (size_t)M * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+      if ((e = cudaMemsetAsync(d_n, 0xFF, 8, st)) != cudaSuccess) break;  // -1 unless the head scan runs
+      r = run_pipeline(d_vtx, nVtx, S, d_idx, M, d_ovtx, d_n, d_oidx, d_ws, L, st, &ex);
+      if (r != REINDEX_OK) break;
+      if ((e = cudaMemcpyAsync(host_out_idx, d_oidx, (size_t)M * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+      // the unique count, then the unique vertices, on the second stream while the remap runs
+      if ((e = cudaStreamWaitEvent(cs, ev_heads, 0)) != cudaSuccess) break;
+      if ((e = cudaMemcpyAsync(&D, d_n, 8, cudaMemcpyDeviceToHost, cs)) != cudaSuccess) break;
+      if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) break;
+      if (D > 0 && D <= L.Umax &&
+          (e = cudaMemcpyAsync(host_out_vtx, d_ovtx, (size_t)D * S, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+        break;
+      if ((e = cudaEventRecord(ev_cs, cs)) != cudaSuccess) break;
+      if ((e = cudaStreamWaitEvent(st, ev_cs, 0)) != cudaSuccess) break;
+      // the final count: k_finalize replaces it by -status after a device-detected error
+      if ((e = cudaMemcpyAsync(&Dfinal, d_n, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+    } while (0);
+    cudaError_t ef = cudaFreeAsync(d, st);
+    if (e == cudaSuccess) e = ef;
+  }
   cudaError_t es = cudaStreamSynchronize(st);
+  cudaError_t es2 = cs ? cudaStreamSynchronize(cs) : cudaSuccess;
+  D = Dfinal;
+  for (cudaEvent_t ev : {ev_alloc, ev_vtx, ev_heads, ev_cs})
+    if (ev) cudaEventDestroy(ev);
+  if (cs) cudaStreamDestroy(cs);
   if (r != REINDEX_OK) return r;
   if (e != cudaSuccess) return cuda_status(e);
-  if (ef != cudaSuccess) return cuda_status(ef);
   if (es != cudaSuccess) return cuda_status(es);
+  if (es2 != cudaSuccess) return cuda_status(es2);
   *host_out_nVtx = D;
   if (D < 0) return (reindex_status)(-D);
   return REINDEX_OK;

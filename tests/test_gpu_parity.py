@@ -220,14 +220,35 @@ def test_cuda_graph_capture_of_workspace_variant(rx):
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
 
 
-def test_host_buffer_variant(rx):
-    m = synth.heightfield_soup(200, 150, 0.05, seed=6)
+@pytest.mark.parametrize("G,pinned", [(200, True), (1200, True), (64, False)])
+def test_host_buffer_variant(rx, G, pinned):
+    """Host buffers in and out; the vertex upload and the unique-vertex download overlap kernels on
+    a second stream.  1200^2 cells: large enough for the tiles sort."""
+    m = synth.heightfield_soup(G, (3 * G) // 4, 0.05, seed=6)
     ov, oi = oracle.reindex_sort(m.vtx, m.idx)
+    hv = torch.from_numpy(m.vtx.view(np.int32))
+    hi = torch.from_numpy(m.idx)
+    if pinned:
+        hv, hi = hv.pin_memory(), hi.pin_memory()
+    for _ in range(2):  # twice: nothing left over from the first call
+        out_v, out_i = rx.reindex_mesh_host(hv, hi)
+        np.testing.assert_array_equal(out_v.numpy().view(np.uint32), ov)
+        np.testing.assert_array_equal(out_i.numpy().reshape(-1), oi)
+
+
+def test_host_buffer_variant_reports_device_errors(rx):
+    m = synth.heightfield_soup(64, 64, 0.0, seed=7)
+    idx = m.idx.copy()
+    idx.reshape(-1)[12345] = m.n_vtx + 5  # out of range
     hv = torch.from_numpy(m.vtx.view(np.int32)).pin_memory()
-    hi = torch.from_numpy(m.idx).pin_memory()
-    out_v, out_i = rx.reindex_mesh_host(hv, hi)
+    hi = torch.from_numpy(idx).pin_memory()
+    with pytest.raises(rx.ReindexError) as ei:
+        rx.reindex_mesh_host(hv, hi)
+    assert ei.value.code == rx.REINDEX_ERR_INDEX_RANGE
+    rx.reindex_stream_status()  # clear the sticky word
+    out_v, out_i = rx.reindex_mesh_host(hv, torch.from_numpy(m.idx).pin_memory())  # and the next call works
+    ov, oi = oracle.reindex_sort(m.vtx, m.idx)
     np.testing.assert_array_equal(out_v.numpy().view(np.uint32), ov)
-    np.testing.assert_array_equal(out_i.numpy().reshape(-1), oi)
 
 
 SORT_KERNELS = {"regs": ["onesweep"], "tiles,pack=off": ["tile_count", "tile_offsets", "tile_scatter"],
