@@ -55,6 +55,12 @@ WORKLOADS = {
                      "every fifth unused), int32 idx x4", ("quad", 4096)),
     "quadgrid8192": ("quad grid 8192x8192 (Table 1 workload: 67,108,864 quads, float2 vertices, 5 per quad, "
                      "every fifth unused), int32 idx x4", ("quad", 8192)),
+    # The paper's other uses (Section 3): merging meshes and extracting a subset
+    "merge16": ("merging (Section 3.2): 16 heightfield soup patches of 512x512 cells (4x4 tiling of the 2048x2048 "
+                "field, float32 xyz, 5% unused each, each permuted, seed 2) into one mesh; vertices on shared patch "
+                "edges are duplicates across meshes (8,388,608 tris; 2049^2 unique vertices)", ("merge", 512, 4)),
+    "submesh30": ("subset (Section 3.4): the 2048x2048 heightfield soup (seed 2) with 30% of its triangles "
+                  "selected by a seeded hash, re-indexed against the full vertex array", ("submesh", 0.30)),
     # a half-size case of the 2048^2 workload, for profiler captures (still larger than L2)
     "heightfield1448": ("heightfield triangle soup 1448x1448 cells (4,193,408 tris, 12,580,224 soup vertices "
                         "float32 xyz + 5% unused, permuted), int32 idx x3, seed 2", (1448, 0.05, 2)),
@@ -220,6 +226,12 @@ def run_reference(args, world, rank):
         qn = min(cfg[1], 1024)
         sample = synth.quad_grid(qn)
         sample_desc = f"quad grid {qn}x{qn}, the same construction ({qn * qn:,} quads)"
+    elif isinstance(cfg, tuple) and cfg[0] == "merge":
+        sample = usecase_sample(cfg)
+        sample_desc = sample.name + " (merging = re-indexing the concatenation with offset indices)"
+    elif isinstance(cfg, tuple) and cfg[0] == "submesh":
+        sample = usecase_sample(cfg)
+        sample_desc = sample.name
     elif isinstance(cfg, tuple):
         sample = synth.heightfield_soup(min(cfg[0], 1024), min(cfg[0], 1024), cfg[1], cfg[2])
         sample_desc = f"heightfield soup {min(cfg[0], 1024)}^2 cells, same construction"
@@ -508,6 +520,157 @@ def step_model_bytes(N, S, M, U, D):
     return (4 * M + N / 8) + (N * S + N / 8 + U * W) + 2 * S * U * W + (U * W + 4 * U + D * S) + 12 * M
 
 
+def merge_patches(P, T, seed=2, unused=0.05):
+    """T x T heightfield patches of P x P cells tiling one field: (vtx, vtx_off, idx (local), elem_off)."""
+    from paper_2109_09812_gb300 import synth
+
+    meshes = [synth.heightfield_soup(P, P, unused, seed, origin=(P * i, P * j)) for j in range(T) for i in range(T)]
+    vtx = np.concatenate([m.vtx for m in meshes])
+    idx = np.concatenate([m.idx for m in meshes])
+    voff = np.concatenate([[0], np.cumsum([m.n_vtx for m in meshes])]).astype(np.int64)
+    eoff = np.concatenate([[0], np.cumsum([m.n_elem for m in meshes])]).astype(np.int64)
+    return vtx, voff, idx, eoff
+
+
+def subset_list(n_elem, frac, seed=2):
+    """Sorted element ids selected by a seeded hash (fraction frac)."""
+    from paper_2109_09812_gb300 import synth
+
+    u = synth.unit_float(synth.hash_u64(seed, 7, np.arange(n_elem, dtype=np.int64)))
+    return np.nonzero(u < np.float32(frac))[0].astype(np.int32)
+
+
+def usecase_sample(cfg):
+    """The bounded oracle sample of a merging / subset workload (a quarter-size instance)."""
+    from paper_2109_09812_gb300 import synth
+
+    if cfg[0] == "merge":
+        P, T = cfg[1] // 4, cfg[2]
+        v, voff, i, eoff = merge_patches(P, T)
+        gidx = (i + np.repeat(voff[:-1], np.diff(eoff))[:, None]).astype(np.int32)
+        return synth.Mesh(vtx=v, idx=gidx, expected_unique=(P * T + 1) ** 2,
+                          name=f"merge of {T * T} patches of {P}^2 cells ({int(i.shape[0]):,} tris)")
+    small = synth.heightfield_soup(1024, 1024, 0.05, 2)
+    ssel = subset_list(small.n_elem, cfg[1])
+    return synth.Mesh(vtx=small.vtx, idx=small.idx[ssel], name=f"heightfield 1024^2 cells with {cfg[1]:.0%} of its "
+                      f"triangles ({int(ssel.shape[0]):,} tris)")
+
+
+def run_usecase(args, world, rank, local):
+    """Merging and subset workloads: the same timing, per-kernel breakdown and baselines as the
+    single-mesh workloads, through reindex_merge_meshes / reindex_submesh."""
+    import torch
+
+    import paper_2109_09812_gb300 as rx
+    from paper_2109_09812_gb300 import build as rxbuild
+    from paper_2109_09812_gb300 import synth
+
+    if rank == 0 or world == 1:
+        rxbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfg = WORKLOADS[args.workload][1]
+    if cfg[0] == "merge":
+        P, T = cfg[1], cfg[2]
+        vtx_h, voff_h, idx_h, eoff_h = merge_patches(P, T)
+        vtx = torch.from_numpy(vtx_h.view(np.int32)).to(dev)
+        idx = torch.from_numpy(idx_h).to(dev)
+        voff, eoff = torch.from_numpy(voff_h).to(dev), torch.from_numpy(eoff_h).to(dev)
+        n_elem, expected = int(idx_h.shape[0]), (P * T + 1) ** 2
+        U, S, n_vtx = int(idx_h.size), 12, int(vtx_h.shape[0])
+        ws = torch.empty(rx.lib().reindex_merge_workspace_size(T * T, n_vtx, S, n_elem, 3), dtype=torch.uint8, device=dev)
+        out_v = torch.empty((min(n_vtx, 3 * n_elem), 3), dtype=torch.int32, device=dev)
+        out_n = torch.empty(1, dtype=torch.int64, device=dev)
+        out_i = torch.empty_like(idx)
+        step = lambda: rx.reindex_merge_meshes(vtx, voff, idx, eoff, ws=ws, out_vtx=out_v, out_nVtx=out_n,
+                                               out_idx=out_i)
+        sample_mesh = usecase_sample(cfg)
+    else:
+        mesh = synth.config_mesh(2)
+        sel = subset_list(mesh.n_elem, cfg[1])
+        vtx = torch.from_numpy(mesh.vtx.view(np.int32)).to(dev)
+        idx = torch.from_numpy(mesh.idx).to(dev)
+        elist = torch.from_numpy(sel).to(dev)
+        n_elem, n_vtx, S = int(sel.shape[0]), mesh.n_vtx, 12
+        keys = mesh.vtx.reshape(-1, 3)[mesh.idx[sel].reshape(-1)]
+        expected = int(np.unique(keys.view(np.dtype((np.void, 12)))).shape[0])
+        U = int(np.unique(mesh.idx[sel].reshape(-1)).shape[0])
+        ws = torch.empty(rx.lib().reindex_submesh_workspace_size(n_vtx, S, n_elem, 3), dtype=torch.uint8, device=dev)
+        out_v = torch.empty((min(n_vtx, 3 * n_elem), 3), dtype=torch.int32, device=dev)
+        out_n = torch.empty(1, dtype=torch.int64, device=dev)
+        out_i = torch.empty((n_elem, 3), dtype=torch.int32, device=dev)
+        step = lambda: rx.reindex_submesh(vtx, idx, elist, ws=ws, out_vtx=out_v, out_nVtx=out_n, out_idx=out_i)
+        sample_mesh = usecase_sample(cfg)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize(dev)
+    D = int(out_n.item())
+    if D != expected:
+        raise SystemExit(f"unexpected unique count {D} (expected {expected})")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1) / args.steps
+        rx.profile_collect()
+        rx.profile_enable(True)
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize(dev)
+        rx.profile_enable(False)
+    recs = rx.profile_collect()
+    ms = max_over_ranks(ms, world, dev)
+    value = whole_job_rate(n_elem, world, ms / 1e3)
+    per_kernel = {}
+    for r in recs:
+        key = r["name"] + (" (skipped)" if r["skipped"] else "")
+        a = per_kernel.setdefault(key, [0, 0.0])
+        a[0] += 1
+        a[1] += r["ms"]
+    kname = "tile_scatter" if any(r["name"] == "tile_scatter" for r in recs) else "onesweep"
+    sweeps = [r["ms"] for r in recs if r["name"] == kname and not r["skipped"]]
+    W = S + 4
+    peak, peak_kind = load_peaks()
+    avg_ms = sum(sweeps) / len(sweeps) if sweeps else float("nan")
+    alg_bytes = 2 * U * W
+    roofline = {"kernel": kname, "bound": "hbm", "achieved": alg_bytes / (avg_ms / 1e3) / 1e9, "peak": peak,
+                "unit": "GB/s", "frac": alg_bytes / (avg_ms / 1e3) / 1e9 / peak,
+                "peak_kind": f"{peak_kind} hbm_gbs (copy)", "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": avg_ms, "passes_per_step": len(sweeps) / args.steps}
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, secs = oracle_rate(sample_mesh)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{sample_mesh.name} ({sample_mesh.n_elem:,} elements, {secs:.1f} s), serial std::sort "
+                         "oracle, one thread"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][0], "n_vtx": n_vtx, "n_elem": n_elem, "stride_bytes": S,
+                   "idx_per_elem": 3, "unique_out": D, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": None, "tuning": rx.reindex_tuning_get(S),
+        "gpu_launches": len(recs),
+        "kernels": {k_: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k_, v in sorted(per_kernel.items())},
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -668,6 +831,8 @@ def main():
             run_batched_bench(args, world, rank, local)
         elif args.workload == "serving20000":
             run_serving_bench(args, world, rank, local)
+        elif args.workload in ("merge16", "submesh30"):
+            run_usecase(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

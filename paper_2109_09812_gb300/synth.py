@@ -175,14 +175,17 @@ def _append_unused_and_permute(soup: np.ndarray, n_extra: int, extra_fn, seed: i
 
 
 def heightfield_soup(G: int, Gy: int | None = None, unused_frac: float = 0.10, seed: int = 1,
-                     permute: bool = True) -> Mesh:
+                     permute: bool = True, origin: tuple = (0, 0)) -> Mesh:
     """Triangle soup of a G x Gy-cell heightfield (2 tris per cell, float32 xyz, 3 int32 indices).
 
     Vertex p(a, b) = (float(a), float(b), noise(a, b)); cell (i, j) emits the triangles
     (p(i,j), p(i+1,j), p(i+1,j+1)) and (p(i,j), p(i+1,j+1), p(i,j+1)), cells in row-major
     order (j outer).  round(unused_frac * 6*G*Gy) unreferenced vertices uniform in
-    [0,G] x [0,Gy] x [-2,2) are appended, then the vertex array is permuted."""
+    [0,G] x [0,Gy] x [-2,2) are appended, then the vertex array is permuted.  origin = (a0, b0)
+    places the patch at cells [a0, a0+G) x [b0, b0+Gy) of the same field, so that adjacent patches
+    share the vertices of their common edge bit for bit."""
     Gy = G if Gy is None else Gy
+    a0, b0 = int(origin[0]), int(origin[1])
     i = np.arange(G, dtype=np.int64)[None, :]
     j = np.arange(Gy, dtype=np.int64)[:, None]
     i = np.broadcast_to(i, (Gy, G)).reshape(-1)
@@ -193,12 +196,12 @@ def heightfield_soup(G: int, Gy: int | None = None, unused_frac: float = 0.10, s
     a = (i[:, None] + da[None, :]).reshape(-1)
     b = (j[:, None] + db[None, :]).reshape(-1)
     # evaluate the field once per lattice point, then gather (identical bits by construction)
-    la = np.arange(G + 1, dtype=np.int64)[None, :]
-    lb = np.arange(Gy + 1, dtype=np.int64)[:, None]
+    la = np.arange(a0, a0 + G + 1, dtype=np.int64)[None, :]
+    lb = np.arange(b0, b0 + Gy + 1, dtype=np.int64)[:, None]
     zlat = _value_noise_2d(np.broadcast_to(la, (Gy + 1, G + 1)), np.broadcast_to(lb, (Gy + 1, G + 1)), seed)
     soup = np.empty((a.shape[0], 3), dtype=np.float32)
-    soup[:, 0] = a.astype(np.float32)
-    soup[:, 1] = b.astype(np.float32)
+    soup[:, 0] = (a + a0).astype(np.float32)
+    soup[:, 1] = (b + b0).astype(np.float32)
     soup[:, 2] = zlat[b, a]
     m = soup.shape[0]
     n_extra = int(math.floor(unused_frac * m + 0.5))
@@ -208,8 +211,8 @@ def heightfield_soup(G: int, Gy: int | None = None, unused_frac: float = 0.10, s
         uy = unit_float(hash_u64(seed, TAG_EXTRA, 1, e))
         uz = unit_float(hash_u64(seed, TAG_EXTRA, 2, e))
         out = np.empty((e.shape[0], 3), dtype=np.float32)
-        out[:, 0] = ux * np.float32(G)
-        out[:, 1] = uy * np.float32(Gy)
+        out[:, 0] = ux * np.float32(G) + np.float32(a0)
+        out[:, 1] = uy * np.float32(Gy) + np.float32(b0)
         out[:, 2] = uz * np.float32(4.0) - np.float32(2.0)
         return out
 
