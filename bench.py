@@ -61,6 +61,15 @@ WORKLOADS = {
                 "edges are duplicates across meshes (8,388,608 tris; 2049^2 unique vertices)", ("merge", 512, 4)),
     "submesh30": ("subset (Section 3.4): the 2048x2048 heightfield soup (seed 2) with 30% of its triangles "
                   "selected by a seeded hash, re-indexed against the full vertex array", ("submesh", 0.30)),
+    # wider vertices: the 2048^2 soup with attribute words per lattice point (position + 3 normal-like
+    # words + 2 texture coordinates = 32 bytes; 24 bytes without the texture coordinates)
+    "heightfield2048_s32": ("heightfield triangle soup 2048x2048 cells with 32-byte vertices (float32 xyz + 3 "
+                            "normal-like words in [-1,1) + 2 texture coordinates in [0,1), each a hash of the "
+                            "position; 25,165,824 soup vertices + 5% unused, permuted), int32 idx x3, seed 2",
+                            (2048, 0.05, 2, 32)),
+    "heightfield2048_s24": ("heightfield triangle soup 2048x2048 cells with 24-byte vertices (float32 xyz + 3 "
+                            "normal-like words in [-1,1), each a hash of the position; 25,165,824 soup vertices "
+                            "+ 5% unused, permuted), int32 idx x3, seed 2", (2048, 0.05, 2, 24)),
     # a half-size case of the 2048^2 workload, for profiler captures (still larger than L2)
     "heightfield1448": ("heightfield triangle soup 1448x1448 cells (4,193,408 tris, 12,580,224 soup vertices "
                         "float32 xyz + 5% unused, permuted), int32 idx x3, seed 2", (1448, 0.05, 2)),
@@ -232,6 +241,9 @@ def run_reference(args, world, rank):
     elif isinstance(cfg, tuple) and cfg[0] == "submesh":
         sample = usecase_sample(cfg)
         sample_desc = sample.name
+    elif isinstance(cfg, tuple) and len(cfg) == 4:
+        sample = synth.heightfield_soup_attrs(1024, 1024, cfg[1], cfg[2], stride=cfg[3])
+        sample_desc = f"heightfield soup 1024^2 cells with {cfg[3]}-byte vertices, same construction"
     elif isinstance(cfg, tuple):
         sample = synth.heightfield_soup(min(cfg[0], 1024), min(cfg[0], 1024), cfg[1], cfg[2])
         sample_desc = f"heightfield soup {min(cfg[0], 1024)}^2 cells, same construction"
@@ -507,6 +519,19 @@ def build_mesh(workload):
     if isinstance(cfg, tuple) and cfg[0] == "quad":
         # the oracle on 268M used vertices would take minutes: time it on the 2048^2 grid
         return synth.quad_grid(cfg[1]), (synth.quad_grid(min(cfg[1], 2048)) if cfg[1] > 2048 else None)
+    if isinstance(cfg, tuple) and len(cfg) == 4:
+        # wide vertices, made by the device generators (bit-identical to synth.heightfield_soup_attrs,
+        # which is slow on the host at this size); the oracle is timed on 1024^2 cells
+        def gen(G):
+            import torch
+
+            v, i = synth.heightfield_soup_gpu(G, G, cfg[1], cfg[2])
+            w = synth.with_attributes_gpu(v.view(torch.int32), (cfg[3] - 12) // 4, cfg[2])
+            return synth.Mesh(vtx=w.cpu().numpy().view(np.uint32), idx=i.cpu().numpy(),
+                              name=f"heightfield soup {G}^2 cells, {cfg[3]}-byte vertices",
+                              expected_unique=(G + 1) ** 2)
+
+        return gen(cfg[0]), gen(1024)
     if isinstance(cfg, tuple):
         return synth.heightfield_soup(cfg[0], cfg[0], cfg[1], cfg[2]), None
     return synth.config_mesh(cfg), None

@@ -42,9 +42,12 @@
  *     reported after the stream is synchronised in two ways: *out_nVtx holds the NEGATED
  *     status code (e.g. -REINDEX_ERR_INDEX_RANGE), and reindex_stream_status() returns it.
  *     When one occurs the contents of out_vtx and out_idx are unspecified.
- *   - Supported strides: vtxStrideBytes in {4, 8, 12, 16, 20}.  vtx and out_vtx must be aligned
- *     to the stride's natural vector type: 4 bytes for S = 4, 12 and 20, 8 bytes for S = 8,
- *     16 bytes for S = 16.  idx and out_idx must be 4-byte aligned (16-byte alignment enables
+ *   - Supported strides: vtxStrideBytes in {4, 8, 12, 16, 20, 24, 32} for single meshes
+ *     (Section 3.5 expects other vertex formats to carry over directly: e.g. a position with a
+ *     normal, 24 bytes, or with a normal and texture coordinates, 32 bytes); the batched entry
+ *     point takes {4, 8, 12, 16}.  vtx and out_vtx must be aligned to the stride's natural
+ *     vector type: 4 bytes for S = 4, 12 and 20, 8 bytes for S = 8 and 24, 16 bytes for
+ *     S = 16 and 32.  idx and out_idx must be 4-byte aligned (16-byte alignment enables
  *     128-bit vector loads and stores).
  *   - nVtx <= 2^30 - 1 and nElem * idxPerElem <= 2^31 - 1 (int32 indices; the look-back
  *     status words pack a 30-bit count).
@@ -132,7 +135,7 @@ reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int vtxStri
  *   still the caller's device buffers).
  *   Limit: nVtx <= REINDEX_NOALLOC_MAX_VTX (262,144 vertices, any supported stride and any
  *   number of elements); a larger mesh returns REINDEX_ERR_UNSUPPORTED and nothing is launched.
- *   Scratch: one 16 MiB array of device memory inside the library, reserved on every device
+ *   Scratch: one 20 MiB array of device memory inside the library, reserved on every device
  *   that loads the library and held until the process exits.  The first call on a device looks
  *   up that array's device address (cudaGetSymbolAddress, with the device current) and caches
  *   it; make that first call before any stream capture on the device.

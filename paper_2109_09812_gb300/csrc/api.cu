@@ -159,11 +159,11 @@ static reindex_status cuda_status(cudaError_t e) {
 
 static bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
-static uintptr_t vtx_alignment(int S) { return S == 8 ? 8 : (S == 16 ? 16 : 4); }
+static uintptr_t vtx_alignment(int S) { return S % 16 == 0 ? 16 : (S % 8 == 0 ? 8 : 4); }
 
 // Host-side checks shared by every entry point.  Sets M.
 static reindex_status check_args(int64_t nVtx, int S, int64_t nElem, int k, int64_t* M) {
-  if (S != 4 && S != 8 && S != 12 && S != 16 && S != 20) return REINDEX_ERR_UNSUPPORTED;
+  if (S != 4 && S != 8 && S != 12 && S != 16 && S != 20 && S != 24 && S != 32) return REINDEX_ERR_UNSUPPORTED;
   if (nVtx < 0 || nElem < 0 || k < 1) return REINDEX_ERR_INVALID_ARG;
   if (nVtx > kMaxCount) return REINDEX_ERR_UNSUPPORTED;
   if (nElem > (int64_t)INT32_MAX / k) return REINDEX_ERR_UNSUPPORTED;

@@ -23,7 +23,9 @@ constexpr int kHeadIpt = 8;                // items per thread in the head scan
 constexpr int kHeadTile = kHeadThreads * kHeadIpt;         // 2048 items per tile
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;    // 256 digit values
-constexpr int kMaxDigits = 20;             // 20-byte keys (16-byte vertices + a mesh id) -> 20 digits
+constexpr int kMaxDigits = 32;             // 32-byte keys -> 32 byte digits
+constexpr int kWideMin = 24;               // keys of 24 and 32 bytes (single meshes) use the "tiles"
+                                           // sort with vary ranking only (fewer kernel variants)
 
 // Kernel variants (chosen per device by launch_cfg; see REINDEX_TUNE in api.cu).
 constexpr int kSortRegs = 0;      // radix pass with items in registers (k_onesweep)
@@ -67,11 +69,11 @@ constexpr uint32_t kErrInternal = 7;
 struct Control {             // zeroed at the start of every call
   uint32_t err;              // first device-detected error (0 = none)
   uint32_t U;                // number of used vertices (written by the last compaction tile)
-  uint32_t ctr[32];          // atomic tile counters: [0] compaction, [1 + d] sort digit d,
-                             // [1 + kMaxDigits] head scan
+  uint32_t ctr[2 + kMaxDigits];  // atomic tile counters: [0] compaction, [1 + d] sort digit d,
+                                 // [1 + kMaxDigits] head scan
   uint32_t kor[kMaxDigits / 4];   // OR of key word q over the used vertices (compaction, kHistNone)
   uint32_t knand[kMaxDigits / 4]; // OR of the complement: bit b varies iff set in both masks
-  uint32_t pad[20];
+  uint32_t pad[12];
 };
 static_assert(sizeof(Control) == 256, "Control block is one 256-byte line");
 
@@ -93,9 +95,9 @@ struct KeyPack {
   uint8_t simple;                  // 1: at most one run per word (wshift / wlen describe them)
   uint8_t wshift[kMaxDigits / 4];  // word q's run: lowest bit
   uint8_t wlen[kMaxDigits / 4];    //               and length (0: no varying bit)
-  uint8_t pad[2];
+  uint8_t pad[4];
 };
-static_assert(sizeof(KeyPack) == 80, "KeyPack layout");
+static_assert(sizeof(KeyPack) == 88, "KeyPack layout");
 
 struct Plan {                // written by the sort-plan kernel
   uint32_t U;
@@ -116,6 +118,10 @@ struct Plan {                // written by the sort-plan kernel
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Item buffers of S-byte keys: structure of arrays (a key plane, then an id plane) for S = 8, 16,
+// 24 and 32; array of structures {key, id} for S = 4, 12 and 20.
+__host__ __device__ constexpr bool soa_items(int S) { return S % 8 == 0; }
 
 struct WsLayout {
   int S = 0, K = 0, P = 0;
@@ -143,9 +149,9 @@ struct WsLayout {
     off_plan = o;        o = align_up(o + sizeof(Plan), 256);
     // SoA layouts keep the id plane 256-byte aligned; 256 spare bytes let bulk copies of a
     // ragged last tile round their size up to 16 bytes without leaving the buffer.
-    idoff = (S == 8 || S == 16) ? align_up((size_t)Umax * S, 256) : 0;
-    items_bytes = (S == 8 || S == 16) ? idoff + align_up((size_t)Umax * 4, 256) + 256
-                                      : align_up((size_t)Umax * (size_t)(S + 4), 256) + 256;
+    idoff = soa_items(S) ? align_up((size_t)Umax * S, 256) : 0;
+    items_bytes = soa_items(S) ? idoff + align_up((size_t)Umax * 4, 256) + 256
+                               : align_up((size_t)Umax * (size_t)(S + 4), 256) + 256;
     off_itemsA = o;      o += items_bytes;
     off_itemsB = o;      o += items_bytes;
     off_old2new = o;     o = align_up(o + (size_t)n * 4, 256);
@@ -170,7 +176,7 @@ struct WsPtrs {
                          // pass (of the first one: written by the compaction)
   int64_t tilesS;        // capacity of the sort look-back table, in tiles
   int64_t Umax;          // capacity of each item buffer, in items
-  int64_t idoff;         // byte offset of the id plane inside an item buffer (S = 8, 16)
+  int64_t idoff;         // byte offset of the id plane inside an item buffer (S = 8, 16, 24, 32)
 };
 
 inline WsPtrs ws_ptrs(void* ws, const WsLayout& L) {
@@ -224,6 +230,7 @@ __device__ __forceinline__ uint32_t seg_mesh(int64_t pos, const int64_t* off, in
 //   S = 20:    array of structures, three 8-byte vectors per item {k0,k1}{k2,k3}{k4,id}
 //   S = 8, 16: structure of arrays, an 8- or 16-byte key vector per item, then an id plane
 //              starting at byte offset idoff (256-byte aligned)
+//   S = 24, 32: structure of arrays, three 8-byte or two 16-byte vectors per key, then the id plane
 template <int S>
 struct Item {
   static constexpr int K = S / 4;
@@ -320,6 +327,53 @@ struct ItemIO<20> {
   }
 };
 
+template <>
+struct ItemIO<24> {
+  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t idoff, int64_t i, Item<24>& it) {
+    const uint2* p = reinterpret_cast<const uint2*>(buf) + 3 * i;
+    const uint2 a = p[0], b = p[1], c = p[2];
+    it.k[0] = a.x; it.k[1] = a.y; it.k[2] = b.x; it.k[3] = b.y; it.k[4] = c.x; it.k[5] = c.y;
+    it.id = reinterpret_cast<const uint32_t*>(buf + idoff)[i];
+  }
+  static __device__ __forceinline__ void load_cs(const unsigned char* buf, int64_t idoff, int64_t i, Item<24>& it) {
+    const uint2* p = reinterpret_cast<const uint2*>(buf) + 3 * i;
+    const uint2 a = __ldcs(p), b = __ldcs(p + 1), c = __ldcs(p + 2);
+    it.k[0] = a.x; it.k[1] = a.y; it.k[2] = b.x; it.k[3] = b.y; it.k[4] = c.x; it.k[5] = c.y;
+    it.id = __ldcs(reinterpret_cast<const uint32_t*>(buf + idoff) + i);
+  }
+  static __device__ __forceinline__ void store(unsigned char* buf, int64_t idoff, int64_t i, const Item<24>& it) {
+    uint2* p = reinterpret_cast<uint2*>(buf) + 3 * i;
+    p[0] = make_uint2(it.k[0], it.k[1]);
+    p[1] = make_uint2(it.k[2], it.k[3]);
+    p[2] = make_uint2(it.k[4], it.k[5]);
+    reinterpret_cast<uint32_t*>(buf + idoff)[i] = it.id;
+  }
+};
+
+template <>
+struct ItemIO<32> {
+  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t idoff, int64_t i, Item<32>& it) {
+    const uint4* p = reinterpret_cast<const uint4*>(buf) + 2 * i;
+    const uint4 a = p[0], b = p[1];
+    it.k[0] = a.x; it.k[1] = a.y; it.k[2] = a.z; it.k[3] = a.w;
+    it.k[4] = b.x; it.k[5] = b.y; it.k[6] = b.z; it.k[7] = b.w;
+    it.id = reinterpret_cast<const uint32_t*>(buf + idoff)[i];
+  }
+  static __device__ __forceinline__ void load_cs(const unsigned char* buf, int64_t idoff, int64_t i, Item<32>& it) {
+    const uint4* p = reinterpret_cast<const uint4*>(buf) + 2 * i;
+    const uint4 a = __ldcs(p), b = __ldcs(p + 1);
+    it.k[0] = a.x; it.k[1] = a.y; it.k[2] = a.z; it.k[3] = a.w;
+    it.k[4] = b.x; it.k[5] = b.y; it.k[6] = b.z; it.k[7] = b.w;
+    it.id = __ldcs(reinterpret_cast<const uint32_t*>(buf + idoff) + i);
+  }
+  static __device__ __forceinline__ void store(unsigned char* buf, int64_t idoff, int64_t i, const Item<32>& it) {
+    uint4* p = reinterpret_cast<uint4*>(buf) + 2 * i;
+    p[0] = make_uint4(it.k[0], it.k[1], it.k[2], it.k[3]);
+    p[1] = make_uint4(it.k[4], it.k[5], it.k[6], it.k[7]);
+    reinterpret_cast<uint32_t*>(buf + idoff)[i] = it.id;
+  }
+};
+
 // Vertex key loads from the caller's vertex array (stride S, natural alignment).
 // (streaming: the caller's vertex array is read once per call)
 template <int S>
@@ -335,6 +389,14 @@ __device__ __forceinline__ void load_key(const void* vtx, int64_t i, uint32_t (&
   } else if constexpr (S == 16) {
     uint4 v = __ldcs(reinterpret_cast<const uint4*>(vtx) + i);
     k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+  } else if constexpr (S == 24) {
+    const uint2* p = reinterpret_cast<const uint2*>(vtx) + 3 * i;
+    const uint2 a = __ldcs(p), b = __ldcs(p + 1), c = __ldcs(p + 2);
+    k[0] = a.x; k[1] = a.y; k[2] = b.x; k[3] = b.y; k[4] = c.x; k[5] = c.y;
+  } else if constexpr (S == 32) {
+    const uint4* p = reinterpret_cast<const uint4*>(vtx) + 2 * i;
+    const uint4 a = __ldcs(p), b = __ldcs(p + 1);
+    k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w; k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
   } else {
     const uint32_t* p = reinterpret_cast<const uint32_t*>(vtx) + i * (S / 4);
 #pragma unroll
@@ -354,6 +416,12 @@ __device__ __forceinline__ void store_key(void* out, int64_t i, const uint32_t (
     __stcs(p, k[0]); __stcs(p + 1, k[1]); __stcs(p + 2, k[2]);
   } else if constexpr (S == 16) {
     __stcs(reinterpret_cast<uint4*>(out) + i, make_uint4(k[0], k[1], k[2], k[3]));
+  } else if constexpr (S == 24) {
+    uint2* p = reinterpret_cast<uint2*>(out) + 3 * i;
+    __stcs(p, make_uint2(k[0], k[1])); __stcs(p + 1, make_uint2(k[2], k[3])); __stcs(p + 2, make_uint2(k[4], k[5]));
+  } else if constexpr (S == 32) {
+    uint4* p = reinterpret_cast<uint4*>(out) + 2 * i;
+    __stcs(p, make_uint4(k[0], k[1], k[2], k[3])); __stcs(p + 1, make_uint4(k[4], k[5], k[6], k[7]));
   } else {
     uint32_t* p = reinterpret_cast<uint32_t*>(out) + i * (S / 4);
 #pragma unroll

@@ -29,7 +29,12 @@ struct LaunchCfg {
 
 // The configuration for one call: kSortAuto resolved for S-byte keys and up to Umax items.
 // batched: the call sorts (mesh id, vertex) keys, whose mesh-id bytes are mostly constant.
+// 24- and 32-byte keys always take the "tiles" sort with vary ranking (the only variants built).
 inline LaunchCfg resolve_cfg(LaunchCfg c, int S, int64_t Umax, bool batched = false) {
+  if (S >= kWideMin) {
+    c.sort_kernel = kSortTiles;
+    c.rank_mode = kRankBallotVary;
+  }
   if (c.sort_kernel == kSortAuto) c.sort_kernel = Umax >= kTilesMinItems ? kSortTiles : kSortRegs;
   if (c.pack_keys < 0) c.pack_keys = (batched || S <= 8) ? 1 : 0;
   return c;

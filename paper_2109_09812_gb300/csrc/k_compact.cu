@@ -276,13 +276,15 @@ __global__ void __launch_bounds__(kThreads) k_key_masks(const void* __restrict__
 template <int S>
 static int occ() {
   int a = 0, b = 0, c = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistUniform, false>, kThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistPeel, false>, kThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_compact<S, kHistMatchAny, false>, kThreads, 0);
-  int n = min(a, min(b, c));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistNone, false>, kThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistMasks, false>, kThreads, 0);
-  n = min(n, min(a, b));
+  int n = min(a, b);
+  if constexpr (S < kWideMin) {  // upfront histograms (onesweep sort) for keys of up to 20 bytes
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistUniform, false>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistPeel, false>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_compact<S, kHistMatchAny, false>, kThreads, 0);
+    n = min(n, min(a, min(b, c)));
+  }
   if constexpr (S <= 16) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistUniform, true>, kThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistNone, true>, kThreads, 0);
@@ -298,7 +300,9 @@ int occupancy_compact(int S) {
     case 8: return occ<8>();
     case 12: return occ<12>();
     case 16: return occ<16>();
-    default: return occ<20>();
+    case 20: return occ<20>();
+    case 24: return occ<24>();
+    default: return occ<32>();
   }
 }
 
@@ -327,8 +331,10 @@ static void launch_s(int64_t g, int sms, bool persistent, const void* vtx, int64
                      int mode, const SegArgs& seg, cudaStream_t st) {
   if (mode == kHistNone)
     launch_v<S, kHistNone, kSeg>(g, sms, persistent, vtx, nVtx, ws, tilesV, seg, st);
-  else if (mode == kHistMasks)
+  else if (mode == kHistMasks || S >= kWideMin)  // 24- and 32-byte keys: "tiles" sort only
     launch_v<S, kHistMasks, kSeg>(g, sms, persistent, vtx, nVtx, ws, tilesV, seg, st);
+  else if constexpr (S >= kWideMin)
+    return;
   else if (kSeg || mode == kHistUniform)
     launch_v<S, kHistUniform, kSeg>(g, sms, persistent, vtx, nVtx, ws, tilesV, seg, st);
   else if (mode == kHistMatchAny)
@@ -358,7 +364,10 @@ cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int6
       case 8: launch_s<8, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
       case 12: launch_s<12, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
       case 16: launch_s<16, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
-      default: launch_s<20, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      case 20: launch_s<20, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      case 24: launch_s<24, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      case 32: launch_s<32, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      default: return cudaErrorInvalidValue;
     }
   }
   return cudaGetLastError();
@@ -388,7 +397,10 @@ cudaError_t launch_key_masks(int S, const void* vtx, int64_t nVtx, WsPtrs ws, co
       case 8: REINDEX_KM(8, false); break;
       case 12: REINDEX_KM(12, false); break;
       case 16: REINDEX_KM(16, false); break;
-      default: REINDEX_KM(20, false); break;
+      case 20: REINDEX_KM(20, false); break;
+      case 24: REINDEX_KM(24, false); break;
+      case 32: REINDEX_KM(32, false); break;
+      default: return cudaErrorInvalidValue;
     }
   }
 #undef REINDEX_KM

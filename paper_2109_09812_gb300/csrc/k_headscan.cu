@@ -177,7 +177,9 @@ int occupancy_head(int S) {
     case 8: return occ<8>();
     case 12: return occ<12>();
     case 16: return occ<16>();
-    default: return occ<20>();
+    case 20: return occ<20>();
+    case 24: return occ<24>();
+    default: return occ<32>();
   }
 }
 
@@ -211,7 +213,10 @@ cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx,
       case 8: launch_s<8, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
       case 12: launch_s<12, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
       case 16: launch_s<16, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
-      default: launch_s<20, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
+      case 20: launch_s<20, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
+      case 24: launch_s<24, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
+      case 32: launch_s<32, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
+      default: return cudaErrorInvalidValue;
     }
   }
   return cudaGetLastError();

@@ -192,7 +192,8 @@ int occupancy_sort(int S) {
     case 8: return occ<8>();
     case 12: return occ<12>();
     case 16: return occ<16>();
-    default: return occ<20>();
+    case 20: return occ<20>();
+    default: return 1;  // 24- and 32-byte keys use the "tiles" sort only
   }
 }
 
@@ -225,7 +226,8 @@ cudaError_t launch_onesweep(int S, int digit, WsPtrs ws, const LaunchCfg& c, cud
     case 8: launch_s<8>((int)g, digit, ws, c.rank_mode, st); break;
     case 12: launch_s<12>((int)g, digit, ws, c.rank_mode, st); break;
     case 16: launch_s<16>((int)g, digit, ws, c.rank_mode, st); break;
-    default: launch_s<20>((int)g, digit, ws, c.rank_mode, st); break;
+    case 20: launch_s<20>((int)g, digit, ws, c.rank_mode, st); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

@@ -339,7 +339,8 @@ int occupancy_sort_pipe(int S) {
     case 8: return occ<8>();
     case 12: return occ<12>();
     case 16: return occ<16>();
-    default: return occ<20>();
+    case 20: return occ<20>();
+    default: return 0;  // 24- and 32-byte keys use the "tiles" sort only
   }
 }
 
@@ -366,7 +367,8 @@ cudaError_t launch_onesweep_pipe(int S, int digit, WsPtrs ws, const LaunchCfg& c
     case 8: launch_s<8>((int)g, digit, ws, st); break;
     case 12: launch_s<12>((int)g, digit, ws, st); break;
     case 16: launch_s<16>((int)g, digit, ws, st); break;
-    default: launch_s<20>((int)g, digit, ws, st); break;
+    case 20: launch_s<20>((int)g, digit, ws, st); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

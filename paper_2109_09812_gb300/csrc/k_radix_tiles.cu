@@ -64,7 +64,7 @@ __device__ __forceinline__ PassInfo pass_info(const WsPtrs& ws, int d) {
 // Word `word` of item i's key, read from an item buffer.
 template <int S>
 __device__ __forceinline__ uint32_t item_key_word(const unsigned char* buf, int64_t i, int word) {
-  constexpr int kStride = (S == 8 || S == 16) ? S / 4 : S / 4 + 1;  // words per item in the key array
+  constexpr int kStride = soa_items(S) ? S / 4 : S / 4 + 1;  // words per item in the key array
   return reinterpret_cast<const uint32_t*>(buf)[i * kStride + word];
 }
 
@@ -336,19 +336,20 @@ static int occ_one() {
   return n < 1 ? 1 : n;
 }
 
-template <int S, int kMode>
+template <int S, int kMode, int kWord = 0>
 static int occ_mode() {
-  int n = occ_one<S, 0, kMode>();
-  if constexpr (S >= 8) n = min(n, occ_one<S, 1, kMode>());
-  if constexpr (S >= 12) n = min(n, occ_one<S, 2, kMode>());
-  if constexpr (S >= 16) n = min(n, occ_one<S, 3, kMode>());
-  if constexpr (S >= 20) n = min(n, occ_one<S, 4, kMode>());
+  const int n = occ_one<S, kWord, kMode>();
+  if constexpr (kWord + 1 < S / 4) return min(n, occ_mode<S, kMode, kWord + 1>());
   return n;
 }
 
+// 24- and 32-byte keys are ranked with the vary ballots only.
 template <int S>
 static int occ() {
-  return min(occ_mode<S, kRankBallot>(), min(occ_mode<S, kRankMatchAny>(), occ_mode<S, kRankBallotVary>()));
+  if constexpr (S >= kWideMin)
+    return occ_mode<S, kRankBallotVary>();
+  else
+    return min(occ_mode<S, kRankBallot>(), min(occ_mode<S, kRankMatchAny>(), occ_mode<S, kRankBallotVary>()));
 }
 
 int occupancy_tiles(int S) {
@@ -357,7 +358,9 @@ int occupancy_tiles(int S) {
     case 8: return occ<8>();
     case 12: return occ<12>();
     case 16: return occ<16>();
-    default: return occ<20>();
+    case 20: return occ<20>();
+    case 24: return occ<24>();
+    default: return occ<32>();
   }
 }
 
@@ -370,7 +373,10 @@ cudaError_t launch_tile_count(int S, int digit, WsPtrs ws, const LaunchCfg& c, c
     case 8: return launch_pdl(k_tile_count<8>, g, kThreads, 0, st, ws, digit);
     case 12: return launch_pdl(k_tile_count<12>, g, kThreads, 0, st, ws, digit);
     case 16: return launch_pdl(k_tile_count<16>, g, kThreads, 0, st, ws, digit);
-    default: return launch_pdl(k_tile_count<20>, g, kThreads, 0, st, ws, digit);
+    case 20: return launch_pdl(k_tile_count<20>, g, kThreads, 0, st, ws, digit);
+    case 24: return launch_pdl(k_tile_count<24>, g, kThreads, 0, st, ws, digit);
+    case 32: return launch_pdl(k_tile_count<32>, g, kThreads, 0, st, ws, digit);
+    default: return cudaErrorInvalidValue;
   }
 }
 
@@ -379,26 +385,26 @@ cudaError_t launch_tile_offsets(int digit, WsPtrs ws, cudaStream_t st) {
   return launch_pdl(k_tile_offsets, kRadix, kOffThreads, 0, st, ws, digit);
 }
 
-template <int S, int kMode>
-static cudaError_t scatter_mode(int g, int digit, WsPtrs ws, cudaStream_t st) {
-  const int word = S / 4 - 1 - (digit >> 2);  // word 0 is the most significant
-  constexpr size_t sm = SortSmem<S>::bytes;
-  cudaError_t e = cudaSuccess;
-  switch (word) {
-    case 0: e = launch_pdl(k_tile_scatter<S, 0, kMode>, g, kSortThreads, sm, st, ws, digit); break;
-    case 1: if constexpr (S >= 8) e = launch_pdl(k_tile_scatter<S, 1, kMode>, g, kSortThreads, sm, st, ws, digit); break;
-    case 2: if constexpr (S >= 12) e = launch_pdl(k_tile_scatter<S, 2, kMode>, g, kSortThreads, sm, st, ws, digit); break;
-    case 3: if constexpr (S >= 16) e = launch_pdl(k_tile_scatter<S, 3, kMode>, g, kSortThreads, sm, st, ws, digit); break;
-    default: if constexpr (S >= 20) e = launch_pdl(k_tile_scatter<S, 4, kMode>, g, kSortThreads, sm, st, ws, digit); break;
-  }
-  return e;
+// The pass over key word `word` (word 0 is the most significant), one instantiation per word.
+template <int S, int kMode, int kWord = 0>
+static cudaError_t scatter_word(int word, int g, int digit, WsPtrs ws, cudaStream_t st) {
+  if (word == kWord)
+    return launch_pdl(k_tile_scatter<S, kWord, kMode>, g, kSortThreads, SortSmem<S>::bytes, st, ws, digit);
+  if constexpr (kWord + 1 < S / 4) return scatter_word<S, kMode, kWord + 1>(word, g, digit, ws, st);
+  return cudaErrorInvalidValue;
 }
 
 template <int S>
 static cudaError_t scatter_s(int g, int digit, WsPtrs ws, int mode, cudaStream_t st) {
-  if (mode == kRankMatchAny) return scatter_mode<S, kRankMatchAny>(g, digit, ws, st);
-  if (mode == kRankBallotVary) return scatter_mode<S, kRankBallotVary>(g, digit, ws, st);
-  return scatter_mode<S, kRankBallot>(g, digit, ws, st);
+  const int word = S / 4 - 1 - (digit >> 2);
+  if constexpr (S >= kWideMin) {
+    if (mode != kRankBallotVary) return cudaErrorInvalidValue;
+    return scatter_word<S, kRankBallotVary>(word, g, digit, ws, st);
+  } else {
+    if (mode == kRankMatchAny) return scatter_word<S, kRankMatchAny>(word, g, digit, ws, st);
+    if (mode == kRankBallotVary) return scatter_word<S, kRankBallotVary>(word, g, digit, ws, st);
+    return scatter_word<S, kRankBallot>(word, g, digit, ws, st);
+  }
 }
 
 cudaError_t launch_tile_scatter(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st) {
@@ -412,7 +418,10 @@ cudaError_t launch_tile_scatter(int S, int digit, WsPtrs ws, const LaunchCfg& c,
     case 8: return scatter_s<8>(g, digit, ws, c.rank_mode, st);
     case 12: return scatter_s<12>(g, digit, ws, c.rank_mode, st);
     case 16: return scatter_s<16>(g, digit, ws, c.rank_mode, st);
-    default: return scatter_s<20>(g, digit, ws, c.rank_mode, st);
+    case 20: return scatter_s<20>(g, digit, ws, c.rank_mode, st);
+    case 24: return scatter_s<24>(g, digit, ws, c.rank_mode, st);
+    case 32: return scatter_s<32>(g, digit, ws, c.rank_mode, st);
+    default: return cudaErrorInvalidValue;
   }
 }
 

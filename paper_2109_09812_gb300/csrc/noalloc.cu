@@ -8,7 +8,7 @@
 // They pass inputs and outputs as usual; the scratch is the static array below.
 //
 // The array is a file-scope __device__ variable, so every device that loads this library holds
-// it (16 MiB) until the process exits.  Host code only sees a stand-in for its name; the real
+// it (20 MiB) until the process exits.  Host code only sees a stand-in for its name; the real
 // device address is looked up once per device with cudaGetSymbolAddress (with that device
 // current) and cached.  Every call shares the array: the pipeline's first kernel zeroes the
 // parts that must start at zero, and calls whose work overlaps on the GPU (for example two
@@ -19,7 +19,7 @@
 
 namespace {
 
-constexpr size_t kScratchBytes = 16u << 20;  // 16 MiB, enough for nVtx <= REINDEX_NOALLOC_MAX_VTX
+constexpr size_t kScratchBytes = 20u << 20;  // 20 MiB, enough (for every stride) for nVtx <= REINDEX_NOALLOC_MAX_VTX
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 

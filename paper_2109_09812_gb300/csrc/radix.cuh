@@ -8,7 +8,7 @@
 namespace reindex {
 
 // Shared-memory staging of one tile: a vector per item (the key words, plus the old index for
-// the array-of-structures layouts) and, for S = 8 and 16, a separate old-index plane.
+// the array-of-structures layouts) and, for S = 8, 16, 24 and 32, a separate old-index plane.
 template <int S>
 struct Stage;
 
@@ -74,6 +74,42 @@ struct Stage<20> {
     const uint2* q = reinterpret_cast<const uint2*>(sm) + 3 * p;
     const uint2 a = q[0], b = q[1], c = q[2];
     it.k[0] = a.x; it.k[1] = a.y; it.k[2] = b.x; it.k[3] = b.y; it.k[4] = c.x; it.id = c.y;
+  }
+};
+
+// 24- and 32-byte keys: key vectors, then the old-index plane.
+template <>
+struct Stage<24> {
+  static constexpr size_t bytes = (size_t)kSortTile * 28;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<24>& it) {
+    uint2* q = reinterpret_cast<uint2*>(sm) + 3 * p;
+    q[0] = make_uint2(it.k[0], it.k[1]);
+    q[1] = make_uint2(it.k[2], it.k[3]);
+    q[2] = make_uint2(it.k[4], it.k[5]);
+    reinterpret_cast<uint32_t*>(sm + (size_t)kSortTile * 24)[p] = it.id;
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<24>& it) {
+    const uint2* q = reinterpret_cast<const uint2*>(sm) + 3 * p;
+    const uint2 a = q[0], b = q[1], c = q[2];
+    it.k[0] = a.x; it.k[1] = a.y; it.k[2] = b.x; it.k[3] = b.y; it.k[4] = c.x; it.k[5] = c.y;
+    it.id = reinterpret_cast<const uint32_t*>(sm + (size_t)kSortTile * 24)[p];
+  }
+};
+template <>
+struct Stage<32> {
+  static constexpr size_t bytes = (size_t)kSortTile * 36;
+  static __device__ __forceinline__ void put(unsigned char* sm, int p, const Item<32>& it) {
+    uint4* q = reinterpret_cast<uint4*>(sm) + 2 * p;
+    q[0] = make_uint4(it.k[0], it.k[1], it.k[2], it.k[3]);
+    q[1] = make_uint4(it.k[4], it.k[5], it.k[6], it.k[7]);
+    reinterpret_cast<uint32_t*>(sm + (size_t)kSortTile * 32)[p] = it.id;
+  }
+  static __device__ __forceinline__ void get(const unsigned char* sm, int p, Item<32>& it) {
+    const uint4* q = reinterpret_cast<const uint4*>(sm) + 2 * p;
+    const uint4 a = q[0], b = q[1];
+    it.k[0] = a.x; it.k[1] = a.y; it.k[2] = a.z; it.k[3] = a.w;
+    it.k[4] = b.x; it.k[5] = b.y; it.k[6] = b.z; it.k[7] = b.w;
+    it.id = reinterpret_cast<const uint32_t*>(sm + (size_t)kSortTile * 32)[p];
   }
 };
 

@@ -105,8 +105,10 @@ reindex_status reindex_autotune(const void* vtx, int64_t nVtx, int S, const int3
                             {"grid=persist", "grid=tile", nullptr, nullptr},
                             {"swaves=tile", "swaves=1", "swaves=4", nullptr},
                             {"pack=auto", "pack=on", "pack=off", nullptr}};
-  for (auto& knob : knobs) {
+  for (int ki = 0; ki < 6; ++ki) {
+    const auto& knob = knobs[ki];
     if (rs != REINDEX_OK) break;
+    if (S >= kWideMin && ki < 3) continue;  // 24- and 32-byte keys: one sort and rank variant only
     for (const char* v : knob) {
       if (!v) continue;
       LaunchCfg c = best;

@@ -45,6 +45,7 @@ TAG_PERM = 3
 TAG_JITTER = 4
 TAG_FIELD = 5
 TAG_SIZES = 6
+TAG_ATTR = 7
 
 
 def splitmix64(x: np.ndarray) -> np.ndarray:
@@ -222,6 +223,34 @@ def heightfield_soup(G: int, Gy: int | None = None, unused_frac: float = 0.10, s
                 meta=dict(G=G, Gy=Gy, unused_frac=unused_frac, seed=seed, n_extra=n_extra))
 
 
+def with_attributes(vtx_words: np.ndarray, n_attr: int, seed: int) -> np.ndarray:
+    """Appends n_attr float32 attribute words to every vertex (e.g. 3 -> a 24-byte position +
+    normal vertex, 5 -> 32 bytes with texture coordinates).  Attribute q of a vertex is a function
+    of its key words only, so bit-identical vertices stay bit-identical and the unique count is
+    unchanged:  h = hash(seed, TAG_ATTR, q, w0, w1, ...);  q < 3: unit_float(h) * 2 - 1 (a
+    normal-like component in [-1, 1)),  q >= 3: unit_float(h) (a texture coordinate in [0, 1))."""
+    vtx_words = np.ascontiguousarray(vtx_words, dtype=np.uint32)
+    n, k0 = vtx_words.shape
+    out = np.empty((n, k0 + n_attr), dtype=np.uint32)
+    out[:, :k0] = vtx_words
+    cols = [vtx_words[:, c].astype(np.int64) for c in range(k0)]
+    for q in range(n_attr):
+        u = unit_float(hash_u64(seed, TAG_ATTR, q, *cols))
+        if q < 3:
+            u = u * np.float32(2.0) - np.float32(1.0)
+        out[:, k0 + q] = u.astype(np.float32).view(np.uint32)
+    return out
+
+
+def heightfield_soup_attrs(G: int, Gy: int | None = None, unused_frac: float = 0.10, seed: int = 1,
+                           stride: int = 32, permute: bool = True) -> Mesh:
+    """heightfield_soup with (stride - 12) / 4 attribute words per vertex (with_attributes)."""
+    m = heightfield_soup(G, Gy, unused_frac, seed, permute)
+    vtx = with_attributes(m.vtx, (stride - 12) // 4, seed)
+    return Mesh(vtx=vtx, idx=m.idx, name=f"{m.name}_s{stride}", expected_unique=m.expected_unique,
+                meta=dict(m.meta, stride=stride))
+
+
 def _value_noise_3d(a, b, c, seed: int, cs: int = 16) -> np.ndarray:
     ca, cb, cc = a // cs, b // cs, c // cs
     inv = np.float32(1.0 / cs)
@@ -352,6 +381,8 @@ def _gpu_lib():
         L.synth_heightfield.restype = ctypes.c_int
         L.synth_tets.argtypes = [vp, vp, i64, i64, ctypes.c_uint64, ctypes.c_int, vp]
         L.synth_tets.restype = ctypes.c_int
+        L.synth_attributes.argtypes = [vp, i64, ctypes.c_int, vp, ctypes.c_int, ctypes.c_uint64, vp]
+        L.synth_attributes.restype = ctypes.c_int
         _synth_lib = L
     return _synth_lib
 
@@ -380,6 +411,23 @@ def heightfield_soup_gpu(G: int, Gy: int | None = None, unused_frac: float = 0.1
     if rc:
         raise RuntimeError(f"synth_heightfield: CUDA error {rc}")
     return vtx, idx
+
+
+def with_attributes_gpu(vtx, n_attr: int, seed: int, stream=None):
+    """with_attributes on the GPU: vtx is a CUDA tensor (N, k0) of 4-byte words; returns an int32
+    (N, k0 + n_attr) CUDA tensor, bit-identical to the host generator."""
+    import ctypes
+
+    import torch
+
+    vtx = vtx.contiguous()
+    n, k0 = int(vtx.shape[0]), int(vtx.shape[1])
+    out = torch.empty((n, k0 + n_attr), dtype=torch.int32, device=vtx.device)
+    rc = _gpu_lib().synth_attributes(ctypes.c_void_p(vtx.data_ptr()), n, k0, ctypes.c_void_p(out.data_ptr()),
+                                     k0 + n_attr, seed, _stream_ptr(torch, stream))
+    if rc:
+        raise RuntimeError(f"synth_attributes: CUDA error {rc}")
+    return out
 
 
 def tet_soup_gpu(L: int, unused_frac: float = 0.03, seed: int = 3, device="cuda", permute: bool = True, stream=None):

@@ -8,13 +8,15 @@
 // C ABI (device pointers, asynchronous on `stream`; returns 0, or a cudaError_t value):
 //   synth_heightfield(vtx float32[N][3], idx int32[6*G*Gy], G, Gy, n_extra, seed, permute, stream)
 //   synth_tets(vtx float32[N][4], idx int32[20*L^3], L, n_extra, seed, permute, stream)
-// with N = soup vertices + n_extra.
+// with N = soup vertices + n_extra, and
+//   synth_attributes(in uint32[n][k_in], n, k_in, out uint32[n][k_out], k_out, seed, stream)
+// which copies each vertex and appends k_out - k_in attribute words (synth.with_attributes).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace {
 
-constexpr uint64_t kTagNoise = 1, kTagExtra = 2, kTagPerm = 3, kTagJitter = 4, kTagField = 5;
+constexpr uint64_t kTagNoise = 1, kTagExtra = 2, kTagPerm = 3, kTagJitter = 4, kTagField = 5, kTagAttr = 7;
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   uint64_t z = x + 0x9E3779B97F4A7C15ull;
@@ -168,6 +170,23 @@ __global__ void k_tets(float4* vtx, int32_t* idx, int64_t L, int64_t n_extra, ui
   }
 }
 
+// Attribute q of vertex i: hash of (seed, kTagAttr, q, its key words); q < 3 maps to [-1, 1).
+__global__ void k_attributes(const uint32_t* in, int64_t n, int k_in, uint32_t* out, int k_out, uint64_t seed) {
+  const uint64_t base = hash_base(seed, kTagAttr);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t* v = in + i * k_in;
+    uint32_t* o = out + i * k_out;
+    for (int c = 0; c < k_in; ++c) o[c] = v[c];
+    for (int q = 0; q < k_out - k_in; ++q) {
+      uint64_t h = hmix(base, q);
+      for (int c = 0; c < k_in; ++c) h = hmix(h, (int64_t)v[c]);
+      float u = unit_float(h);
+      if (q < 3) u = __fsub_rn(__fmul_rn(u, 2.0f), 1.0f);
+      o[k_in + q] = __float_as_uint(u);
+    }
+  }
+}
+
 int grid_for(int64_t n) {
   int64_t g = (n + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
@@ -189,5 +208,14 @@ extern "C" int synth_tets(void* vtx, int32_t* idx, int64_t L, int64_t n_extra, u
   const int64_t N = 20 * L * L * L + n_extra;
   if (N == 0) return 0;
   k_tets<<<grid_for(N), 256, 0, stream>>>(static_cast<float4*>(vtx), idx, L, n_extra, seed, permute);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int synth_attributes(const void* in, int64_t n, int k_in, void* out, int k_out, uint64_t seed,
+                                cudaStream_t stream) {
+  if (n == 0) return 0;
+  if (k_in < 1 || k_out < k_in) return (int)cudaErrorInvalidValue;
+  k_attributes<<<grid_for(n), 256, 0, stream>>>(static_cast<const uint32_t*>(in), n, k_in, static_cast<uint32_t*>(out),
+                                                k_out, seed);
   return (int)cudaGetLastError();
 }

@@ -49,7 +49,12 @@ def test_workspace_size_model(L):
     b = rx.reindex_workspace_size(n, S, ne, k)
     U = min(n, ne * k)
     assert 2 * U * (S + 4) + U + 4 * n <= b <= 2 * U * (S + 4) + U + 4 * n + 64 * 2**20
-    assert rx.reindex_workspace_size(n, 5, ne, k) == 0  # unsupported stride
+    for S in (24, 32):  # wide vertices: the same model
+        b = rx.reindex_workspace_size(n, S, ne, k)
+        assert 2 * U * (S + 4) + U + 4 * n <= b <= 2 * U * (S + 4) + U + 4 * n + 64 * 2**20
+    for S in (5, 28, 36, 64):  # unsupported strides
+        assert rx.reindex_workspace_size(n, S, ne, k) == 0
+    assert rx.reindex_meshes_workspace_size(2, n, 24, ne, k) == 0  # batched: up to 16 bytes
     assert rx.reindex_workspace_size(-1, 12, ne, k) == 0
     assert rx.reindex_workspace_size(10, 12, 0, 3) > 0
 
@@ -68,9 +73,11 @@ def test_host_side_argument_checks(L):
     # null output count, null idx
     assert L.reindex_mesh(fake, 10, 12, fake, 3, 3, fake, z, fake, z) == rx.REINDEX_ERR_INVALID_ARG
     assert L.reindex_mesh(fake, 10, 12, z, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_INVALID_ARG
-    # misaligned 16-byte vertices
-    assert L.reindex_mesh(ctypes.c_void_p((1 << 20) + 4), 10, 16, fake, 3, 3, fake, fake, fake, z) \
-        == rx.REINDEX_ERR_INVALID_ARG
+    # misaligned 16-, 24- and 32-byte vertices (16-, 8- and 16-byte alignment)
+    for S, off in ((16, 4), (24, 4), (32, 8)):
+        assert L.reindex_mesh(ctypes.c_void_p((1 << 20) + off), 10, S, fake, 3, 3, fake, fake, fake, z) \
+            == rx.REINDEX_ERR_INVALID_ARG
+    assert L.reindex_mesh(fake, 10, 28, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
     # no vertices but some indices: every index is out of range
     assert L.reindex_mesh(z, 0, 12, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_INDEX_RANGE
     # workspace too small

@@ -74,7 +74,7 @@ SIZES = [(1, 3), (2, 4), (33, 30), (2047, 2047), (2049, 6000), (4096, 4096), (40
          (70001, 70001), (150_000, 40_000)]
 
 
-@pytest.mark.parametrize("S", [4, 8, 12, 16, 20])
+@pytest.mark.parametrize("S", [4, 8, 12, 16, 20, 24, 32])
 @pytest.mark.parametrize("mode", ["random", "dups", "floats", "const"])
 def test_random_meshes(rx, S, mode):
     rng = np.random.default_rng(1000 + S * 10 + ["random", "dups", "floats", "const"].index(mode))
@@ -308,6 +308,52 @@ def test_sort_variants_bit_exact(rx, spec, S):
         rx.reindex_tuning_set(S, saved)
 
 
+WIDE_VARIANTS = ["pack=off,swaves=tile", "pack=on,swaves=tile", "pack=auto,swaves=1", "pack=on,swaves=4"]
+
+
+@pytest.mark.parametrize("spec", WIDE_VARIANTS)
+@pytest.mark.parametrize("S", [24, 32])
+def test_wide_vertices_bit_exact(rx, spec, S):
+    """24- and 32-byte vertices (always the "tiles" sort): random words, many duplicates, constant
+    low bytes, and a heightfield whose vertices carry normal and texture-coordinate words."""
+    saved = rx.reindex_tuning_get(S)
+    rx.reindex_tuning_set(S, spec)
+    try:
+        rng = np.random.default_rng(9100 + S + 10 * WIDE_VARIANTS.index(spec))
+        for mode in ["random", "dups", "const", "hibyte"]:
+            for n, m in SIZES:
+                assert_parity(rx, *random_mesh(rng, n, m, S // 4, mode))
+        mesh = synth.heightfield_soup_attrs(300, 170, 0.05, seed=12, stride=S)
+        assert assert_parity(rx, mesh.vtx, mesh.idx.reshape(-1), 3) == mesh.expected_unique
+    finally:
+        rx.reindex_tuning_set(S, saved)
+
+
+@pytest.mark.parametrize("S", [24, 32])
+def test_wide_vertices_large_heightfield(rx, S):
+    """A 1448^2-cell heightfield with attribute words (12.6 M soup vertices): D = 1449^2, and the
+    unique vertices and indices equal the oracle's on a sample of the output."""
+    vtx, idx = synth.heightfield_soup_gpu(1448, 1448, 0.05, seed=2)
+    wide = synth.with_attributes_gpu(vtx.view(torch.int32), (S - 12) // 4, seed=2)
+    out_v, out_n, out_i = rx.reindex_mesh(wide, idx)
+    torch.cuda.synchronize()
+    D = int(out_n.item())
+    assert D == 1449 * 1449
+    uv = out_v[:D].cpu().numpy().view(np.uint32)
+    # strictly ascending (raw-bit lexicographic order), hence duplicate-free
+    a, b = uv[:-1].astype(np.uint64), uv[1:].astype(np.uint64)
+    diff = a != b
+    first = np.argmax(diff, axis=1)
+    rows = np.arange(a.shape[0])
+    assert diff.any(axis=1).all() and (a[rows, first] < b[rows, first]).all()
+    # every index points at its vertex's value (sampled) and every unique vertex is referenced
+    rng = np.random.default_rng(S)
+    j = rng.integers(0, idx.numel(), size=200_000)
+    src = wide.cpu().numpy().view(np.uint32)[idx.reshape(-1).cpu().numpy()[j]]
+    np.testing.assert_array_equal(uv[out_i.reshape(-1).cpu().numpy()[j]], src)
+    assert torch.unique(out_i).numel() == D
+
+
 def test_lookback_wait_runs_out_and_reports_timeout(rx):
     """A compaction tile that never publishes its status (test hook): the waits after it give up
     after their iteration limit, the call reports REINDEX_ERR_TIMEOUT, and the next call works."""
@@ -328,3 +374,12 @@ def test_lookback_wait_runs_out_and_reports_timeout(rx):
     assert int(out_n.item()) == -rx.REINDEX_ERR_TIMEOUT
     assert elapsed < 60
     assert assert_parity(rx, m.vtx, m.idx.reshape(-1), 3) == 65 * 65
+
+
+def test_attribute_generator_device_matches_host(rx):
+    """The device attribute generator writes the same bits as the host one (inputs only)."""
+    m = synth.heightfield_soup(50, 40, 0.1, seed=23)
+    for n_attr in (3, 5):
+        host = synth.with_attributes(m.vtx, n_attr, 23)
+        dev = synth.with_attributes_gpu(torch.from_numpy(m.vtx.view(np.int32)).cuda(), n_attr, 23)
+        np.testing.assert_array_equal(dev.cpu().numpy().view(np.uint32), host)

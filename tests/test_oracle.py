@@ -123,7 +123,7 @@ ALPHABET = [0x00000000, 0x80000000, 0x7FC00000, 0x7FC00001, 0xFFC00000, 0x3F8000
             0x00000001, 0x7F800000, 0xFFFFFFFF, 0x40000000]  # +0, -0, NaNs, 1, -1, denormal, inf, ...
 
 
-@pytest.mark.parametrize("K", [1, 2, 3, 4])
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 5, 6, 8])
 @pytest.mark.parametrize("trial", range(12))
 def test_brute_force_tiny(oracle_lib, K, trial):
     rng = random.Random(1000 * K + trial)
@@ -141,6 +141,24 @@ def test_brute_force_tiny(oracle_lib, K, trial):
     r = oracle.paper_steps(vtx, idx)
     np.testing.assert_array_equal(r["newVtx"], bv)
     np.testing.assert_array_equal(r["idxNew"], bi)
+
+
+@pytest.mark.parametrize("stride", [24, 32])
+def test_wide_vertices_extend_the_narrow_result(oracle_lib, stride):
+    """Attribute words that are a function of the position words change neither the order nor the
+    equality of the vertices: the wide result is the 12-byte result with its attributes appended
+    (and D keeps its closed form (G+1)(Gy+1))."""
+    m = synth.heightfield_soup(37, 23, 0.1, seed=19)
+    w = synth.heightfield_soup_attrs(37, 23, 0.1, seed=19, stride=stride)
+    ov, oi = oracle.reindex_sort(m.vtx, m.idx)
+    wv, wi = oracle.reindex_sort(w.vtx, w.idx)
+    assert wv.shape == (38 * 24, stride // 4)
+    np.testing.assert_array_equal(wv[:, :3], ov)
+    np.testing.assert_array_equal(wv, synth.with_attributes(ov, stride // 4 - 3, 19))
+    np.testing.assert_array_equal(wi, oi)
+    mv, mi = oracle.reindex_map(w.vtx, w.idx, canonical=True)
+    np.testing.assert_array_equal(mv, wv)
+    np.testing.assert_array_equal(mi, wi)
 
 
 # --------------------------------------------------------------------------- order and equality
