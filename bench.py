@@ -106,14 +106,17 @@ SORT_KERNEL_SOURCES = {
 }
 
 
-def ncu_traffic(kernel, workload):
+def ncu_traffic(kernel, workload, item_bytes=None):
     """Per-launch DRAM bytes of a radix-pass kernel from the committed ncu summary
-    (profiles/<kernel>_traffic.json), if it was taken on the current kernel source (else None)."""
+    (profiles/<kernel>_traffic.json), if it was taken on the current kernel source with items of
+    the same size (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         if rec.get("source_digest") != source_digest(SORT_KERNEL_SOURCES[kernel]):
+            return None
+        if item_bytes is not None and rec.get("item_bytes") not in (None, item_bytes):
             return None
         return rec.get("per_launch_bytes_full", {}).get(workload)
     except Exception:
@@ -537,6 +540,21 @@ def build_mesh(workload):
     return synth.config_mesh(cfg), None
 
 
+def sort_pass_roofline(recs, U):
+    """The radix scatter's roofline from the per-launch records: (kernel, algorithmic bytes per
+    launch, average launch ms, item bytes, launches).  One pass reads and writes every (key, old
+    index) item once: 2 * U * item bytes, averaged over the passes that moved data (a call that
+    sorts by key prefix first has 12-byte items in those passes)."""
+    kname = "tile_scatter" if any(r["name"] == "tile_scatter" for r in recs) else "onesweep"
+    sw = [r for r in recs if r["name"] == kname and not r["skipped"]]
+    if not sw:
+        return kname, float("nan"), float("nan"), None, 0
+    total_bytes = sum(2 * U * r["item_bytes"] for r in sw)
+    avg_ms = sum(r["ms"] for r in sw) / len(sw)
+    sizes = sorted({r["item_bytes"] for r in sw})
+    return kname, total_bytes / len(sw), avg_ms, sizes[0] if len(sizes) == 1 else sizes, len(sw)
+
+
 def step_model_bytes(N, S, M, U, D):
     """Bytes a re-indexing step must move under a fixed model: 8-bit digits, all S radix passes
     (no credit for skipped ones), items of W = S + 4 bytes.  Used-flag scatter 4M + N/8; compaction
@@ -663,16 +681,12 @@ def run_usecase(args, world, rank, local):
         a = per_kernel.setdefault(key, [0, 0.0])
         a[0] += 1
         a[1] += r["ms"]
-    kname = "tile_scatter" if any(r["name"] == "tile_scatter" for r in recs) else "onesweep"
-    sweeps = [r["ms"] for r in recs if r["name"] == kname and not r["skipped"]]
-    W = S + 4
+    kname, alg_bytes, avg_ms, item_bytes, n_sweeps = sort_pass_roofline(recs, U)
     peak, peak_kind = load_peaks()
-    avg_ms = sum(sweeps) / len(sweeps) if sweeps else float("nan")
-    alg_bytes = 2 * U * W
     roofline = {"kernel": kname, "bound": "hbm", "achieved": alg_bytes / (avg_ms / 1e3) / 1e9, "peak": peak,
                 "unit": "GB/s", "frac": alg_bytes / (avg_ms / 1e3) / 1e9 / peak,
                 "peak_kind": f"{peak_kind} hbm_gbs (copy)", "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
-                "avg_launch_ms": avg_ms, "passes_per_step": len(sweeps) / args.steps}
+                "item_bytes": item_bytes, "avg_launch_ms": avg_ms, "passes_per_step": n_sweeps / args.steps}
     if rank != 0:
         return
     cpu = None
@@ -763,22 +777,18 @@ def run_ours(args, world, rank, local):
         a = per_kernel.setdefault(key, [0, 0.0])
         a[0] += 1
         a[1] += r["ms"]
-    kname = "tile_scatter" if any(r["name"] == "tile_scatter" for r in recs) else "onesweep"
-    sweeps = [r["ms"] for r in recs if r["name"] == kname and not r["skipped"]]
-    W = S + 4
-    alg_bytes = 2 * U * W  # one pass reads and writes every (key, index) item once
+    kname, alg_bytes, avg_ms, item_bytes, n_sweeps = sort_pass_roofline(recs, U)
     peak, peak_kind = load_peaks()
-    avg_ms = sum(sweeps) / len(sweeps) if sweeps else float("nan")
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
     per_pass = {}
     for r in recs:
         if r["name"] == kname and not r["skipped"]:
-            per_pass.setdefault(r["digit"], []).append(r["ms"])
+            per_pass.setdefault(f'{r["digit"]}/{r["item_bytes"]}B', []).append(r["ms"])
     roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "per_pass_ms": {d: round(sum(v) / len(v), 4) for d, v in sorted(per_pass.items())},
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                "traffic": ncu_traffic(kname, args.workload), "algorithmic_bytes_per_launch": alg_bytes,
-                "avg_launch_ms": avg_ms, "passes_per_step": len(sweeps) / args.steps}
+                "traffic": ncu_traffic(kname, args.workload, item_bytes), "algorithmic_bytes_per_launch": alg_bytes,
+                "item_bytes": item_bytes, "avg_launch_ms": avg_ms, "passes_per_step": n_sweeps / args.steps}
 
     # the whole step against the fixed byte model (8-bit digits, all S passes, W-byte items)
     model = step_model_bytes(n_vtx, S, M, U, D)

@@ -31,6 +31,10 @@
  *      newIdx);
  *   7. gather of the unique vertices (Section 2.3, newVtx);
  *   8. remap of every index: out_idx[j] = oldToNew[idx[j]] (Section 2.4).
+ * For vertices of 16 bytes and more, steps 3-7 first run on the 64 most significant varying bits
+ * of each key (an order-preserving prefix); a check that every used vertex equals the unique
+ * vertex it was given proves that result exact, and only where it fails do steps 3-7 run again
+ * on the whole keys.  Either way the result is the one defined above.
  *
  * Conventions shared by all entry points:
  *   - Pointers named vtx/idx/out_* are DEVICE pointers owned by the caller unless the entry
@@ -304,6 +308,7 @@ typedef struct {
   int digit;       /* radix digit position of a sort pass (0 = least significant byte), else -1 */
   int skipped;     /* 1 if a sort pass found its digit constant and moved no data */
   float ms;        /* event-measured duration */
+  int item_bytes;  /* sort passes: bytes per item moved (key + old index), else 0 */
 } reindex_profile_record;
 
 typedef enum {
@@ -321,7 +326,9 @@ typedef enum {
   REINDEX_K_TILE_OFFSETS = 11, /* step 3, "tiles" variant: tile offsets per digit */
   REINDEX_K_TILE_SCATTER = 12, /* step 3, "tiles" variant: the pass's data movement */
   REINDEX_K_KEY_MASKS = 13,    /* "tiles" variant: which key bits vary over the used vertices */
-  REINDEX_K_COUNT = 14
+  REINDEX_K_PREFIX_GATE = 14,  /* prefix sort: skip the full-key sort unless two keys shared a prefix */
+  REINDEX_K_PREFIX_CHECK = 15, /* prefix sort: every used vertex equals the unique vertex it was given */
+  REINDEX_K_COUNT = 16
 } reindex_kernel_id;
 
 void reindex_profile_enable(int on);

@@ -31,7 +31,8 @@ REINDEX_ERR_CUDA = 6
 REINDEX_ERR_INTERNAL = 7
 
 KERNEL_NAMES = ["clear", "used_flags", "compact_hist", "sort_plan", "onesweep", "head_scan", "remap", "finalize",
-                "seg_prepare", "seg_offsets", "tile_count", "tile_offsets", "tile_scatter", "key_masks"]
+                "seg_prepare", "seg_offsets", "tile_count", "tile_offsets", "tile_scatter", "key_masks", "prefix_gate",
+                "prefix_check"]
 
 # Symbols declared in include/reindex.h (checked by the ABI test).
 EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "reindex_mesh_ws",
@@ -76,7 +77,8 @@ class _ServerStats(ctypes.Structure):
 
 
 class _ProfileRecord(ctypes.Structure):
-    _fields_ = [("kernel", ctypes.c_int), ("digit", ctypes.c_int), ("skipped", ctypes.c_int), ("ms", ctypes.c_float)]
+    _fields_ = [("kernel", ctypes.c_int), ("digit", ctypes.c_int), ("skipped", ctypes.c_int), ("ms", ctypes.c_float),
+                ("item_bytes", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:
@@ -394,7 +396,8 @@ def profile_collect(max_records: int = 1 << 16):
     n = lib().reindex_profile_collect(buf, max_records)
     if n < 0:
         raise ReindexError(REINDEX_ERR_CUDA, "reindex_profile_collect")
-    return [dict(kernel=r.kernel, name=KERNEL_NAMES[r.kernel], digit=r.digit, skipped=bool(r.skipped), ms=r.ms)
+    return [dict(kernel=r.kernel, name=KERNEL_NAMES[r.kernel], digit=r.digit, skipped=bool(r.skipped), ms=r.ms,
+                 item_bytes=r.item_bytes)
             for r in buf[: min(n, max_records)]]
 
 

@@ -43,6 +43,9 @@ void apply_tuning(LaunchCfg& c, const char* spec) {
   if (std::strstr(spec, "pack=on")) c.pack_keys = 1;
   if (std::strstr(spec, "pack=off")) c.pack_keys = 0;
   if (std::strstr(spec, "pack=auto")) c.pack_keys = -1;
+  if (std::strstr(spec, "prefix=on")) c.prefix = 1;
+  if (std::strstr(spec, "prefix=off")) c.prefix = 0;
+  if (std::strstr(spec, "prefix=auto")) c.prefix = -1;
 }
 
 std::string describe_tuning(const LaunchCfg& c) {
@@ -53,6 +56,7 @@ std::string describe_tuning(const LaunchCfg& c) {
   d += c.grid_per_tile ? ",grid=tile" : ",grid=persist";
   d += c.scatter_waves ? ",swaves=" + std::to_string(c.scatter_waves) : std::string(",swaves=tile");
   d += c.pack_keys < 0 ? ",pack=auto" : (c.pack_keys ? ",pack=on" : ",pack=off");
+  d += c.prefix < 0 ? ",prefix=auto" : (c.prefix ? ",prefix=on" : ",prefix=off");
   return d;
 }
 
@@ -95,6 +99,7 @@ void set_launch_cfg(int S, const LaunchCfg& c) {
 namespace prof {
 struct Pending {
   int kernel, digit;
+  int item_bytes;       // bytes per sort item (key + old index) of a sort pass, else 0
   cudaEvent_t a, b;
   const uint8_t* skip;  // pinned host copy of the plan's skip flags (sort passes only)
 };
@@ -107,7 +112,8 @@ struct Scope {
   bool on;
   Pending p;
   cudaStream_t st;
-  Scope(int kernel, int digit, cudaStream_t s, const uint8_t* skip = nullptr) : on(false), st(s) {
+  Scope(int kernel, int digit, cudaStream_t s, const uint8_t* skip = nullptr, int item_bytes = 0)
+      : on(false), st(s) {
     {
       std::lock_guard<std::mutex> g(mu);
       on = enabled;
@@ -115,6 +121,7 @@ struct Scope {
     if (!on) return;
     p.kernel = kernel;
     p.digit = digit;
+    p.item_bytes = item_bytes;
     p.skip = skip;
     cudaEventCreate(&p.a);
     cudaEventCreate(&p.b);
@@ -196,19 +203,19 @@ static cudaError_t sort_pass(int S, int d, const WsPtrs& p, const LaunchCfg& c, 
                              const uint8_t* skip) {
   if (c.sort_kernel == kSortTiles) {
     {
-      prof::Scope s(REINDEX_K_TILE_COUNT, d, st, skip);
+      prof::Scope s(REINDEX_K_TILE_COUNT, d, st, skip, S + 4);
       cudaError_t e = launch_tile_count(S, d, p, c, st);
       if (e != cudaSuccess) return e;
     }
     {
-      prof::Scope s(REINDEX_K_TILE_OFFSETS, d, st, skip);
+      prof::Scope s(REINDEX_K_TILE_OFFSETS, d, st, skip, S + 4);
       cudaError_t e = launch_tile_offsets(d, p, st);
       if (e != cudaSuccess) return e;
     }
-    prof::Scope s(REINDEX_K_TILE_SCATTER, d, st, skip);
+    prof::Scope s(REINDEX_K_TILE_SCATTER, d, st, skip, S + 4);
     return launch_tile_scatter(S, d, p, c, st);
   }
-  prof::Scope s(REINDEX_K_ONESWEEP, d, st, skip);
+  prof::Scope s(REINDEX_K_ONESWEEP, d, st, skip, S + 4);
   return c.sort_kernel == kSortPipe ? launch_onesweep_pipe(S, d, p, c, st) : launch_onesweep(S, d, p, c, st);
 }
 
@@ -216,21 +223,64 @@ static cudaError_t sort_pass(int S, int d, const WsPtrs& p, const LaunchCfg& c, 
 static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t M,
                                    void* out_vtx, int64_t* out_nVtx, int32_t* out_idx, void* ws,
                                    const WsLayout& L, cudaStream_t st, const PipeExtras* extra = nullptr) {
-  const LaunchCfg c = resolve_cfg(launch_cfg(S), S, L.Umax);  // one configuration for the whole call
+  LaunchCfg c = resolve_cfg(launch_cfg(S), S, L.Umax);  // one configuration for the whole call
   const WsPtrs p = ws_ptrs(ws, L);
+  // Prefix sort first: items keep the 64 most significant varying key bits; the full-key sort
+  // below then runs only if two different keys shared a prefix (else every kernel of it returns
+  // at once).  Both write the same outputs; the remap and the finalize come once, at the end.
+  const bool prefix = c.prefix && S > kPrefixBytes;
+  if (prefix) c.scatter_waves = 1;  // the full-key sort's passes: few CTAs, cheap when skipped
+  const WsPtrs pp = prefix ? ws_ptrs_prefix(ws, L) : p;
   {
     prof::Scope s(REINDEX_K_CLEAR, -1, st);
-    REINDEX_TRY(launch_clear(ws, L.zero_bytes, c, st));
+    REINDEX_TRY(launch_clear(ws, L.zero_bytes + (prefix ? 256 : 0), c, st));  // + the prefix control block
   }
   if (extra && extra->pre) {
     prof::Scope s(extra->flags_done ? REINDEX_K_USED_FLAGS : REINDEX_K_SEG_PREPARE, -1, st);
-    REINDEX_TRY(extra->pre(p, c));
+    REINDEX_TRY(extra->pre(pp, c));
   }
   if (!(extra && extra->flags_done)) {
     prof::Scope s(REINDEX_K_USED_FLAGS, -1, st);
-    REINDEX_TRY(launch_used_flags(idx, M, nVtx, p, c, st));
+    REINDEX_TRY(launch_used_flags(idx, M, nVtx, pp, c, st));
   }
   if (extra && extra->vtx_ready) REINDEX_TRY(cudaStreamWaitEvent(st, extra->vtx_ready, 0));
+  if (prefix) {
+    LaunchCfg cp = c;  // the passes sort 12-byte keys (8 varying bytes) with the tiles sort
+    cp.sort_kernel = kSortTiles;
+    cp.occ_tiles = launch_cfg(kPrefixItem).occ_tiles;
+    {
+      prof::Scope s(REINDEX_K_KEY_MASKS, -1, st);
+      REINDEX_TRY(launch_key_masks(S, vtx, nVtx, pp, c, nullptr, st));
+    }
+    {
+      prof::Scope s(REINDEX_K_SORT_PLAN, -1, st);
+      REINDEX_TRY(launch_prefix_plan(S, pp, st));
+    }
+    {
+      prof::Scope s(REINDEX_K_COMPACT, -1, st);
+      REINDEX_TRY(launch_compact_prefix(S, vtx, nVtx, pp, L.tilesV, c, st));
+    }
+    const uint8_t* pskip = prof::skip_buffer(pp.plan, st);
+    for (int d = 0; d < kPrefixBytes; ++d) REINDEX_TRY(sort_pass(kPrefixItem, d, pp, cp, st, pskip));
+    {
+      prof::Scope s(REINDEX_K_HEAD_SCAN, -1, st);
+      REINDEX_TRY(launch_head_scan_prefix(S, pp, vtx, out_vtx, out_nVtx, (uint32_t)nVtx, c, st));
+    }
+    {
+      prof::Scope s(REINDEX_K_PREFIX_CHECK, -1, st);
+      REINDEX_TRY(launch_prefix_check(S, vtx, nVtx, out_vtx, pp, c, st));
+    }
+    {
+      prof::Scope s(REINDEX_K_CLEAR, -1, st);
+      REINDEX_TRY(launch_clear(ws, L.zero_bytes, c, st));  // the full-key sort's tables
+    }
+    {
+      prof::Scope s(REINDEX_K_PREFIX_GATE, -1, st);
+      REINDEX_TRY(launch_prefix_gate(pp, p, st));
+    }
+    prof::Scope s(REINDEX_K_USED_FLAGS, -1, st);
+    REINDEX_TRY(launch_used_flags(idx, M, nVtx, p, c, st));
+  }
   if (c.sort_kernel == kSortTiles && c.pack_keys) {  // bit masks -> plan (key packing) -> compaction
     {
       prof::Scope s(REINDEX_K_KEY_MASKS, -1, st);
@@ -680,6 +730,7 @@ int reindex_profile_collect(reindex_profile_record* out, int maxRecords) {
       out[i].kernel = p.kernel;
       out[i].digit = p.digit;
       out[i].skipped = (p.skip && p.digit >= 0) ? (int)p.skip[p.digit] : 0;
+      out[i].item_bytes = p.item_bytes;
       out[i].ms = ms;
     }
     cudaEventDestroy(p.a);
@@ -695,7 +746,7 @@ const char* reindex_kernel_name(int kernel) {
   static const char* names[REINDEX_K_COUNT] = {"clear",     "used_flags", "compact_hist", "sort_plan",
                                                "onesweep",  "head_scan",  "remap",        "finalize",
                                                "seg_prepare", "seg_offsets", "tile_count", "tile_offsets",
-                                               "tile_scatter", "key_masks"};
+                                               "tile_scatter", "key_masks", "prefix_gate", "prefix_check"};
   return (kernel >= 0 && kernel < REINDEX_K_COUNT) ? names[kernel] : "unknown";
 }
 

@@ -24,6 +24,8 @@ constexpr int kHeadTile = kHeadThreads * kHeadIpt;         // 2048 items per til
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;    // 256 digit values
 constexpr int kMaxDigits = 32;             // 32-byte keys -> 32 byte digits
+constexpr int kPrefixBytes = 8;           // prefix sort: keys cut to their 64 most significant varying bits,
+constexpr int kPrefixItem = 12;           // held in 12-byte item keys (word 0 zero: 16-byte records)
 constexpr int kWideMin = 24;               // keys of 24 and 32 bytes (single meshes) use the "tiles"
                                            // sort with vary ranking only (fewer kernel variants)
 
@@ -43,6 +45,7 @@ constexpr int kHistMatchAny = 2;  // histogram: one atomic per distinct digit (m
 constexpr int kHistNone = 3;      // no histograms: packed keys and the first pass's digit plane instead
 constexpr int kHistMasks = 4;     // no histograms: key bit masks and the plane of key byte 0 instead
                                   // (the "tiles" sort counts digits per pass itself)
+constexpr int kHistPrefix = 5;    // prefix sort: items carry the 64 most significant varying key bits
 
 // Look-back status word: 2-bit flag + 30-bit count.
 constexpr uint32_t kFlagAgg = 1u << 30;    // tile aggregate only
@@ -63,6 +66,9 @@ constexpr int kLbPad = 32;
 constexpr uint32_t kErrIndexRange = 4;
 constexpr uint32_t kErrTimeout = 5;
 constexpr uint32_t kErrInternal = 7;
+// Not an error: set in the control block of a call's full-key sort when its prefix sort already
+// produced the result (every kernel of the full-key sort then returns at once).
+constexpr uint32_t kErrSkip = 0x100;
 
 // ---------------------------------------------------------------------------------------------
 // Workspace.
@@ -73,7 +79,8 @@ struct Control {             // zeroed at the start of every call
                                  // [1 + kMaxDigits] head scan
   uint32_t kor[kMaxDigits / 4];   // OR of key word q over the used vertices (compaction, kHistNone)
   uint32_t knand[kMaxDigits / 4]; // OR of the complement: bit b varies iff set in both masks
-  uint32_t pad[12];
+  uint32_t amb;                   // prefix sort: two different keys share a prefix (1)
+  uint32_t pad[11];
 };
 static_assert(sizeof(Control) == 256, "Control block is one 256-byte line");
 
@@ -131,6 +138,7 @@ struct WsLayout {
          off_bitmask = 0, zero_bytes = 0;
   size_t off_plan = 0, off_itemsA = 0, off_itemsB = 0, items_bytes = 0, idoff = 0, off_old2new = 0, off_digits = 0,
          total = 0;
+  size_t off_ctrl_pre = 0;  // prefix sort: its control block
 
   void compute(int64_t n, int s, int64_t m) {
     S = s; K = s / 4; P = s; nVtx = n; M = m;
@@ -146,12 +154,17 @@ struct WsLayout {
     off_lb_sort = o;     o = align_up(o + (size_t)2 * tilesS * kRadix * 4, 256);
     off_bitmask = o;     o = align_up(o + (size_t)((n + 31) / 32) * 4, 256);
     zero_bytes = o;
+    off_ctrl_pre = o;    o += 256;  // control block of the prefix sort (outside the full sort's zeroing)
     off_plan = o;        o = align_up(o + sizeof(Plan), 256);
     // SoA layouts keep the id plane 256-byte aligned; 256 spare bytes let bulk copies of a
     // ragged last tile round their size up to 16 bytes without leaving the buffer.
     idoff = soa_items(S) ? align_up((size_t)Umax * S, 256) : 0;
     items_bytes = soa_items(S) ? idoff + align_up((size_t)Umax * 4, 256) + 256
                                : align_up((size_t)Umax * (size_t)(S + 4), 256) + 256;
+    if (S > kPrefixBytes) {  // the prefix sort's items (16-byte records) share the item buffers
+      const size_t pre = align_up((size_t)Umax * (kPrefixItem + 4), 256) + 256;
+      if (pre > items_bytes) items_bytes = pre;
+    }
     off_itemsA = o;      o += items_bytes;
     off_itemsB = o;      o += items_bytes;
     off_old2new = o;     o = align_up(o + (size_t)n * 4, 256);
@@ -196,6 +209,16 @@ inline WsPtrs ws_ptrs(void* ws, const WsLayout& L) {
   p.tilesS = L.tilesS;
   p.Umax = L.Umax;
   p.idoff = (int64_t)L.idoff;
+  return p;
+}
+
+// The prefix sort's view: its own control block, 16-byte {0, prefix, old index} records in the
+// same item buffers; the other tables are shared with the full-key sort, which runs (or is
+// skipped) after it.
+inline WsPtrs ws_ptrs_prefix(void* ws, const WsLayout& L) {
+  WsPtrs p = ws_ptrs(ws, L);
+  p.ctrl = reinterpret_cast<Control*>(static_cast<unsigned char*>(ws) + L.off_ctrl_pre);
+  p.idoff = 0;  // array of structures
   return p;
 }
 
@@ -401,6 +424,30 @@ __device__ __forceinline__ void load_key(const void* vtx, int64_t i, uint32_t (&
     const uint32_t* p = reinterpret_cast<const uint32_t*>(vtx) + i * (S / 4);
 #pragma unroll
     for (int q = 0; q < S / 4; ++q) k[q] = __ldcs(p + q);
+  }
+}
+
+// Vertex key load through the read-only cache, for random accesses (natural alignment).
+template <int S>
+__device__ __forceinline__ void load_key_ro(const void* vtx, uint32_t i, uint32_t (&k)[S / 4]) {
+  if constexpr (S == 16 || S == 32) {
+    const uint4* p = reinterpret_cast<const uint4*>(vtx) + (size_t)i * (S / 16);
+#pragma unroll
+    for (int h = 0; h < S / 16; ++h) {
+      const uint4 v = __ldg(p + h);
+      k[4 * h] = v.x; k[4 * h + 1] = v.y; k[4 * h + 2] = v.z; k[4 * h + 3] = v.w;
+    }
+  } else if constexpr (S == 8 || S == 24) {
+    const uint2* p = reinterpret_cast<const uint2*>(vtx) + (size_t)i * (S / 8);
+#pragma unroll
+    for (int h = 0; h < S / 8; ++h) {
+      const uint2 v = __ldg(p + h);
+      k[2 * h] = v.x; k[2 * h + 1] = v.y;
+    }
+  } else {
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(vtx) + (size_t)i * (S / 4);
+#pragma unroll
+    for (int q = 0; q < S / 4; ++q) k[q] = __ldg(p + q);
   }
 }
 

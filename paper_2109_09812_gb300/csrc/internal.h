@@ -25,6 +25,9 @@ struct LaunchCfg {
   int scatter_waves = 0;        // "tiles" scatter: 0 one CTA per tile, else CTAs = waves x SMs x occupancy
   int pack_keys = -1;           // "tiles" sort: pack the varying key bits when that saves a pass
                                 // (1 on, 0 off, -1 auto: keys of up to 8 bytes and batched calls)
+  int prefix = -1;              // single meshes of 12- to 32-byte vertices: sort by the 64 most
+                                // significant varying key bits first (1 on, 0 off, -1 auto: 16 bytes
+                                // and wider)
 };
 
 // The configuration for one call: kSortAuto resolved for S-byte keys and up to Umax items.
@@ -37,6 +40,10 @@ inline LaunchCfg resolve_cfg(LaunchCfg c, int S, int64_t Umax, bool batched = fa
   }
   if (c.sort_kernel == kSortAuto) c.sort_kernel = Umax >= kTilesMinItems ? kSortTiles : kSortRegs;
   if (c.pack_keys < 0) c.pack_keys = (batched || S <= 8) ? 1 : 0;
+  if (batched || S <= kPrefixBytes)
+    c.prefix = 0;
+  else if (c.prefix < 0)  // 12-byte keys: the two passes saved do not pay for the check (GB300)
+    c.prefix = S >= 16 ? 1 : 0;
   return c;
 }
 
@@ -74,6 +81,17 @@ cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int6
                            const SegArgs* seg, cudaStream_t st);
 // from_masks: trivial passes from the key bit masks (the "tiles" sort takes no upfront histograms).
 cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, bool allow_pack, cudaStream_t st);
+// Prefix sort (single meshes, S > 8): the plan keeping the 64 most significant varying key bits,
+// the compaction into (prefix, old index) items, the head scan that checks whole keys, and the
+// gate that skips the full-key sort unless two different keys shared a prefix.
+cudaError_t launch_prefix_plan(int S, WsPtrs ws, cudaStream_t st);
+cudaError_t launch_compact_prefix(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
+                                  cudaStream_t st);
+cudaError_t launch_head_scan_prefix(int S, WsPtrs ws, const void* vtx, void* out_vtx, int64_t* out_nVtx,
+                                    uint32_t nVtx, const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_prefix_check(int S, const void* vtx, int64_t nVtx, const void* out_vtx, WsPtrs ws,
+                                const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_prefix_gate(WsPtrs pre, WsPtrs full, cudaStream_t st);
 // Key bit masks over the used vertices (tiles sort; S is the vertex stride, seg as for the compaction).
 cudaError_t launch_key_masks(int S, const void* vtx, int64_t nVtx, WsPtrs ws, const LaunchCfg& c, const SegArgs* seg,
                              cudaStream_t st);

@@ -28,18 +28,21 @@ namespace reindex {
 template <int S, int kHist, bool kSeg>
 __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ vtx, int64_t nVtx, WsPtrs ws,
                                                        int64_t tilesV, SegArgs seg, int64_t stall_tile) {
-  constexpr int SI = kSeg ? S + 4 : S;  // item key bytes
+  constexpr bool kPrefix = kHist == kHistPrefix;  // items keep the 8-byte prefix of the packed key
+  constexpr int KL = kSeg ? S / 4 + 1 : S / 4;     // key words loaded per vertex
+  constexpr int SI = kPrefix ? kPrefixItem : 4 * KL;  // item key bytes
   constexpr int K = SI / 4;
-  constexpr int P = SI;  // byte digits per key
-  constexpr bool kCount = kHist != kHistNone && kHist != kHistMasks;
+  constexpr int P = 4 * KL;  // byte digits per key
+  constexpr bool kCount = kHist != kHistNone && kHist != kHistMasks && !kPrefix;
   constexpr bool kMasks = kHist == kHistMasks;  // tiles sort without packing: the plan comes after
+  constexpr bool kPacks = kHist == kHistNone || kPrefix;  // the plan ran first (packing known)
   __shared__ uint32_t s_hist[kCount ? P * kRadix : 1];
   __shared__ uint32_t s_warp[kWarps];
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ KeyPack s_pack;
   __shared__ int s_first;
   Control* ctrl = ws.ctrl;
-  if (kHist == kHistNone && threadIdx.x == 0) {
+  if (kPacks && threadIdx.x == 0) {
     s_pack = ws.plan->pack;
     s_first = ws.plan->first;
   }
@@ -49,7 +52,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
     for (int i = t; i < P * kRadix; i += kThreads) s_hist[i] = 0;
   // digit of the first radix pass (tiles sort): byte 0 of the packed key, or a byte of the key
   // (kHistMasks: key byte 0, the first pass's digit unless that byte is constant)
-  const bool packed = kHist == kHistNone && s_pack.on;
+  const bool packed = kPacks && s_pack.on;
   const int first = kMasks ? 0 : (kCount ? -1 : s_first);
   const int fword = packed ? K - 1 : K - 1 - (first >> 2), fshift = packed ? 0 : (first & 3) * 8;
   uint32_t kor[K], knand[K];  // kHistMasks: this thread's OR of each key word and of its complement
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
       const int64_t wi = (vbase >> 5) + lane;
       if (wi * 32 < nVtx) myword = ws.bitmask[wi];
     }
-    uint32_t k[kCompactRows][K];
+    uint32_t k[kCompactRows][KL];
     uint32_t pos[kCompactRows];
     uint32_t used = 0, cnt = 0;
 #pragma unroll
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
         s_prefix = prefix;
         if (tile == tilesV - 1) {
           ctrl->U = prefix + total;
-          if (kHist == kHistNone) ws.plan->U = prefix + total;  // the plan ran before the compaction
+          if (kPacks) ws.plan->U = prefix + total;  // the plan ran before the compaction
         }
       }
     }
@@ -130,11 +133,24 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
       if (umask == 0) continue;  // warp-uniform
       if (u) {
         Item<SI> it;
-#pragma unroll
-        for (int q = 0; q < K; ++q) it.k[q] = k[r][q];
         it.id = (uint32_t)(vbase + r * 32 + lane);
+        if constexpr (kPrefix) {  // pack the whole key; its low 8 bytes are the prefix's bits
+          uint32_t full[KL];
+#pragma unroll
+          for (int q = 0; q < KL; ++q) full[q] = k[r][q];
+          if (s_pack.simple)
+            pack_key_simple<KL>(full, s_pack);
+          else
+            pack_key<KL>(full, s_pack);
+          it.k[0] = 0;
+          it.k[1] = full[KL - 2];
+          it.k[2] = full[KL - 1];
+        } else {
+#pragma unroll
+          for (int q = 0; q < K; ++q) it.k[q] = k[r][q];
+        }
         if constexpr (!kCount) {
-          if (packed) {
+          if (packed && !kPrefix) {
             if (s_pack.simple)
               pack_key_simple<K>(it.k, s_pack);
             else
@@ -158,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
       const int leader = __ffs(umask) - 1;
 #pragma unroll
       for (int d = 0; d < P; ++d) {
-        const uint32_t dig = u ? key_digit<K>(k[r], d) : 0u;
+        const uint32_t dig = u ? key_digit<KL>(k[r], d) : 0u;
         if (kHist == kHistMatchAny) {
           const uint32_t peers = __match_any_sync(0xffffffffu, u ? dig : 0x100u);
           if (u && (peers & lanemask_lt()) == 0) atomicAdd(&s_hist[d * kRadix + dig], (uint32_t)__popc(peers));
@@ -273,6 +289,66 @@ __global__ void __launch_bounds__(kThreads) k_key_masks(const void* __restrict__
   }
 }
 
+// Prefix sort check: every used vertex's key must equal the unique vertex it was given
+// (out_vtx[oldToNew[i]], written by the head scan).  Then each run of equal prefixes held one
+// key, runs with different prefixes hold different keys, and the runs are in key order: the
+// result is exact.  Otherwise ctrl->amb is set and the full-key sort runs.  The vertex array is
+// streamed (four vertices per thread with vector loads when 16-byte aligned); the unique vertices
+// are gathered (a fraction of the vertex array, largely served by L2).
+template <int S, bool kVec>
+__global__ void __launch_bounds__(kThreads) k_prefix_check(const void* __restrict__ vtx, int64_t nVtx,
+                                                            const void* __restrict__ out_vtx, WsPtrs ws) {
+  constexpr int KV = S / 4;
+  if (block_error(ws.ctrl)) return;
+  const uint32_t U = ws.plan->U;  // unique vertices are fewer (an index past it fails the check)
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  int64_t done = 0;
+  if constexpr (kVec) {
+    const uint4* v4 = reinterpret_cast<const uint4*>(vtx);
+    const int64_t n4 = nVtx >> 2;
+    for (int64_t g = blockIdx.x * (int64_t)kThreads + threadIdx.x; g < n4; g += stride) {
+      // the four vertices, their used bits and their new indices, all loads in flight together
+      uint32_t wds[4 * KV];
+#pragma unroll
+      for (int i = 0; i < KV; ++i) {
+        const uint4 x = __ldcs(v4 + g * KV + i);
+        wds[4 * i] = x.x; wds[4 * i + 1] = x.y; wds[4 * i + 2] = x.z; wds[4 * i + 3] = x.w;
+      }
+      const uint4 n4 = __ldg(reinterpret_cast<const uint4*>(ws.old2new) + g);
+      const uint32_t nids[4] = {n4.x, n4.y, n4.z, n4.w};
+      const uint32_t bits = (__ldg(ws.bitmask + (g >> 3)) >> ((g & 7) * 4)) & 0xFu;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!((bits >> j) & 1u)) continue;
+        if (nids[j] >= U) {
+          bad = true;
+          continue;
+        }
+        uint32_t u[KV];
+        load_key_ro<S>(out_vtx, nids[j], u);
+#pragma unroll
+        for (int q = 0; q < KV; ++q) bad |= u[q] != wds[j * KV + q];
+      }
+    }
+    done = n4 << 2;
+  }
+  for (int64_t v = done + blockIdx.x * (int64_t)kThreads + threadIdx.x; v < nVtx; v += stride) {
+    if (!((__ldg(ws.bitmask + (v >> 5)) >> (v & 31)) & 1u)) continue;
+    const uint32_t nid = __ldg(ws.old2new + v);
+    if (nid >= U) {
+      bad = true;
+      continue;
+    }
+    uint32_t k[KV], u[KV];
+    load_key<S>(vtx, v, k);
+    load_key_ro<S>(out_vtx, nid, u);
+#pragma unroll
+    for (int q = 0; q < KV; ++q) bad |= u[q] != k[q];
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&ws.ctrl->amb, 1u);
+}
+
 template <int S>
 static int occ() {
   int a = 0, b = 0, c = 0;
@@ -370,6 +446,44 @@ cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int6
       default: return cudaErrorInvalidValue;
     }
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact_prefix(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
+                                  cudaStream_t st) {
+  if (tilesV == 0) return cudaSuccess;
+  const bool persistent = !c.grid_per_tile;
+  const SegArgs none{};
+  switch (S) {
+    case 12: launch_v<12, kHistPrefix, false>(tilesV, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
+    case 16: launch_v<16, kHistPrefix, false>(tilesV, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
+    case 20: launch_v<20, kHistPrefix, false>(tilesV, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
+    case 24: launch_v<24, kHistPrefix, false>(tilesV, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
+    case 32: launch_v<32, kHistPrefix, false>(tilesV, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prefix_check(int S, const void* vtx, int64_t nVtx, const void* out_vtx, WsPtrs ws,
+                                const LaunchCfg& c, cudaStream_t st) {
+  if (nVtx == 0) return cudaSuccess;
+  int64_t g = (nVtx / 4 + kThreads - 1) / kThreads;
+  if (g > (int64_t)c.sms * 8) g = (int64_t)c.sms * 8;
+  if (g < 1) g = 1;
+  const bool vec = (reinterpret_cast<uintptr_t>(vtx) & 15) == 0;
+#define REINDEX_PC(SS)                                                                           \
+  (vec ? k_prefix_check<SS, true><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, out_vtx, ws)          \
+       : k_prefix_check<SS, false><<<(int)g, kThreads, 0, st>>>(vtx, nVtx, out_vtx, ws))
+  switch (S) {
+    case 12: REINDEX_PC(12); break;
+    case 16: REINDEX_PC(16); break;
+    case 20: REINDEX_PC(20); break;
+    case 24: REINDEX_PC(24); break;
+    case 32: REINDEX_PC(32); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef REINDEX_PC
   return cudaGetLastError();
 }
 

@@ -10,6 +10,8 @@
 // neither nodup nor newIdx is materialised.  If the radix sort packed the keys (their varying
 // bits only), run heads are found on the packed keys (equal exactly when the keys are) and only
 // the keys written out are restored; a mesh id (batched mode) is read from its packed bits.
+#include <atomic>
+
 #include "internal.h"
 
 namespace reindex {
@@ -19,11 +21,19 @@ constexpr int kHeadWarps = kHeadThreads / 32;
 // S is the item key size.  In batched mode (kSeg) key word 0 is the mesh id: only words 1.. are
 // written to out_vtx, and the first item of each mesh records that mesh's first output vertex.
 // kMayPack: the sort may have packed the keys (the call allows packing); else they are never packed.
-template <int S, bool kSeg, bool kMayPack>
-__global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsPtrs ws, void* __restrict__ out_vtx,
-                                                         int64_t* __restrict__ out_nVtx, uint32_t nVtx,
-                                                         SegArgs seg) {
+//
+// SV > 0 (prefix sort, S = 12, key word 0 zero): the items carry the 64 most significant varying bits of SV-byte
+// vertex keys; run heads are where that prefix changes, and each head writes its whole key, read
+// from the vertex array by its old index (loaded before the scan, so that the look-back wait
+// covers the latency of these random reads).  (k_prefix_check then confirms that equal prefixes
+// meant equal keys.)
+template <int S, bool kSeg, bool kMayPack, int SV = 0>
+__global__ void __launch_bounds__(kHeadThreads, (S >= 16 || SV > 0) ? 2 : 4)
+    k_head_scan(WsPtrs ws, void* __restrict__ out_vtx, int64_t* __restrict__ out_nVtx, uint32_t nVtx, SegArgs seg,
+                const void* __restrict__ vtx) {
   constexpr int K = S / 4;
+  constexpr bool kVerify = SV > 0;
+  constexpr int KV = kVerify ? SV / 4 : 1;
   __shared__ uint32_t s_warp[kHeadWarps];
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ KeyPack s_pack;
@@ -72,6 +82,7 @@ __global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsP
 
     uint32_t within[kHeadIpt];
     uint32_t heads = 0, cnt = 0, firsts = 0;
+    uint32_t hkey[kHeadIpt][KV];  // kVerify: whole keys of the heads
 #pragma unroll
     for (int r = 0; r < kHeadIpt; ++r) {
       const int64_t j = wbase + r * 32 + lane;
@@ -95,6 +106,8 @@ __global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsP
                            : it[r].k[0] != pks[0];
       }
       const bool head = (j < U) && (j == 0 || diff);
+      if constexpr (kVerify)  // the head's whole key, loaded now: in flight during the scan
+        if (head && it[r].id < nVtx) load_key_ro<SV>(vtx, it[r].id, hkey[r]);
       const uint32_t m = __ballot_sync(0xffffffffu, head);
       within[r] = cnt + __popc(m & lanemask_lt());
       heads |= (uint32_t)head << r;
@@ -136,7 +149,9 @@ __global__ void __launch_bounds__(kHeadThreads, S >= 16 ? 2 : 4) k_head_scan(WsP
         const uint32_t nid = head ? e : e - 1u;
         if (it[r].id < nVtx) {
           st_u32_hint(ws.old2new + it[r].id, nid, keep);
-          if (head || (kSeg && ((firsts >> r) & 1u))) {
+          if constexpr (kVerify) {
+            if (head) store_key<SV>(out_vtx, nid, hkey[r]);  // the unique vertex
+          } else if (head || (kSeg && ((firsts >> r) & 1u))) {
             uint32_t key[K];
 #pragma unroll
             for (int q = 0; q < K; ++q) key[q] = it[r].k[q];
@@ -171,6 +186,43 @@ static int occ() {
   return n < 1 ? 1 : n;
 }
 
+// Resident CTAs per SM of the prefix-sort variant (queried once per stride).
+template <int SV>
+static int occ_verify() {
+  static std::atomic<int> cached{0};
+  int n = cached.load(std::memory_order_relaxed);
+  if (n == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_head_scan<kPrefixItem, false, false, SV>, kHeadThreads, 0);
+    if (n < 1) n = 1;
+    cached.store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+
+template <int SV>
+static void launch_verify(int64_t tiles, const LaunchCfg& c, WsPtrs ws, const void* vtx, void* out_vtx,
+                          int64_t* out_nVtx, uint32_t nVtx, cudaStream_t st) {
+  int64_t g = c.grid_per_tile ? tiles : (int64_t)c.sms * occ_verify<SV>();
+  if (g > tiles) g = tiles;
+  if (g < 1) g = 1;
+  k_head_scan<kPrefixItem, false, false, SV><<<(int)g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx,
+                                                                                  SegArgs{}, vtx);
+}
+
+cudaError_t launch_head_scan_prefix(int S, WsPtrs ws, const void* vtx, void* out_vtx, int64_t* out_nVtx,
+                                    uint32_t nVtx, const LaunchCfg& c, cudaStream_t st) {
+  const int64_t tiles = (ws.Umax + kHeadTile - 1) / kHeadTile;
+  switch (S) {
+    case 12: launch_verify<12>(tiles, c, ws, vtx, out_vtx, out_nVtx, nVtx, st); break;
+    case 16: launch_verify<16>(tiles, c, ws, vtx, out_vtx, out_nVtx, nVtx, st); break;
+    case 20: launch_verify<20>(tiles, c, ws, vtx, out_vtx, out_nVtx, nVtx, st); break;
+    case 24: launch_verify<24>(tiles, c, ws, vtx, out_vtx, out_nVtx, nVtx, st); break;
+    case 32: launch_verify<32>(tiles, c, ws, vtx, out_vtx, out_nVtx, nVtx, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 int occupancy_head(int S) {
   switch (S) {
     case 4: return occ<4>();
@@ -187,9 +239,9 @@ template <int S, bool kSeg>
 static void launch_s(int g, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx, const SegArgs& seg,
                      bool may_pack, cudaStream_t st) {
   if (may_pack)
-    k_head_scan<S, kSeg, true><<<g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx, seg);
+    k_head_scan<S, kSeg, true><<<g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx, seg, nullptr);
   else
-    k_head_scan<S, kSeg, false><<<g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx, seg);
+    k_head_scan<S, kSeg, false><<<g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx, seg, nullptr);
 }
 
 cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx,

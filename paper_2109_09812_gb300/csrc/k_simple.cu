@@ -35,6 +35,7 @@ constexpr int kBatch = 4;
 template <bool kVec>
 __global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int64_t M, uint32_t nVtx,
                                                           uint32_t* bitmask, Control* ctrl) {
+  if (*(volatile const uint32_t*)&ctrl->err) return;  // skipped full-key sort (or an earlier error)
   bool bad = false;
   const int64_t t0 = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * kThreads;
@@ -69,7 +70,59 @@ __global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int
 // the histogram.  From the key bit masks (tiles sort, no histograms): if packing the varying bits
 // (KeyPack) saves at least one pass, the passes sort the bytes of the packed key and the positions
 // past its last byte are trivial; otherwise the raw bytes without a varying bit are trivial.
-__global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from_masks, int allow_pack) {
+//
+// Prefix sort (prefix_words = K > 0 words of key masks, P = 12): the packing keeps only the 64 most
+// significant varying bits of the K-word key (the top part of a run that straddles the cut), so
+// the items sort by an order-preserving 8-byte prefix of the packed key (digits 8-11 are zero).
+//
+// After a device-detected error (or in a skipped full-key sort) every pass is marked trivial.
+__device__ void plan_prefix_pack(const Control* ctrl, int K, KeyPack& kp, int& nbits) {
+  uint8_t rw[kMaxPackRuns], rs[kMaxPackRuns], rl[kMaxPackRuns];  // most significant run first
+  int n = 0, need = 8 * kPrefixBytes;
+  for (int wd = 0; wd < K && need > 0 && n < kMaxPackRuns; ++wd) {
+    const uint32_t m = ctrl->kor[wd] & ctrl->knand[wd];
+    for (int b = 31; b >= 0 && need > 0 && n < kMaxPackRuns;) {
+      if (!((m >> b) & 1u)) {
+        --b;
+        continue;
+      }
+      int e = b;
+      while (e >= 0 && ((m >> e) & 1u)) --e;  // run = bits e+1 .. b
+      int len = b - e, lo = e + 1;
+      if (len > need) {  // keep the run's most significant bits
+        lo = b - need + 1;
+        len = need;
+      }
+      rw[n] = (uint8_t)wd;
+      rs[n] = (uint8_t)lo;
+      rl[n] = (uint8_t)len;
+      ++n;
+      need -= len;
+      b = e;
+    }
+  }
+  kp = KeyPack{};
+  kp.on = 1;
+  kp.simple = 1;
+  int pos = 0;
+  for (int i = n - 1; i >= 0; --i) {  // least significant first
+    const int r = n - 1 - i;
+    kp.word[r] = rw[i];
+    kp.shift[r] = rs[i];
+    kp.len[r] = rl[i];
+    kp.pos[r] = (uint8_t)pos;
+    pos += rl[i];
+    if (kp.wlen[rw[i]]) kp.simple = 0;  // two runs in one word
+    kp.wshift[rw[i]] = rs[i];
+    kp.wlen[rw[i]] = rl[i];
+  }
+  kp.nruns = (uint8_t)n;
+  kp.nbits = (uint8_t)pos;
+  nbits = pos;
+}
+
+__global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from_masks, int allow_pack,
+                                                      int prefix_words) {
   __shared__ uint32_t s_warp[kRadix / 32];
   __shared__ uint32_t s_or[kRadix / 32], s_and[kRadix / 32];
   __shared__ int s_np;  // bytes of the packed key, or -1 (keys not packed)
@@ -77,10 +130,28 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from
   const uint32_t U = ws.ctrl->U;
   Plan* plan = ws.plan;
   const int K = P / 4;
+  if (*(volatile const uint32_t*)&ws.ctrl->err != 0) {  // same value in every thread (written before launch)
+    if (t < kMaxDigits) {
+      plan->skip[t] = 1;
+      plan->next[t] = -1;
+    }
+    if (t == 0) {
+      plan->first = -1;
+      plan->pack.on = 0;
+      plan->U = 0;
+    }
+    return;
+  }
   if (t == 0) {
     int np = -1;
     plan->pack.on = 0;
-    if (from_masks && allow_pack) {
+    if (prefix_words > 0) {
+      KeyPack kp;
+      int nbits = 0;
+      plan_prefix_pack(ws.ctrl, prefix_words, kp, nbits);
+      plan->pack = kp;
+      np = (nbits + 7) / 8;
+    } else if (from_masks && allow_pack) {
       KeyPack kp{};
       int pos = 0, nraw = 0;
       bool fits = true;
@@ -190,7 +261,8 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from
 template <bool kVec>
 __global__ void __launch_bounds__(kThreads) k_remap(const int32_t* idx, int32_t* out, int64_t M,
                                                      const uint32_t* __restrict__ o2n, const Control* ctrl) {
-  if (ctrl->err) return;  // outputs are unspecified after a device-detected error
+  const uint32_t err = ctrl->err;
+  if (err && err != kErrSkip) return;  // outputs are unspecified after a device-detected error
   const int64_t t0 = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * kThreads;
   int64_t done = 0;
@@ -244,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_elements(const int32_t* idx
 
 __global__ void k_finalize(Control* ctrl, int64_t* out_nVtx) {
   const uint32_t e = ctrl->err;
-  if (e) {
+  if (e && e != kErrSkip) {
     *out_nVtx = -(int64_t)e;
     atomicCAS(&g_sticky_err, 0u, e);
   }
@@ -281,7 +353,27 @@ cudaError_t launch_used_flags(const int32_t* idx, int64_t M, int64_t nVtx, WsPtr
 }
 
 cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, bool allow_pack, cudaStream_t st) {
-  k_sort_plan<<<1, kRadix, 0, st>>>(ws, S, from_masks ? 1 : 0, allow_pack ? 1 : 0);
+  k_sort_plan<<<1, kRadix, 0, st>>>(ws, S, from_masks ? 1 : 0, allow_pack ? 1 : 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prefix_plan(int S, WsPtrs ws, cudaStream_t st) {
+  k_sort_plan<<<1, kRadix, 0, st>>>(ws, kPrefixItem, 1, 1, S / 4);
+  return cudaGetLastError();
+}
+
+// The full-key sort of a prefix-sorted call runs only where the prefix sort found two different
+// keys with one prefix; a device error of the prefix sort skips it and is reported by it.
+__global__ void k_prefix_gate(const Control* pre, Control* full) {
+  const uint32_t e = pre->err;
+  if (e)
+    full->err = e;
+  else if (!pre->amb)
+    full->err = kErrSkip;
+}
+
+cudaError_t launch_prefix_gate(WsPtrs pre, WsPtrs full, cudaStream_t st) {
+  k_prefix_gate<<<1, 1, 0, st>>>(pre.ctrl, full.ctrl);
   return cudaGetLastError();
 }
 

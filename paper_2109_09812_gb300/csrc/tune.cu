@@ -104,8 +104,9 @@ reindex_status reindex_autotune(const void* vtx, int64_t nVtx, int S, const int3
                             {"hist=uniform", "hist=peel", "hist=match", nullptr},
                             {"grid=persist", "grid=tile", nullptr, nullptr},
                             {"swaves=tile", "swaves=1", "swaves=4", nullptr},
-                            {"pack=auto", "pack=on", "pack=off", nullptr}};
-  for (int ki = 0; ki < 6; ++ki) {
+                            {"pack=auto", "pack=on", "pack=off", nullptr},
+                            {"prefix=auto", "prefix=on", "prefix=off", nullptr}};
+  for (int ki = 0; ki < 7; ++ki) {
     const auto& knob = knobs[ki];
     if (rs != REINDEX_OK) break;
     if (S >= kWideMin && ki < 3) continue;  // 24- and 32-byte keys: one sort and rank variant only

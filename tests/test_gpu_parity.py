@@ -260,7 +260,7 @@ def test_profile_records_every_kernel(rx, sort):
     m = synth.config_mesh(1)
     v, i = to_dev(m.vtx, m.idx)
     saved = rx.reindex_tuning_get(12)
-    rx.reindex_tuning_set(12, f"sort={sort}")
+    rx.reindex_tuning_set(12, f"sort={sort},prefix=off")
     rx.profile_collect()
     rx.profile_enable(True)
     try:
@@ -275,7 +275,7 @@ def test_profile_records_every_kernel(rx, sort):
     for k in mine:
         assert names.count(k) == (1 if k == "key_masks" else 12)
     others = {k for ks in SORT_KERNELS.values() for k in ks} - set(mine)
-    assert set(names) == set(rx.KERNEL_NAMES) - {"seg_prepare", "seg_offsets"} - others
+    assert set(names) == set(rx.KERNEL_NAMES) - {"seg_prepare", "seg_offsets", "prefix_gate", "prefix_check"} - others
     # x and y are integers 0..256 as float32: their lowest byte is always zero -> skipped passes
     # (packed keys: the skipped passes are the top digit positions instead)
     sk = {r["digit"]: r["skipped"] for r in recs if r["name"] == mine[0]}
@@ -285,10 +285,10 @@ def test_profile_records_every_kernel(rx, sort):
 
 
 # Every radix-pass variant (and grid shape) must give the same bit-exact result.
-SORT_VARIANTS = ["sort=regs,rank=ballot,grid=persist", "sort=regs,rank=match,grid=tile",
-                 "sort=pipe,rank=ballot,grid=persist", "sort=tiles,rank=ballot,swaves=1,pack=on",
-                 "sort=tiles,rank=match,swaves=tile,pack=off", "sort=tiles,rank=ballot,swaves=4,pack=off",
-                 "sort=tiles,rank=vary,swaves=tile,pack=on", "sort=tiles,rank=ballot,pack=auto"]
+SORT_VARIANTS = ["sort=regs,rank=ballot,grid=persist,prefix=off", "sort=regs,rank=match,grid=tile",
+                 "sort=pipe,rank=ballot,grid=persist,prefix=off", "sort=tiles,rank=ballot,swaves=1,pack=on",
+                 "sort=tiles,rank=match,swaves=tile,pack=off,prefix=off", "sort=tiles,rank=ballot,swaves=4,pack=off",
+                 "sort=tiles,rank=vary,swaves=tile,pack=on,prefix=off", "sort=tiles,rank=ballot,pack=auto"]
 
 
 @pytest.mark.parametrize("spec", SORT_VARIANTS)
@@ -308,7 +308,8 @@ def test_sort_variants_bit_exact(rx, spec, S):
         rx.reindex_tuning_set(S, saved)
 
 
-WIDE_VARIANTS = ["pack=off,swaves=tile", "pack=on,swaves=tile", "pack=auto,swaves=1", "pack=on,swaves=4"]
+WIDE_VARIANTS = ["pack=off,swaves=tile,prefix=off", "pack=on,swaves=tile,prefix=off", "pack=auto,swaves=1",
+                 "pack=on,swaves=4"]
 
 
 @pytest.mark.parametrize("spec", WIDE_VARIANTS)
@@ -383,3 +384,53 @@ def test_attribute_generator_device_matches_host(rx):
         host = synth.with_attributes(m.vtx, n_attr, 23)
         dev = synth.with_attributes_gpu(torch.from_numpy(m.vtx.view(np.int32)).cuda(), n_attr, 23)
         np.testing.assert_array_equal(dev.cpu().numpy().view(np.uint32), host)
+
+
+def _sort_records(rx, S, spec, vtx, idx):
+    """Per-launch records of one call under tuning `spec` for stride S."""
+    saved = rx.reindex_tuning_get(S)
+    rx.reindex_tuning_set(S, spec)
+    v, i = to_dev(vtx, idx.reshape(-1, 3))
+    rx.profile_collect()
+    rx.profile_enable(True)
+    try:
+        out_v, out_n, out_i = rx.reindex_mesh(v, i)
+        torch.cuda.synchronize()
+    finally:
+        rx.profile_enable(False)
+        rx.reindex_tuning_set(S, saved)
+    return rx.profile_collect(), int(out_n.item()), out_v, out_i
+
+
+@pytest.mark.parametrize("S", [12, 16, 24, 32])
+def test_prefix_sort_skips_the_full_key_sort(rx, S):
+    """Vertices whose 64 most significant varying bits already tell them apart (a heightfield's x, y
+    and the top of z): the prefix sort gives the result and every pass of the full-key sort is
+    skipped.  Keys that share prefixes (few values per word) run the full-key sort; both bit-exact."""
+    m = synth.heightfield_soup_attrs(200, 130, 0.05, seed=3, stride=S) if S > 12 else \
+        synth.heightfield_soup(200, 130, 0.05, seed=3)
+    if S == 16:
+        m = synth.Mesh(vtx=m.vtx[:, :4], idx=m.idx)
+    ov, oi = oracle.reindex_sort(m.vtx, m.idx.reshape(-1))
+    recs, D, out_v, out_i = _sort_records(rx, S, "prefix=on,sort=tiles", m.vtx, m.idx)
+    assert D == ov.shape[0]
+    np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+    sc = [r for r in recs if r["name"] == "tile_scatter"]  # in launch order: the prefix sort's 8 passes first
+    pre, full = sc[:8], sc[8:]
+    assert len(full) == S and all(r["item_bytes"] == 16 for r in pre) and all(r["item_bytes"] == S + 4 for r in full)
+    assert sum(not r["skipped"] for r in pre) >= 6
+    assert all(r["skipped"] for r in full)
+    assert [r["name"] for r in recs].count("prefix_gate") == 1
+    assert [r["name"] for r in recs].count("prefix_check") == 1
+
+    rng = np.random.default_rng(S)
+    vtx, idx = random_mesh(rng, 30000, 30000, S // 4, "dups")  # 7 values per word: prefixes collide
+    ov, oi = oracle.reindex_sort(vtx, idx)
+    recs, D, out_v, out_i = _sort_records(rx, S, "prefix=on,sort=tiles", vtx, idx[: 30000 // 3 * 3])
+    ov, oi = oracle.reindex_sort(vtx, idx[: 30000 // 3 * 3])
+    assert D == ov.shape[0]
+    np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+    full = [r for r in recs if r["name"] == "tile_scatter"][8:]
+    assert sum(not r["skipped"] for r in full) >= 8
