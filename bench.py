@@ -70,6 +70,8 @@ WORKLOADS = {
     "heightfield2048_s24": ("heightfield triangle soup 2048x2048 cells with 24-byte vertices (float32 xyz + 3 "
                             "normal-like words in [-1,1), each a hash of the position; 25,165,824 soup vertices "
                             "+ 5% unused, permuted), int32 idx x3, seed 2", (2048, 0.05, 2, 24)),
+    "heightfield1448_s32": ("heightfield triangle soup 1448x1448 cells with 32-byte vertices (as heightfield2048_s32), "
+                            "for profiler captures", (1448, 0.05, 2, 32)),
     # a half-size case of the 2048^2 workload, for profiler captures (still larger than L2)
     "heightfield1448": ("heightfield triangle soup 1448x1448 cells (4,193,408 tris, 12,580,224 soup vertices "
                         "float32 xyz + 5% unused, permuted), int32 idx x3, seed 2", (1448, 0.05, 2)),
