@@ -229,7 +229,6 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
   // below then runs only if two different keys shared a prefix (else every kernel of it returns
   // at once).  Both write the same outputs; the remap and the finalize come once, at the end.
   const bool prefix = c.prefix && S > kPrefixBytes;
-  if (prefix) c.scatter_waves = 1;  // the full-key sort's passes: few CTAs, cheap when skipped
   const WsPtrs pp = prefix ? ws_ptrs_prefix(ws, L) : p;
   {
     prof::Scope s(REINDEX_K_CLEAR, -1, st);
@@ -280,6 +279,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
     }
     prof::Scope s(REINDEX_K_USED_FLAGS, -1, st);
     REINDEX_TRY(launch_used_flags(idx, M, nVtx, p, c, st));
+    c.scatter_waves = 1;  // the full-key sort's passes: few CTAs, cheap when skipped
   }
   if (c.sort_kernel == kSortTiles && c.pack_keys) {  // bit masks -> plan (key packing) -> compaction
     {
