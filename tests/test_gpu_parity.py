@@ -434,3 +434,63 @@ def test_prefix_sort_skips_the_full_key_sort(rx, S):
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
     full = [r for r in recs if r["name"] == "tile_scatter"][8:]
     assert sum(not r["skipped"] for r in full) >= 8
+
+
+@pytest.mark.parametrize("S", [16, 32])
+def test_prefix_sort_reports_device_errors(rx, S):
+    """An index out of range, and a look-back wait that runs out, inside the prefix sort: the call
+    reports the error (the full-key sort is skipped), and the next call is exact."""
+    import time
+
+    m = synth.heightfield_soup_attrs(64, 64, 0.05, seed=31, stride=S)  # 25,805 vertices: 13 compaction tiles
+    idx = m.idx.copy()
+    idx.reshape(-1)[777] = m.n_vtx
+    v, i = to_dev(m.vtx, idx)
+    rx.reindex_stream_status()
+    out_v, out_n, out_i = rx.reindex_mesh(v, i)
+    assert rx.reindex_stream_status() == rx.REINDEX_ERR_INDEX_RANGE
+    assert int(out_n.item()) == -rx.REINDEX_ERR_INDEX_RANGE
+    v, i = to_dev(m.vtx, m.idx)
+    rx.lib().reindex_debug_stall_tile(5)
+    try:
+        t0 = time.time()
+        out_v, out_n, out_i = rx.reindex_mesh(v, i)
+        status = rx.reindex_stream_status()
+        elapsed = time.time() - t0
+    finally:
+        rx.lib().reindex_debug_stall_tile(-1)
+    assert status == rx.REINDEX_ERR_TIMEOUT and int(out_n.item()) == -rx.REINDEX_ERR_TIMEOUT
+    assert elapsed < 60
+    assert assert_parity(rx, m.vtx, m.idx.reshape(-1), 3) == 65 * 65
+
+
+@pytest.mark.parametrize("S", [16, 32])
+def test_prefix_sort_host_buffers_and_graph_capture(rx, S):
+    """The host-buffer entry point and a captured CUDA graph of the workspace variant, both on
+    the prefix sort."""
+    m = synth.heightfield_soup_attrs(150, 90, 0.05, seed=5, stride=S)
+    ov, oi = oracle.reindex_sort(m.vtx, m.idx)
+    hv = torch.from_numpy(m.vtx.view(np.int32)).pin_memory()
+    hi = torch.from_numpy(m.idx).pin_memory()
+    out_v, out_i = rx.reindex_mesh_host(hv, hi)
+    np.testing.assert_array_equal(out_v.numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out_i.numpy().reshape(-1), oi)
+    v, i = to_dev(m.vtx, m.idx)
+    ws = torch.empty(rx.reindex_workspace_size(m.n_vtx, S, m.n_elem, 3), dtype=torch.uint8, device="cuda")
+    out_v = torch.empty((min(m.n_vtx, i.numel()), S // 4), dtype=torch.int32, device="cuda")
+    out_n = torch.empty(1, dtype=torch.int64, device="cuda")
+    out_i = torch.empty_like(i)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        rx.reindex_mesh_ws(v, i, ws, out_v, out_n, out_i)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rx.reindex_mesh_ws(v, i, ws, out_v, out_n, out_i, stream=s)
+    out_i.zero_()
+    out_n.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(out_n.item()) == ov.shape[0]
+    np.testing.assert_array_equal(out_v[: ov.shape[0]].cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)

@@ -27,7 +27,7 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("S", [4, 8, 12, 16, 20])
+@pytest.mark.parametrize("S", [4, 8, 12, 16, 20, 24, 32])
 def test_merge_equals_concatenate_offset_dedup(rx, S):
     """Section 3.2: concatenate the vertex arrays, add each mesh's vertex offset to its indices,
     then remove duplicates -- here across meshes."""
@@ -77,6 +77,38 @@ def test_submesh_equals_copy_of_selected_elements(rx, keep):
         sel = np.concatenate([sel, sel[:17]])  # repeats are allowed and kept
     ov, oi = oracle.reindex_sort(m.vtx, m.idx[sel])
     out_v, out_n, out_i = rx.reindex_submesh(dev(m.vtx.view(np.int32)), dev(m.idx), dev(sel))
+    torch.cuda.synchronize()
+    D = int(out_n.item())
+    assert D == ov.shape[0]
+    np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+
+
+@pytest.mark.parametrize("S", [16, 32])
+def test_merge_and_submesh_with_prefix_sort(rx, S):
+    """Merging and subset extraction of wide vertices go through the prefix sort (its first pass
+    rewrites the indices in place, so the full-key sort, when needed, must see them intact)."""
+    meshes = [synth.heightfield_soup_attrs(40, 30, 0.05, seed=3, stride=S)] * 2
+    m0 = meshes[0]
+    vtx = np.concatenate([m0.vtx, m0.vtx])
+    voff = np.array([0, m0.n_vtx, 2 * m0.n_vtx], np.int64)
+    eoff = np.array([0, m0.n_elem, 2 * m0.n_elem], np.int64)
+    idx = np.concatenate([m0.idx, m0.idx])
+    ov, oi = oracle.reindex_sort(vtx, np.concatenate([m0.idx, m0.idx + m0.n_vtx]))
+    out_v, out_n, out_i = rx.reindex_merge_meshes(dev(vtx.view(np.int32)), dev(voff), dev(idx), dev(eoff))
+    torch.cuda.synchronize()
+    D = int(out_n.item())
+    assert D == ov.shape[0] == 41 * 31
+    np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+    # subset of a mesh whose keys share prefixes (few values per word): the full-key sort runs
+    rng = np.random.default_rng(S)
+    pool = rng.integers(0, 2**32, size=(5, S // 4), dtype=np.uint64).astype(np.uint32)
+    wv = pool[rng.integers(0, 5, size=(6000, S // 4)), np.arange(S // 4)]
+    widx = rng.integers(0, 6000, size=(4000, 3)).astype(np.int32)
+    sel = np.flatnonzero(rng.random(4000) < 0.4).astype(np.int32)
+    ov, oi = oracle.reindex_sort(wv, widx[sel])
+    out_v, out_n, out_i = rx.reindex_submesh(dev(wv.view(np.int32)), dev(widx), dev(sel))
     torch.cuda.synchronize()
     D = int(out_n.item())
     assert D == ov.shape[0]

@@ -70,6 +70,19 @@ def test_noalloc_matches_reindex_mesh_twice_in_a_row(rx):
         assert torch.equal(ni, ri)
 
 
+@pytest.mark.parametrize("words", [6, 8])
+def test_noalloc_wide_vertices_at_the_limit(rx, words):
+    """24- and 32-byte vertices at the largest size the static scratch holds."""
+    v, i = _mesh(3, 262_144, 87_381, 3, words)
+    rc, nv, nn, ni = _noalloc(rx, v, i)
+    assert rc == rx.REINDEX_OK
+    rv, rn, ri = rx.reindex_mesh(v, i)
+    torch.cuda.synchronize()
+    D = int(rn.item())
+    assert D > 0 and int(nn.item()) == D
+    assert torch.equal(nv[:D], rv[:D]) and torch.equal(ni, ri)
+
+
 def test_noalloc_refuses_meshes_over_the_limit(rx):
     n = 262_144 + 1
     v = torch.zeros((n, 3), dtype=torch.int32, device="cuda")
