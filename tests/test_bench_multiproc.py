@@ -58,3 +58,25 @@ def test_reference_arm_under_torchrun_prints_one_line():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_sort_pass_roofline_weighs_each_pass_by_its_item_size():
+    """The dominant kernel's algorithmic bytes come from each launch's own item size (a call that
+    sorts by key prefix first moves 16-byte records, then maybe whole (S+4)-byte items); skipped
+    passes do not count."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    U = 1000
+    recs = [dict(name="tile_scatter", skipped=False, ms=1.0, item_bytes=16) for _ in range(8)]
+    recs += [dict(name="tile_scatter", skipped=True, ms=0.01, item_bytes=36) for _ in range(32)]
+    recs += [dict(name="head_scan", skipped=False, ms=5.0, item_bytes=0)]
+    kname, per_launch, avg_ms, item_bytes, n = bench.sort_pass_roofline(recs, U)
+    assert (kname, per_launch, avg_ms, item_bytes, n) == ("tile_scatter", 2 * U * 16, 1.0, 16, 8)
+    recs[8]["skipped"] = False  # one whole-key pass moved data too
+    recs[8]["ms"] = 2.0
+    kname, per_launch, avg_ms, item_bytes, n = bench.sort_pass_roofline(recs, U)
+    assert n == 9 and item_bytes == [16, 36]
+    assert per_launch == (8 * 2 * U * 16 + 2 * U * 36) / 9 and avg_ms == 10.0 / 9
+    kname, *_ = bench.sort_pass_roofline([dict(name="onesweep", skipped=False, ms=1.0, item_bytes=16)], U)
+    assert kname == "onesweep"
