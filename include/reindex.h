@@ -273,6 +273,15 @@ void reindex_debug_stall_tile(int64_t tile);
  * number of inconsistencies (0 = correct).  Needs no GPU. */
 int reindex_debug_arena_check(uint64_t seed, int ops, size_t size);
 
+/* Host-only test hook: the bit selection of the prefix sort for keys of K (1..8) 32-bit words,
+ * given per word the OR of the word over the used vertices (kor) and of its complement (knand): a
+ * bit varies iff it is set in both.  The prefix is the 64 most significant varying bits (at most
+ * 16 runs of consecutive bits), word 0 most significant.  Writes the packing description (88
+ * bytes: on, nbits, nruns, word[16], shift[16], len[16], pos[16] -- runs least significant first,
+ * pos = the run's offset in the prefix --, simple, wshift[8], wlen[8], 4 bytes padding) to `out`
+ * and returns the number of prefix bits, or -1 for bad arguments.  Needs no GPU. */
+int reindex_debug_prefix_pack(const uint32_t* kor, const uint32_t* knand, int K, void* out, int outBytes);
+
 /* Synchronises `stream`, then returns and clears this device's sticky device-side error: the
  * first INDEX_RANGE or TIMEOUT raised by any call on the current device since the last
  * reindex_stream_status() (REINDEX_OK if none).  A CUDA error from the synchronisation is

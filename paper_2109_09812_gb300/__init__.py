@@ -42,7 +42,7 @@ EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "
             "reindex_server_drain", "reindex_server_get_stats", "reindex_server_destroy", "reindex_debug_arena_check",
             "reindex_merge_workspace_size", "reindex_merge_meshes", "reindex_submesh_workspace_size",
             "reindex_submesh", "reindex_autotune", "reindex_tuning_get", "reindex_tuning_set",
-            "reindex_debug_stall_tile"]
+            "reindex_debug_stall_tile", "reindex_debug_prefix_pack"]
 
 _lock = threading.Lock()
 _lib = None
@@ -147,6 +147,8 @@ def lib() -> ctypes.CDLL:
             L.reindex_debug_stall_tile.restype = None
             L.reindex_debug_arena_check.argtypes = [ctypes.c_uint64, ci, ctypes.c_size_t]
             L.reindex_debug_arena_check.restype = ci
+            L.reindex_debug_prefix_pack.argtypes = [vp, vp, ci, vp, ci]
+            L.reindex_debug_prefix_pack.restype = ci
             _lib = L
     return _lib
 
@@ -478,6 +480,23 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def debug_prefix_pack(kor, knand) -> dict:
+    """Host-only: the prefix sort's choice of key bits for per-word masks (test hook)."""
+    import numpy as np
+
+    kor = np.ascontiguousarray(kor, dtype=np.uint32)
+    knand = np.ascontiguousarray(knand, dtype=np.uint32)
+    buf = ctypes.create_string_buffer(88)
+    nbits = lib().reindex_debug_prefix_pack(kor.ctypes.data, knand.ctypes.data, int(kor.shape[0]), buf, 88)
+    if nbits < 0:
+        raise ValueError("bad masks")
+    b = buf.raw
+    n = b[2]
+    return dict(on=b[0], nbits=b[1], nruns=n, word=list(b[3:3 + n]), shift=list(b[19:19 + n]),
+                len=list(b[35:35 + n]), pos=list(b[51:51 + n]), simple=b[67], wshift=list(b[68:76]),
+                wlen=list(b[76:84]), returned=nbits)
 
 
 def debug_arena_check(seed: int, ops: int, size: int) -> int:

@@ -5,6 +5,8 @@
 //                 trivial (digit constant over all items) and the buffer each pass reads
 //   k_remap       Section 2.4: out_idx[j] = oldToNew[idx[j]]
 //   k_finalize    propagate a device-detected error into *out_nVtx and the sticky word
+#include <cstring>
+
 #include "internal.h"
 
 namespace reindex {
@@ -76,11 +78,13 @@ __global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int
 // the items sort by an order-preserving 8-byte prefix of the packed key (digits 8-11 are zero).
 //
 // After a device-detected error (or in a skipped full-key sort) every pass is marked trivial.
-__device__ void plan_prefix_pack(const Control* ctrl, int K, KeyPack& kp, int& nbits) {
+// kor[q] / knand[q]: OR of key word q over the used vertices and of its complement.
+__host__ __device__ void plan_prefix_pack(const uint32_t* kor, const uint32_t* knand, int K, KeyPack& kp,
+                                          int& nbits) {
   uint8_t rw[kMaxPackRuns], rs[kMaxPackRuns], rl[kMaxPackRuns];  // most significant run first
   int n = 0, need = 8 * kPrefixBytes;
   for (int wd = 0; wd < K && need > 0 && n < kMaxPackRuns; ++wd) {
-    const uint32_t m = ctrl->kor[wd] & ctrl->knand[wd];
+    const uint32_t m = kor[wd] & knand[wd];
     for (int b = 31; b >= 0 && need > 0 && n < kMaxPackRuns;) {
       if (!((m >> b) & 1u)) {
         --b;
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from
     if (prefix_words > 0) {
       KeyPack kp;
       int nbits = 0;
-      plan_prefix_pack(ws.ctrl, prefix_words, kp, nbits);
+      plan_prefix_pack(ws.ctrl->kor, ws.ctrl->knand, prefix_words, kp, nbits);
       plan->pack = kp;
       np = (nbits + 7) / 8;
     } else if (from_masks && allow_pack) {
@@ -416,3 +420,14 @@ cudaError_t read_and_clear_sticky(uint32_t* value, cudaStream_t st) {
 }
 
 }  // namespace reindex
+
+// Host test hook (include/reindex.h): the prefix sort's packing for given key masks.
+extern "C" int reindex_debug_prefix_pack(const uint32_t* kor, const uint32_t* knand, int K, void* out, int outBytes) {
+  using namespace reindex;
+  if (K < 1 || K > kMaxDigits / 4 || !kor || !knand || !out || outBytes < (int)sizeof(KeyPack)) return -1;
+  KeyPack kp;
+  int nbits = 0;
+  plan_prefix_pack(kor, knand, K, kp, nbits);
+  std::memcpy(out, &kp, sizeof(KeyPack));
+  return nbits;
+}

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2109_09812_gb300 as rx
@@ -89,3 +90,64 @@ def test_server_arena_allocator_host_check(L, seed, size):
     """The serving arena allocator (first fit, coalescing, 256-byte alignment) against a brute-force
     model: no overlaps, no refusal while a large enough gap exists, full coalescing at the end."""
     assert rx.debug_arena_check(seed, 5000, size) == 0
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 5, 6, 8])
+def test_prefix_sort_bit_selection(L, K):
+    """The prefix sort keeps the most significant varying key bits: the bits it selects are exactly
+    the first ones of the varying bits listed from word 0's bit 31 down (64 of them, or fewer when
+    the 16-run limit or the key runs out), described as runs least significant first, each placed
+    right above the previous one.  Keys whose prefixes differ then compare like their prefixes."""
+    import random
+
+    rnd = random.Random(100 + K)
+    for trial in range(200):
+        kor, knand = [], []
+        for _ in range(K):
+            style = rnd.randrange(4)
+            if style == 0:
+                m = 0
+            elif style == 1:
+                m = 0xFFFFFFFF
+            elif style == 2:  # a few runs
+                m = 0
+                for _ in range(rnd.randrange(1, 4)):
+                    lo = rnd.randrange(32)
+                    hi = rnd.randrange(lo, 32)
+                    m |= ((1 << (hi - lo + 1)) - 1) << lo
+            else:
+                m = rnd.getrandbits(32)
+            const = rnd.getrandbits(32) & ~m
+            kor.append(m | const)
+            knand.append(m | (~const & 0xFFFFFFFF & ~m))
+        p = rx.debug_prefix_pack(np.array(kor, np.uint32), np.array(knand, np.uint32))
+        varying = [(w, b) for w in range(K) for b in range(31, -1, -1) if ((kor[w] & knand[w]) >> b) & 1]
+        selected = set()
+        for r in range(p["nruns"]):
+            assert 1 <= p["len"][r] and p["shift"][r] + p["len"][r] <= 32
+            selected |= {(p["word"][r], b) for b in range(p["shift"][r], p["shift"][r] + p["len"][r])}
+            assert p["pos"][r] == sum(p["len"][:r])
+        n = p["nbits"]
+        assert p["returned"] == n == len(selected) <= 64 and p["nruns"] <= 16 and p["on"] == 1
+        assert selected == set(varying[:n])
+        if p["nruns"] < 16:
+            assert n == min(64, len(varying))
+        # runs least significant first: each run lies below the next in significance order
+        order = {wb: i for i, wb in enumerate(varying)}
+        for r in range(p["nruns"] - 1):
+            assert order[(p["word"][r], p["shift"][r])] > order[(p["word"][r + 1], p["shift"][r + 1] + p["len"][r + 1] - 1)]
+        words_with_runs = [p["word"][r] for r in range(p["nruns"])]
+        assert p["simple"] == (len(set(words_with_runs)) == len(words_with_runs))
+        if p["simple"]:
+            for r in range(p["nruns"]):
+                assert (p["wshift"][p["word"][r]], p["wlen"][p["word"][r]]) == (p["shift"][r], p["len"][r])
+        # order preservation on random keys with these masks
+        for _ in range(20):
+            a = [(kor[w] & ~knand[w]) | (rnd.getrandbits(32) & kor[w] & knand[w]) for w in range(K)]
+            b = [(kor[w] & ~knand[w]) | (rnd.getrandbits(32) & kor[w] & knand[w]) for w in range(K)]
+
+            def prefix(k):
+                return [(k[w] >> bit) & 1 for (w, bit) in varying[:n]]
+
+            if prefix(a) != prefix(b):
+                assert (prefix(a) < prefix(b)) == (a < b)
