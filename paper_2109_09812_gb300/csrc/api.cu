@@ -74,7 +74,7 @@ static LaunchCfg& launch_cfg_locked(int S) {
   c.occ_sort_pipe = occupancy_sort_pipe(S);
   c.occ_tiles = occupancy_tiles(S);
   if (c.occ_sort_pipe < 1 && c.sort_kernel == kSortPipe) c.sort_kernel = kSortRegs;  // too little shared memory
-  // 16- and 20-byte keys rank faster without the ballots of constant digit bits (register pressure
+  // 16- to 32-byte keys rank faster without the ballots of constant digit bits (register pressure
   // of the wider items); 4- to 12-byte keys with all eight (measured on GB300)
   if (S >= 16) c.rank_mode = kRankBallotVary;
   // Defaults are the variants measured fastest on GB300; a tuning cache (written by the
