@@ -5,8 +5,8 @@
 //   oldToNew[orgID[j]] = newIdx[j]                           (Section 2.4: perm composed with newIdx)
 //   newVtx[newIdx[j]] = key[j] for every head j              (Section 2.3)
 //   *out_nVtx = total number of heads                        (Section 2.3, newN)
-// The prefix sum is a decoupled look-back scan over tiles of 2048 items (256 threads x 8; four
-// CTAs per SM, so that the others keep working while one waits in its look-back);
+// The prefix sum is a decoupled look-back scan over tiles of 2048 items (256 threads x 8; up to
+// four CTAs per SM, so that the others keep working while one waits in its look-back);
 // neither nodup nor newIdx is materialised.  If the radix sort packed the keys (their varying
 // bits only), run heads are found on the packed keys (equal exactly when the keys are) and only
 // the keys written out are restored; a mesh id (batched mode) is read from its packed bits.
@@ -22,11 +22,11 @@ constexpr int kHeadWarps = kHeadThreads / 32;
 // written to out_vtx, and the first item of each mesh records that mesh's first output vertex.
 // kMayPack: the sort may have packed the keys (the call allows packing); else they are never packed.
 //
-// SV > 0 (prefix sort, S = 12, key word 0 zero): the items carry the 64 most significant varying bits of SV-byte
-// vertex keys; run heads are where that prefix changes, and each head writes its whole key, read
-// from the vertex array by its old index (loaded before the scan, so that the look-back wait
-// covers the latency of these random reads).  (k_prefix_check then confirms that equal prefixes
-// meant equal keys.)
+// SV > 0 (prefix sort; S = 12 with key word 0 zero): the items carry the 64 most significant
+// varying bits of SV-byte vertex keys; run heads are where that prefix changes, and each head
+// writes its whole key, read from the vertex array by its old index (loaded before the scan, so
+// that the look-back wait covers the latency of these random reads).  k_prefix_check then
+// confirms that equal prefixes meant equal keys.
 template <int S, bool kSeg, bool kMayPack, int SV = 0>
 __global__ void __launch_bounds__(kHeadThreads, (S >= 16 || SV > 0) ? 2 : 4)
     k_head_scan(WsPtrs ws, void* __restrict__ out_vtx, int64_t* __restrict__ out_nVtx, uint32_t nVtx, SegArgs seg,
