@@ -282,6 +282,15 @@ int reindex_debug_arena_check(uint64_t seed, int ops, size_t size);
  * and returns the number of prefix bits, or -1 for bad arguments.  Needs no GPU. */
 int reindex_debug_prefix_pack(const uint32_t* kor, const uint32_t* knand, int K, void* out, int outBytes);
 
+/* Host-only test hook: the key packing arithmetic of the kernels (the same inline functions),
+ * applied on the host to n keys of K (1..8) words, row-major in `keys`, with a packing
+ * description in the layout written by reindex_debug_prefix_pack.  mode 0: pack (general runs),
+ * 1: pack (at most one run per word), 2: unpack packed keys, filling the constant bits from
+ * kconst[K]; all three write n*K words to `out`.  mode 3: word 0 of each unpacked key (n words),
+ * from kconst[0] and the runs of word 0.  Returns 0, or -1 for bad arguments.  Needs no GPU. */
+int reindex_debug_pack_keys(const void* pack, int packBytes, int K, const uint32_t* kconst,
+                            const uint32_t* keys, int64_t n, int mode, uint32_t* out);
+
 /* Synchronises `stream`, then returns and clears this device's sticky device-side error: the
  * first INDEX_RANGE or TIMEOUT raised by any call on the current device since the last
  * reindex_stream_status() (REINDEX_OK if none).  A CUDA error from the synchronisation is

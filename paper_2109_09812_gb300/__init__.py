@@ -42,7 +42,7 @@ EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "
             "reindex_server_drain", "reindex_server_get_stats", "reindex_server_destroy", "reindex_debug_arena_check",
             "reindex_merge_workspace_size", "reindex_merge_meshes", "reindex_submesh_workspace_size",
             "reindex_submesh", "reindex_autotune", "reindex_tuning_get", "reindex_tuning_set",
-            "reindex_debug_stall_tile", "reindex_debug_prefix_pack"]
+            "reindex_debug_stall_tile", "reindex_debug_prefix_pack", "reindex_debug_pack_keys"]
 
 _lock = threading.Lock()
 _lib = None
@@ -149,6 +149,8 @@ def lib() -> ctypes.CDLL:
             L.reindex_debug_arena_check.restype = ci
             L.reindex_debug_prefix_pack.argtypes = [vp, vp, ci, vp, ci]
             L.reindex_debug_prefix_pack.restype = ci
+            L.reindex_debug_pack_keys.argtypes = [vp, ci, ci, vp, vp, i64, ci, vp]
+            L.reindex_debug_pack_keys.restype = ci
             _lib = L
     return _lib
 
@@ -496,7 +498,23 @@ def debug_prefix_pack(kor, knand) -> dict:
     n = b[2]
     return dict(on=b[0], nbits=b[1], nruns=n, word=list(b[3:3 + n]), shift=list(b[19:19 + n]),
                 len=list(b[35:35 + n]), pos=list(b[51:51 + n]), simple=b[67], wshift=list(b[68:76]),
-                wlen=list(b[76:84]), returned=nbits)
+                wlen=list(b[76:84]), returned=nbits, raw=b)
+
+
+def debug_pack_keys(pack: bytes, keys, mode: int, kconst=None):
+    """Host-only: the kernels' key packing applied to keys (n, K) uint32 (test hook); mode 0/1
+    pack (general / one run per word), 2 unpacks with kconst, 3 returns word 0 of the unpacked keys."""
+    import numpy as np
+
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    n, K = keys.shape
+    out = np.zeros(n if mode == 3 else (n, K), dtype=np.uint32)
+    kc = np.ascontiguousarray(kconst if kconst is not None else np.zeros(K), dtype=np.uint32)
+    buf = ctypes.create_string_buffer(bytes(pack), len(pack))
+    rc = lib().reindex_debug_pack_keys(buf, len(pack), K, kc.ctypes.data, keys.ctypes.data, n, mode, out.ctypes.data)
+    if rc:
+        raise ValueError("bad arguments")
+    return out
 
 
 def debug_arena_check(seed: int, ops: int, size: int) -> int:

@@ -512,7 +512,7 @@ __device__ __forceinline__ uint32_t key_digit(const uint32_t (&k)[K], int d) {
 // Word `w` (run time) of a key held in registers, and OR into it (select chains: a run-time index
 // into a register array would move the array to local memory).
 template <int K>
-__device__ __forceinline__ uint32_t key_word(const uint32_t (&k)[K], int w) {
+__host__ __device__ __forceinline__ uint32_t key_word(const uint32_t (&k)[K], int w) {
   uint32_t x = k[0];
 #pragma unroll
   for (int q = 1; q < K; ++q)
@@ -520,7 +520,7 @@ __device__ __forceinline__ uint32_t key_word(const uint32_t (&k)[K], int w) {
   return x;
 }
 template <int K>
-__device__ __forceinline__ void key_word_or(uint32_t (&k)[K], int w, uint32_t v) {
+__host__ __device__ __forceinline__ void key_word_or(uint32_t (&k)[K], int w, uint32_t v) {
 #pragma unroll
   for (int q = 0; q < K; ++q)
     if (q == w) k[q] |= v;
@@ -528,7 +528,7 @@ __device__ __forceinline__ void key_word_or(uint32_t (&k)[K], int w, uint32_t v)
 
 // Packs the varying bits of a key into its low bits (KeyPack runs, least significant first).
 template <int K>
-__device__ __forceinline__ void pack_key(uint32_t (&k)[K], const KeyPack& P) {
+__host__ __device__ __forceinline__ void pack_key(uint32_t (&k)[K], const KeyPack& P) {
   uint32_t out[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) out[q] = 0;
@@ -555,7 +555,7 @@ __device__ __forceinline__ void pack_key(uint32_t (&k)[K], const KeyPack& P) {
 // pack_key for keys with at most one run of varying bits per word (KeyPack::simple): the words
 // are visited in a fixed order with their run's shift and length, no per-run loop.
 template <int K>
-__device__ __forceinline__ void pack_key_simple(uint32_t (&k)[K], const KeyPack& P) {
+__host__ __device__ __forceinline__ void pack_key_simple(uint32_t (&k)[K], const KeyPack& P) {
   uint32_t out[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) out[q] = 0;
@@ -582,7 +582,7 @@ __device__ __forceinline__ void pack_key_simple(uint32_t (&k)[K], const KeyPack&
 
 // Bits [pos, pos + len) of a packed key (len <= 32).
 template <int K>
-__device__ __forceinline__ uint32_t packed_bits(const uint32_t (&k)[K], uint32_t pos, uint32_t len) {
+__host__ __device__ __forceinline__ uint32_t packed_bits(const uint32_t (&k)[K], uint32_t pos, uint32_t len) {
   const int cw = K - 1 - (int)(pos >> 5), cb = pos & 31;
   uint32_t v = key_word<K>(k, cw) >> cb;
   if (cb + len > 32) v |= key_word<K>(k, cw - 1) << (32 - cb);
@@ -591,7 +591,7 @@ __device__ __forceinline__ uint32_t packed_bits(const uint32_t (&k)[K], uint32_t
 
 // Inverse of pack_key: every run back in place, the constant bits from kconst.
 template <int K>
-__device__ __forceinline__ void unpack_key(uint32_t (&k)[K], const KeyPack& P, const uint32_t* kconst) {
+__host__ __device__ __forceinline__ void unpack_key(uint32_t (&k)[K], const KeyPack& P, const uint32_t* kconst) {
   uint32_t out[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) out[q] = kconst[q];
@@ -603,7 +603,7 @@ __device__ __forceinline__ void unpack_key(uint32_t (&k)[K], const KeyPack& P, c
 
 // Key word 0 (the mesh id in batched mode) of a packed key.
 template <int K>
-__device__ __forceinline__ uint32_t unpacked_word0(const uint32_t (&k)[K], const KeyPack& P, uint32_t kconst0) {
+__host__ __device__ __forceinline__ uint32_t unpacked_word0(const uint32_t (&k)[K], const KeyPack& P, uint32_t kconst0) {
   uint32_t v = kconst0;
   for (int r = 0; r < P.nruns; ++r)
     if (P.word[r] == 0) v |= packed_bits<K>(k, P.pos[r], P.len[r]) << P.shift[r];

@@ -431,3 +431,50 @@ extern "C" int reindex_debug_prefix_pack(const uint32_t* kor, const uint32_t* kn
   std::memcpy(out, &kp, sizeof(KeyPack));
   return nbits;
 }
+
+// Host test hook (include/reindex.h): the key packing arithmetic of the compaction and the head
+// scan (the same inline functions the kernels use) applied to n keys of K words on the host.
+namespace {
+template <int K>
+void debug_pack_k(const reindex::KeyPack& P, const uint32_t* kconst, const uint32_t* keys, int64_t n, int mode,
+                  uint32_t* out) {
+  using namespace reindex;
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t k[K];
+    for (int q = 0; q < K; ++q) k[q] = keys[i * K + q];
+    if (mode == 3) {
+      out[i] = unpacked_word0<K>(k, P, kconst[0]);
+      continue;
+    }
+    if (mode == 0)
+      pack_key<K>(k, P);
+    else if (mode == 1)
+      pack_key_simple<K>(k, P);
+    else
+      unpack_key<K>(k, P, kconst);
+    for (int q = 0; q < K; ++q) out[i * K + q] = k[q];
+  }
+}
+}  // namespace
+
+extern "C" int reindex_debug_pack_keys(const void* pack, int packBytes, int K, const uint32_t* kconst,
+                                       const uint32_t* keys, int64_t n, int mode, uint32_t* out) {
+  using namespace reindex;
+  if (!pack || packBytes < (int)sizeof(KeyPack) || K < 1 || K > kMaxDigits / 4 || n < 0 || mode < 0 || mode > 3 ||
+      (n > 0 && (!keys || !out)) || ((mode >= 2) && !kconst))
+    return -1;
+  KeyPack P;
+  std::memcpy(&P, pack, sizeof(KeyPack));
+  if (P.nruns > kMaxPackRuns) return -1;
+  switch (K) {
+    case 1: debug_pack_k<1>(P, kconst, keys, n, mode, out); break;
+    case 2: debug_pack_k<2>(P, kconst, keys, n, mode, out); break;
+    case 3: debug_pack_k<3>(P, kconst, keys, n, mode, out); break;
+    case 4: debug_pack_k<4>(P, kconst, keys, n, mode, out); break;
+    case 5: debug_pack_k<5>(P, kconst, keys, n, mode, out); break;
+    case 6: debug_pack_k<6>(P, kconst, keys, n, mode, out); break;
+    case 7: debug_pack_k<7>(P, kconst, keys, n, mode, out); break;
+    default: debug_pack_k<8>(P, kconst, keys, n, mode, out); break;
+  }
+  return 0;
+}

@@ -151,3 +151,121 @@ def test_prefix_sort_bit_selection(L, K):
 
             if prefix(a) != prefix(b):
                 assert (prefix(a) < prefix(b)) == (a < b)
+
+
+def _masks_and_keys(rnd, K, n, max_runs=16):
+    """Per-word varying-bit masks (at most max_runs runs in all), constant bits, and n keys."""
+    while True:
+        masks = []
+        for _ in range(K):
+            style = rnd.randrange(4)
+            if style == 0:
+                m = 0
+            elif style == 1:
+                m = 0xFFFFFFFF
+            elif style == 2:
+                m = 0
+                for _ in range(rnd.randrange(1, 4)):
+                    lo = rnd.randrange(32)
+                    hi = rnd.randrange(lo, 32)
+                    m |= ((1 << (hi - lo + 1)) - 1) << lo
+            else:
+                m = rnd.getrandbits(32) & rnd.getrandbits(32)
+            masks.append(m)
+        runs = [(w, lo, ln) for w in range(K - 1, -1, -1) for (lo, ln) in _runs_of(masks[w])]
+        if len(runs) <= max_runs:
+            break
+    const = [rnd.getrandbits(32) & ~m & 0xFFFFFFFF for m in masks]
+    pool = [[const[w] | (rnd.getrandbits(32) & masks[w]) for w in range(K)] for _ in range(max(1, n // 3))]
+    keys = np.array([rnd.choice(pool) for _ in range(n)], dtype=np.uint32)  # with repeats
+    return masks, const, runs, keys
+
+
+def _runs_of(m):
+    out, b = [], 0
+    while b < 32:
+        if not (m >> b) & 1:
+            b += 1
+            continue
+        e = b
+        while e < 32 and (m >> e) & 1:
+            e += 1
+        out.append((b, e - b))
+        b = e
+    return out
+
+
+def _keypack_bytes(runs, K):
+    """The 88-byte packing description (layout of reindex_debug_prefix_pack) for runs listed least
+    significant first as (word, lowest bit, length)."""
+    b = bytearray(88)
+    b[0] = 1
+    b[1] = sum(r[2] for r in runs) & 0xFF
+    b[2] = len(runs)
+    pos = 0
+    per_word = {}
+    for i, (w, lo, ln) in enumerate(runs):
+        b[3 + i], b[19 + i], b[35 + i], b[51 + i] = w, lo, ln, pos
+        pos += ln
+        per_word.setdefault(w, []).append((lo, ln))
+    b[67] = int(all(len(v) == 1 for v in per_word.values()))
+    for w, v in per_word.items():
+        if len(v) == 1:
+            b[68 + w], b[76 + w] = v[0]
+    return bytes(b)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 5, 6, 8])
+def test_key_packing_roundtrip_and_order(L, K):
+    """The kernels' key packing, run on the host: packing keeps only the varying bits and keeps
+    their order, so packed keys compare exactly like the keys (equal iff equal); unpacking with
+    the constant bits restores every key; the one-run-per-word variant agrees with the general one;
+    word 0 (a batched call's mesh id) is read back from the packed bits alone."""
+    import random
+
+    rnd = random.Random(7 + K)
+    for trial in range(60):
+        masks, const, runs, keys = _masks_and_keys(rnd, K, 64)
+        pack = _keypack_bytes(runs, K)
+        nbits = sum(r[2] for r in runs)
+        packed = rx.debug_pack_keys(pack, keys, 0)
+        if pack[67]:
+            np.testing.assert_array_equal(rx.debug_pack_keys(pack, keys, 1), packed)
+        np.testing.assert_array_equal(rx.debug_pack_keys(pack, packed, 2, const), keys)
+        np.testing.assert_array_equal(rx.debug_pack_keys(pack, packed, 3, const), keys[:, 0])
+        for q in range(K):  # nothing above the packed bits
+            lo_bit = 32 * (K - 1 - q)
+            if lo_bit >= nbits:
+                assert not packed[:, q].any()
+            elif nbits - lo_bit < 32:
+                assert not (packed[:, q] >> np.uint32(nbits - lo_bit)).any()
+        kt = [tuple(int(x) for x in r) for r in keys]
+        pt = [tuple(int(x) for x in r) for r in packed]
+        for i in range(0, 64, 2):
+            a, b = i, (i * 7 + 3) % 64
+            assert (kt[a] < kt[b]) == (pt[a] < pt[b]) and (kt[a] == kt[b]) == (pt[a] == pt[b])
+
+
+@pytest.mark.parametrize("K", [3, 4, 6, 8])
+def test_prefix_packing_of_keys(L, K):
+    """The prefix sort's packing (the chosen bits, then the kernels' packing): the prefix sits in
+    the low two words, equal keys get equal prefixes, and keys with different prefixes compare
+    like their prefixes."""
+    import random
+
+    rnd = random.Random(70 + K)
+    for trial in range(60):
+        masks, const, runs, keys = _masks_and_keys(rnd, K, 64, max_runs=64)
+        kor = np.array([m | c for m, c in zip(masks, const)], np.uint32)
+        knand = np.array([m | (~c & ~m & 0xFFFFFFFF) for m, c in zip(masks, const)], np.uint32)
+        p = rx.debug_prefix_pack(kor, knand)
+        packed = rx.debug_pack_keys(p["raw"], keys, 1 if p["simple"] else 0)
+        assert not packed[:, : K - 2].any()
+        kt = [tuple(int(x) for x in r) for r in keys]
+        pre = [tuple(int(x) for x in r[K - 2:]) for r in packed]
+        for a in range(64):
+            b = (a * 5 + 1) % 64
+            if kt[a] == kt[b]:
+                assert pre[a] == pre[b]
+            elif pre[a] != pre[b]:
+                assert (pre[a] < pre[b]) == (kt[a] < kt[b])
