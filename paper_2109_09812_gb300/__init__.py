@@ -10,6 +10,21 @@ Build it with ``python -m paper_2109_09812_gb300.build``.
 
 Method: Wald, "GPGPU-Parallel Re-indexing of Triangle Meshes with Duplicate-Vertex and
 Unused-Vertex Removal" (arXiv 2109.09812), Sections 2.1-2.4.
+
+Usage::
+
+    import torch
+    import paper_2109_09812_gb300 as rx
+
+    vtx = torch.rand(n, 3, device="cuda")                          # one vertex per row
+    idx = torch.randint(0, n, (m, 3), dtype=torch.int32, device="cuda")
+    new_vtx, new_idx = rx.reindex(vtx, idx)                        # reads the unique count once
+    out_vtx, out_n, out_idx = rx.reindex_mesh(vtx, idx)            # fully asynchronous
+    ws = torch.empty(rx.reindex_workspace_size(n, 12, m, 3), dtype=torch.uint8, device="cuda")
+    rx.reindex_mesh_ws(vtx, idx, ws, out_vtx, out_n, out_idx)      # no allocation: graph-capturable
+
+Unique vertices come out in ascending raw-bit order, so the result does not depend on the
+input's vertex order or on the GPU; new_idx[j] points at the unique copy of vtx[idx[j]].
 """
 from __future__ import annotations
 
@@ -198,8 +213,8 @@ def _ptr(t):
 def reindex_mesh(vtx, idx, out_vtx=None, out_nVtx=None, out_idx=None, stream=None):
     """Asynchronously re-index one mesh on the GPU (workspace from the stream-ordered pool).
 
-    vtx: CUDA tensor (nVtx, ...) with one vertex of 4/8/12/16 bytes per row (any dtype; the
-    raw bits are the key).  idx: CUDA int32 tensor (nElem, k).  Returns (out_vtx, out_nVtx,
+    vtx: CUDA tensor (nVtx, ...) with one vertex of 4, 8, 12, 16, 20, 24 or 32 bytes per row
+    (any dtype; the raw bits are the key).  idx: CUDA int32 tensor (nElem, k).  Returns (out_vtx, out_nVtx,
     out_idx): out_vtx has min(nVtx, nElem*k) rows of which the first D = out_nVtx.item() are
     valid; out_nVtx is a 1-element int64 CUDA tensor (negative status on a device error)."""
     torch = _torch()
