@@ -139,14 +139,20 @@ reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int vtxStri
  *   still the caller's device buffers).
  *   Limit: nVtx <= REINDEX_NOALLOC_MAX_VTX (262,144 vertices, any supported stride and any
  *   number of elements); a larger mesh returns REINDEX_ERR_UNSUPPORTED and nothing is launched.
- *   Scratch: one 20 MiB array of device memory inside the library, reserved on every device
- *   that loads the library and held until the process exits.  The first call on a device looks
- *   up that array's device address (cudaGetSymbolAddress, with the device current) and caches
- *   it; make that first call before any stream capture on the device.
+ *   Scratch: one array of REINDEX_NOALLOC_SCRATCH_BYTES (20 MiB) of device memory inside the
+ *   library, held on a device from the time the CUDA runtime loads the library's device code
+ *   there until the process exits.  With lazy module loading (the CUDA default) that happens at
+ *   the FIRST call on the device: that call reserves the 20 MiB (it can fail with
+ *   REINDEX_ERR_CUDA if the device is full, and may synchronise the device) and looks up the
+ *   array's device address (cudaGetSymbolAddress, with the device current), which later calls
+ *   reuse.  So make one warm-up call per device -- nElem == 0 is enough, it launches one tiny
+ *   kernel -- before committing the rest of the device-memory budget and before any stream
+ *   capture on that device.
  *   All calls share the array.  Each call zeroes the parts that must start at zero, but two
  *   calls whose work overlaps on the GPU (e.g. on two streams with no ordering between them)
  *   race on it and corrupt each other's results: order them on one stream or with events.
  *   Keep per-launch timing (reindex_profile_enable) off: that facility allocates for itself. */
+#define REINDEX_NOALLOC_SCRATCH_BYTES (20u << 20)
 #define REINDEX_NOALLOC_MAX_VTX 262144
 reindex_status reindex_mesh_noalloc(const void* vtx, int64_t nVtx, int vtxStrideBytes,
                                     const int32_t* idx, int64_t nElem, int idxPerElem,

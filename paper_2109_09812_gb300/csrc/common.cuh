@@ -124,7 +124,7 @@ struct Plan {                // written by the sort-plan kernel
   uint32_t base[kMaxDigits][kRadix];  // exclusive prefix of the digit histogram
 };
 
-inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Item buffers of S-byte keys: structure of arrays (a key plane, then an id plane) for S = 8, 16,
 // 24 and 32; array of structures {key, id} for S = 4, 12 and 20.
@@ -140,7 +140,7 @@ struct WsLayout {
          total = 0;
   size_t off_ctrl_pre = 0;  // prefix sort: its control block
 
-  void compute(int64_t n, int s, int64_t m) {
+  constexpr void compute(int64_t n, int s, int64_t m) {
     S = s; K = s / 4; P = s; nVtx = n; M = m;
     Umax = n < m ? n : m;
     tilesV = (n + kCompactTile - 1) / kCompactTile;
@@ -172,6 +172,13 @@ struct WsLayout {
     total = o;
   }
 };
+
+// Workspace bytes of one single-mesh call (usable in constant expressions).
+constexpr size_t ws_bytes(int64_t n, int s, int64_t m) {
+  WsLayout L{};
+  L.compute(n, s, m);
+  return L.total;
+}
 
 // Device views of the workspace, passed by value to the kernels.
 struct WsPtrs {

@@ -1,5 +1,5 @@
-// reindex_mesh_noalloc: re-index one small mesh with scratch memory that the library reserved
-// when it was loaded, so that the call itself allocates nothing.
+// reindex_mesh_noalloc: re-index one small mesh with scratch memory that lives inside the library,
+// so that the call itself allocates nothing.
 //
 // Who needs this: callers that cannot (or must not) allocate device memory at call time -- a
 // host program that committed its whole device-memory budget up front and accounts for every
@@ -7,19 +7,33 @@
 // its other streams, or a plugin whose host application forbids allocations behind its back.
 // They pass inputs and outputs as usual; the scratch is the static array below.
 //
-// The array is a file-scope __device__ variable, so every device that loads this library holds
-// it (20 MiB) until the process exits.  Host code only sees a stand-in for its name; the real
-// device address is looked up once per device with cudaGetSymbolAddress (with that device
-// current) and cached.  Every call shares the array: the pipeline's first kernel zeroes the
-// parts that must start at zero, and calls whose work overlaps on the GPU (for example two
-// calls on two streams without ordering between them) race on it.
+// The array is a file-scope __device__ variable (REINDEX_NOALLOC_SCRATCH_BYTES), held on a device
+// from the moment the CUDA runtime loads this file's device code there until the process exits.
+// With lazy module loading (the CUDA default) that moment is the first call on the device, whose
+// cudaGetSymbolAddress loads the code: that first call reserves the 20 MiB (and may synchronise).
+// Host code only sees a stand-in for the array's name; the real device address is looked up once
+// per device (with that device current) and cached.  Every call shares the array: the pipeline's
+// first kernel zeroes the parts that must start at zero, and calls whose work overlaps on the GPU
+// (for example two calls on two streams without ordering between them) race on it.
 #include <mutex>
 
+#include "internal.h"
 #include "reindex.h"
 
 namespace {
 
-constexpr size_t kScratchBytes = 20u << 20;  // 20 MiB, enough (for every stride) for nVtx <= REINDEX_NOALLOC_MAX_VTX
+constexpr size_t kScratchBytes = REINDEX_NOALLOC_SCRATCH_BYTES;
+
+// The scratch holds the workspace of the largest mesh the entry point accepts, for every stride
+// (the workspace grows with min(nVtx, nElem * idxPerElem), so nElem * idxPerElem = nVtx is the
+// largest case).  A change of the workspace layout that breaks this fails to compile.
+constexpr bool fits_every_stride() {
+  const int strides[] = {4, 8, 12, 16, 20, 24, 32};
+  for (int S : strides)
+    if (reindex::ws_bytes(REINDEX_NOALLOC_MAX_VTX, S, REINDEX_NOALLOC_MAX_VTX) > kScratchBytes) return false;
+  return true;
+}
+static_assert(fits_every_stride(), "the no-allocation scratch must hold the workspace of the largest accepted mesh");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 

@@ -269,3 +269,17 @@ def test_prefix_packing_of_keys(L, K):
                 assert pre[a] == pre[b]
             elif pre[a] != pre[b]:
                 assert (pre[a] < pre[b]) == (kt[a] < kt[b])
+
+
+def test_noalloc_scratch_holds_the_largest_accepted_mesh(L):
+    """reindex_mesh_noalloc accepts every mesh of up to REINDEX_NOALLOC_MAX_VTX vertices, whatever
+    its stride and element count; its fixed scratch must hold the workspace of each of them."""
+    src = open(HEADER).read()
+    max_vtx = int(re.search(r"#define REINDEX_NOALLOC_MAX_VTX (\d+)", src).group(1))
+    m = re.search(r"#define REINDEX_NOALLOC_SCRATCH_BYTES \((\d+)u << (\d+)\)", src)
+    scratch = int(m.group(1)) << int(m.group(2))
+    for S in (4, 8, 12, 16, 20, 24, 32):
+        for k in (1, 3, 4):
+            for n_elem in (1, max_vtx // k, max_vtx, 10 * max_vtx):
+                b = rx.reindex_workspace_size(max_vtx, S, n_elem, k)
+                assert 0 < b <= scratch, (S, k, n_elem, b, scratch)

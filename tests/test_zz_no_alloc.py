@@ -2,21 +2,29 @@
 
 Such callers (a program that reserved its whole device-memory budget up front, a real-time loop
 in which cudaMalloc/cudaFree would synchronise the device, a plugin whose host forbids hidden
-allocations) get the same result as reindex_mesh from scratch memory the library reserved when
-it was loaded.  This test calls the entry point through the C ABI twice in a row, on two
-different meshes, and checks each result bit for bit against reindex_mesh on the same input;
-the second call would expose anything the first call left behind in the shared scratch array.
-It also checks that meshes over the stated limit are refused.
+allocations) get the same result as reindex_mesh from a fixed scratch array inside the library.
+These tests call the entry point through the C ABI several times in a row and check every result
+bit for bit against the serial oracle and against reindex_mesh on the same input; a later call
+would expose anything an earlier call left behind in the shared scratch array (a small mesh, then
+a larger one of the same stride, then the small one again).  They also check that a call, once
+the library is warm on the device, allocates nothing (the device's default memory pool and the
+device's free memory are unchanged), and that meshes over the stated limit are refused.
 
 The file name makes pytest collect it last.
 """
 import ctypes
+import glob
+import os
 
 import numpy as np
 import pytest
 
+import oracle
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+MAX_VTX = 262_144  # REINDEX_NOALLOC_MAX_VTX
 
 
 @pytest.fixture(scope="module")
@@ -41,15 +49,20 @@ def _mesh(seed, n_vtx, n_elem, k, words):
     pool = rng.integers(0, 2**32, size=(n_vtx // 3 + 1, words), dtype=np.uint64).astype(np.uint32)
     vtx = pool[rng.integers(0, pool.shape[0], size=n_vtx)]  # many exact duplicates
     idx = rng.integers(0, n_vtx, size=(n_elem, k)).astype(np.int32)  # some vertices unused
-    return (torch.from_numpy(vtx.view(np.int32)).cuda(), torch.from_numpy(idx).cuda())
+    return vtx, idx
 
 
-def _noalloc(rx, v, i):
+def _dev(vtx, idx):
+    return torch.from_numpy(vtx.view(np.int32)).cuda(), torch.from_numpy(idx).cuda()
+
+
+def _noalloc(rx, v, i, out=None):
     S = v.shape[1] * 4
     cap = min(v.shape[0], i.numel())
-    out_v = torch.full((cap, v.shape[1]), -1, dtype=torch.int32, device="cuda")
-    out_n = torch.full((1,), -99, dtype=torch.int64, device="cuda")
-    out_i = torch.full_like(i, -1)
+    if out is None:
+        out = (torch.full((max(cap, 1), v.shape[1]), -1, dtype=torch.int32, device="cuda"),
+               torch.full((1,), -99, dtype=torch.int64, device="cuda"), torch.full_like(i, -1))
+    out_v, out_n, out_i = out
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = rx.lib().reindex_mesh_noalloc(ctypes.c_void_p(v.data_ptr()), v.shape[0], S, ctypes.c_void_p(i.data_ptr()),
                                        i.shape[0], i.shape[1], ctypes.c_void_p(out_v.data_ptr()),
@@ -57,34 +70,91 @@ def _noalloc(rx, v, i):
     return rc, out_v, out_n, out_i
 
 
-def test_noalloc_matches_reindex_mesh_twice_in_a_row(rx):
-    meshes = [_mesh(1, 200_000, 150_000, 3, 3), _mesh(2, 90_001, 40_000, 4, 4)]
-    for v, i in meshes:  # two calls in a row, different strides and sizes
-        rc, nv, nn, ni = _noalloc(rx, v, i)
-        assert rc == rx.REINDEX_OK
-        rv, rn, ri = rx.reindex_mesh(v, i)
-        torch.cuda.synchronize()
-        D = int(rn.item())
-        assert D > 0 and int(nn.item()) == D
-        assert torch.equal(nv[:D], rv[:D])
-        assert torch.equal(ni, ri)
+def _check(rx, vtx, idx):
+    """One no-allocation call, compared with the oracle and with reindex_mesh, element by element."""
+    v, i = _dev(vtx, idx)
+    rc, nv, nn, ni = _noalloc(rx, v, i)
+    assert rc == rx.REINDEX_OK
+    torch.cuda.synchronize()
+    D = int(nn.item())
+    ov, oi = oracle.reindex_sort(vtx, idx)
+    assert D == ov.shape[0] > 0
+    np.testing.assert_array_equal(nv[:D].cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(ni.cpu().numpy().reshape(-1), oi)
+    rv, rn, ri = rx.reindex_mesh(v, i)
+    torch.cuda.synchronize()
+    assert int(rn.item()) == D
+    assert torch.equal(nv[:D], rv[:D]) and torch.equal(ni, ri)
+
+
+def test_noalloc_matches_oracle_on_calls_in_a_row(rx):
+    small = _mesh(1, 30_001, 12_000, 3, 3)
+    large = _mesh(2, 200_000, 150_000, 3, 3)
+    other = _mesh(3, 90_001, 40_000, 4, 4)
+    for vtx, idx in (small, large, small, other, small):  # same stride small -> large -> small, then another
+        _check(rx, vtx, idx)
 
 
 @pytest.mark.parametrize("words", [6, 8])
 def test_noalloc_wide_vertices_at_the_limit(rx, words):
     """24- and 32-byte vertices at the largest size the static scratch holds."""
-    v, i = _mesh(3, 262_144, 87_381, 3, words)
-    rc, nv, nn, ni = _noalloc(rx, v, i)
-    assert rc == rx.REINDEX_OK
-    rv, rn, ri = rx.reindex_mesh(v, i)
+    _check(rx, *_mesh(4, MAX_VTX, 87_381, 3, words))
+
+
+def _cudart():
+    """The CUDA runtime library as a separate handle, for the memory-pool queries."""
+    cands = ["libcudart.so", "libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so"]
+    cands += sorted(glob.glob("/usr/local/cuda*/lib64/libcudart.so*"))
+    cands += sorted(glob.glob(os.path.join(os.path.dirname(torch.__file__), "lib", "libcudart*.so*")))
+    for c in cands:
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    pytest.fail("no CUDA runtime library found for the memory-pool queries")
+
+
+def test_noalloc_call_allocates_nothing(rx):
+    """Once the library is warm on the device, a call changes neither the default memory pool's
+    usage (not even transiently: its high-water mark is reset first) nor the device's free memory."""
+    rt = _cudart()
+    dev = torch.cuda.current_device()
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    USED_CURRENT, USED_HIGH, RESERVED_CURRENT, RESERVED_HIGH = 7, 8, 5, 6
+
+    def attr(a):
+        v = ctypes.c_uint64(0)
+        assert rt.cudaMemPoolGetAttribute(pool, a, ctypes.byref(v)) == 0
+        return v.value
+
+    vtx, idx = _mesh(5, 150_000, 100_000, 3, 3)
+    v, i = _dev(vtx, idx)
+    out = (torch.empty((150_000, 3), dtype=torch.int32, device="cuda"), torch.empty(1, dtype=torch.int64,
+                                                                                      device="cuda"),
+           torch.empty_like(i))
+    assert _noalloc(rx, v, i, out)[0] == rx.REINDEX_OK  # warm: scratch resolved, kernels loaded
     torch.cuda.synchronize()
-    D = int(rn.item())
-    assert D > 0 and int(nn.item()) == D
-    assert torch.equal(nv[:D], rv[:D]) and torch.equal(ni, ri)
+    used0, reserved0 = attr(USED_CURRENT), attr(RESERVED_CURRENT)
+    zero = ctypes.c_uint64(0)
+    assert rt.cudaMemPoolSetAttribute(pool, USED_HIGH, ctypes.byref(zero)) == 0  # reset the high-water marks
+    assert rt.cudaMemPoolSetAttribute(pool, RESERVED_HIGH, ctypes.byref(zero)) == 0
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        assert _noalloc(rx, v, i, out)[0] == rx.REINDEX_OK
+    torch.cuda.synchronize()
+    assert attr(USED_HIGH) <= used0, "a no-allocation call took memory from the default pool"
+    assert attr(RESERVED_HIGH) <= reserved0 and attr(RESERVED_CURRENT) == reserved0
+    assert torch.cuda.mem_get_info()[0] == free0, "device free memory changed across no-allocation calls"
+    ov, oi = oracle.reindex_sort(vtx, idx)
+    D = int(out[1].item())
+    assert D == ov.shape[0]
+    np.testing.assert_array_equal(out[0][:D].cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(out[2].cpu().numpy().reshape(-1), oi)
 
 
 def test_noalloc_refuses_meshes_over_the_limit(rx):
-    n = 262_144 + 1
+    n = MAX_VTX + 1
     v = torch.zeros((n, 3), dtype=torch.int32, device="cuda")
     i = torch.zeros((10, 3), dtype=torch.int32, device="cuda")
     rc, *_ = _noalloc(rx, v, i)
