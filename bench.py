@@ -105,6 +105,8 @@ SORT_KERNEL_SOURCES = {
                  "paper_2109_09812_gb300/csrc/common.cuh"],
     "tile_scatter": ["paper_2109_09812_gb300/csrc/k_radix_tiles.cu", "paper_2109_09812_gb300/csrc/radix.cuh",
                      "paper_2109_09812_gb300/csrc/common.cuh"],
+    "chunk_scatter": ["paper_2109_09812_gb300/csrc/k_radix_chunk.cu", "paper_2109_09812_gb300/csrc/radix.cuh",
+                      "paper_2109_09812_gb300/csrc/tma.cuh", "paper_2109_09812_gb300/csrc/common.cuh"],
 }
 
 
@@ -288,58 +290,24 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def _gen_chunk(specs):
-    from paper_2109_09812_gb300 import synth
-
-    out = []
-    for (g, gy, uf, sd) in specs:
-        m = synth.heightfield_soup(g, gy, uf, sd)
-        out.append((m.vtx, m.idx))
-    return out
-
-
-def generate_batched(n_meshes, seed, workers):
-    """The batched workload, generated in a pool of spawned processes (before any CUDA use)."""
-    import multiprocessing as mp
-
-    from paper_2109_09812_gb300 import synth
-
-    specs = synth.batched_heightfield_sizes(n_meshes, seed=seed)
-    chunks = [specs[i::workers] for i in range(workers)]
-    with mp.get_context("spawn").Pool(workers) as pool:
-        parts = pool.map(_gen_chunk, chunks)
-    meshes = [None] * n_meshes
-    for w, part in enumerate(parts):
-        for j, m in enumerate(part):
-            meshes[w + j * workers] = m
-    return meshes
-
-
-def run_batched_bench(args, world, rank, local):
-    """Batched path: one CUDA-graph replay of reindex_meshes over all meshes vs one
-    reindex_mesh_ws call per mesh (same library, preallocated workspace, one stream)."""
+def batched_measure(rx, torch, dev, local, steps, warmup):
+    """Batched path on the 4096-mesh workload (generated on the device, bit-identical to the host
+    generator): one CUDA-graph replay of reindex_meshes over all meshes vs one reindex_mesh_ws
+    call per mesh (same library, preallocated workspace, one stream).  Returns a dict."""
     import ctypes
 
-    workers = max(1, min(16, os.cpu_count() or 1))
-    meshes = generate_batched(4096, 4, workers)
-    import torch
+    from paper_2109_09812_gb300 import synth
 
-    import paper_2109_09812_gb300 as rx
-    from paper_2109_09812_gb300 import build as rxbuild
-
-    rxbuild.build()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    nv = np.array([m[0].shape[0] for m in meshes], dtype=np.int64)
-    ne = np.array([m[1].shape[0] for m in meshes], dtype=np.int64)
+    specs = synth.batched_heightfield_sizes(4096, seed=4)
+    parts = [synth.heightfield_soup_gpu(g, gy, uf, sd, device=dev) for (g, gy, uf, sd) in specs]
+    nv = np.array([int(v.shape[0]) for v, _ in parts], dtype=np.int64)
+    ne = np.array([int(i.shape[0]) for _, i in parts], dtype=np.int64)
+    vtx = torch.cat([v for v, _ in parts]).view(torch.int32)
+    idx = torch.cat([i for _, i in parts])
+    del parts
     voff = np.concatenate([[0], np.cumsum(nv)]).astype(np.int64)
     eoff = np.concatenate([[0], np.cumsum(ne)]).astype(np.int64)
-    vtx_h = np.concatenate([m[0] for m in meshes])
-    idx_h = np.concatenate([m[1] for m in meshes])
-    del meshes
-    N, E, k, S = vtx_h.shape[0], idx_h.shape[0], 3, 12
-    vtx = torch.from_numpy(vtx_h.view(np.int32)).to(dev)
-    idx = torch.from_numpy(idx_h).to(dev)
+    N, E, k, S = int(voff[-1]), int(eoff[-1]), 3, 12
     vo, eo = torch.from_numpy(voff).to(dev), torch.from_numpy(eoff).to(dev)
     ws = torch.empty(rx.reindex_meshes_workspace_size(len(nv), N, S, E, k), dtype=torch.uint8, device=dev)
     out_v = torch.empty((min(N, E * k), 3), dtype=torch.int32, device=dev)
@@ -347,24 +315,24 @@ def run_batched_bench(args, world, rank, local):
     out_i = torch.empty_like(idx)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
-        rx.reindex_meshes(vtx, vo, idx, eo, ws, out_v, out_off, out_i)
+        rx.reindex_meshes(vtx, vo, idx, eo, ws, out_v, out_off, out_i, stream=stream)
     torch.cuda.synchronize(dev)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         rx.reindex_meshes(vtx, vo, idx, eo, ws, out_v, out_off, out_i, stream=stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):  # CUDAGraph.replay launches on the current stream
-        for _ in range(max(args.warmup, 1)):
+        for _ in range(max(warmup, 1)):
             graph.replay()
         torch.cuda.synchronize(dev)
         with ClockSampler(local) as clocks:
             torch.cuda.synchronize(dev)
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 graph.replay()
             e1.record(stream)
             torch.cuda.synchronize(dev)
-    ms_batched = e0.elapsed_time(e1) / args.steps
+    ms_batched = e0.elapsed_time(e1) / steps
     D = int(out_off[-1].item())
     if D < 0:
         raise SystemExit(f"batched run reported device error {-D}")
@@ -393,7 +361,7 @@ def run_batched_bench(args, world, rank, local):
 
     loop()
     torch.cuda.synchronize(dev)
-    loop_steps = max(2, min(args.steps, 5))
+    loop_steps = max(2, min(steps, 5))
     t0 = time.perf_counter()
     for _ in range(loop_steps):
         loop()
@@ -406,39 +374,49 @@ def run_batched_bench(args, world, rank, local):
     if same:
         ov, pv_h = out_v.cpu().numpy(), pv.cpu().numpy()
         same = all(np.array_equal(ov[offs[m]:offs[m + 1]], pv_h[voff[m]:voff[m] + counts[m]]) for m in range(len(nv)))
-    value = E / (ms_batched / 1e3)
+    return {"n_meshes": int(len(nv)), "n_vtx": N, "n_elem": E, "unique_out": D, "ms_graph_replay": ms_batched,
+            "value": E / (ms_batched / 1e3), "unit": UNIT,
+            "per_mesh_loop": {"value": E / (ms_loop / 1e3), "unit": UNIT, "ms_per_step": ms_loop,
+                              "launch_sequences": int(len(nv))},
+            "batched_vs_per_mesh": ms_loop / ms_batched, "identical_results": same,
+            "l2": f"inputs larger than L2 ({(N * S + E * k * 4) / 1e9:.2f} GB)", "clocks": clocks.summary()}
+
+
+def run_batched_bench(args, world, rank, local):
+    """Batched path: one CUDA-graph replay of reindex_meshes over all meshes vs one
+    reindex_mesh_ws call per mesh (same library, preallocated workspace, one stream)."""
+    import torch
+
+    import paper_2109_09812_gb300 as rx
+    from paper_2109_09812_gb300 import build as rxbuild
+
+    rxbuild.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    b = batched_measure(rx, torch, dev, local, args.steps, args.warmup)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload][0], "n_meshes": int(len(nv)), "n_vtx": int(N),
-                   "n_elem": int(E), "unique_out": D, "parallelism": f"replicas x{world}",
-                   "l2": f"inputs larger than L2 ({(N * S + E * k * 4) / 1e9:.2f} GB)"},
-        "per_mesh_loop": {"value": E / (ms_loop / 1e3), "unit": UNIT, "ms_per_step": ms_loop,
-                          "launch_sequences": int(len(nv))},
-        "batched_vs_per_mesh": ms_loop / ms_batched, "identical_results": same,
-        "clocks": clocks.summary(),
+        "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": b["ms_graph_replay"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (generated on the device)",
+        "config": {"workload": WORKLOADS[args.workload][0], "n_meshes": b["n_meshes"], "n_vtx": b["n_vtx"],
+                   "n_elem": b["n_elem"], "unique_out": b["unique_out"], "parallelism": f"replicas x{world}",
+                   "l2": b["l2"]},
+        "per_mesh_loop": b["per_mesh_loop"], "batched_vs_per_mesh": b["batched_vs_per_mesh"],
+        "identical_results": b["identical_results"], "clocks": b["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_serving_bench(args, world, rank, local):
-    """Serving: capacity from a closed-loop run, then open-loop Poisson arrivals at fractions of
-    that capacity; latency = completion - arrival (host monotonic clock, as the library's)."""
+def serving_measure(rx, torch, dev, local, n_req, loads, calib_n=2000):
+    """Serving: capacity from a closed-loop run of calib_n requests, then open-loop Poisson
+    arrivals of the first n_req requests at the given fractions of that capacity; latency =
+    completion - arrival (host monotonic clock, as the library's).  Returns a dict."""
     import collections
 
-    import torch
-
-    import paper_2109_09812_gb300 as rx
-    from paper_2109_09812_gb300 import build as rxbuild
     from paper_2109_09812_gb300 import synth
 
-    rxbuild.build()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    n_req = args.requests
-    specs = synth.serving_requests(n_req, seed=5)
+    specs = synth.serving_requests(max(n_req, calib_n), seed=5)
     elems = np.array([sp["n_elem"] for sp in specs], dtype=np.float64)
     gen_stream = torch.cuda.Stream(dev)
 
@@ -494,23 +472,38 @@ def run_serving_bench(args, world, rank, local):
                 "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(lat_ms.max()),
                 "batches": st["batches"], "failed": st["requests_failed"]}
 
-    calib_n = min(n_req, 2000)
     run(0, min(64, n_req))  # warm-up (kernels, allocator)
-    cap = run(0, calib_n)
+    cap = run(0, min(calib_n, len(specs)))
     capacity_eps = cap["elements_per_s"]
-    mean_elems = float(elems.mean())
-    loads = {}
-    for frac in [float(x) for x in args.loads.split(",")]:
-        loads[f"{frac:.2f}"] = run(frac * capacity_eps / mean_elems, n_req)
+    mean_elems = float(elems[:n_req].mean())
+    out = {}
+    for frac in loads:
+        out[f"{frac:.2f}"] = run(frac * capacity_eps / mean_elems, n_req)
+    return {"capacity_closed_loop": cap, "loads": out, "mean_elements": mean_elems}
+
+
+def run_serving_bench(args, world, rank, local):
+    """Serving: capacity from a closed-loop run, then open-loop Poisson arrivals at fractions of
+    that capacity (the 20,000-request stream by default)."""
+    import torch
+
+    import paper_2109_09812_gb300 as rx
+    from paper_2109_09812_gb300 import build as rxbuild
+
+    rxbuild.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    m = serving_measure(rx, torch, dev, local, args.requests, [float(x) for x in args.loads.split(",")])
+    loads = m["loads"]
     head = loads.get("0.70") or next(iter(loads.values()))
     line = {
         "metric": METRIC, "value": head["elements_per_s"], "unit": UNIT, "n_gpus": world, "steps": 1,
         "warmup": 1, "ms_per_step": head["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (generated on the device)",
-        "config": {"workload": WORKLOADS[args.workload][0], "requests": n_req, "mean_elements": mean_elems,
-                   "parallelism": f"replicas x{world}", "headline_load": 0.7},
+        "config": {"workload": WORKLOADS[args.workload][0], "requests": args.requests,
+                   "mean_elements": m["mean_elements"], "parallelism": f"replicas x{world}", "headline_load": 0.7},
         "latency_ms": {"p50": head["p50_ms"], "p99": head["p99_ms"], "max": head["max_ms"]},
-        "capacity_closed_loop": cap, "loads": loads,
+        "capacity_closed_loop": m["capacity_closed_loop"], "loads": loads,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -547,7 +540,8 @@ def sort_pass_roofline(recs, U):
     launch, average launch ms, item bytes, launches).  One pass reads and writes every (key, old
     index) item once: 2 * U * item bytes, averaged over the passes that moved data (a call that
     sorts by key prefix first has 12-byte items in those passes)."""
-    kname = "tile_scatter" if any(r["name"] == "tile_scatter" for r in recs) else "onesweep"
+    names = {r["name"] for r in recs}
+    kname = next((k for k in ("chunk_scatter", "tile_scatter") if k in names), "onesweep")
     sw = [r for r in recs if r["name"] == kname and not r["skipped"]]
     if not sw:
         return kname, float("nan"), float("nan"), None, 0
@@ -563,6 +557,95 @@ def step_model_bytes(N, S, M, U, D):
     N*S + N/8 + U*W; sort 2*S*U*W; run heads, scan, scatter and gather U*W + 4U + D*S; remap 12M."""
     W = S + 4
     return (4 * M + N / 8) + (N * S + N / 8 + U * W) + 2 * S * U * W + (U * W + 4 * U + D * S) + 12 * M
+
+
+def path_model_bytes(recs, N, S, M, U, D):
+    """Algorithmic bytes of the kernels that actually ran (per-launch records of whole calls, in
+    launch order), for soups (U = M used vertices, each referenced once).  Full-key path: used flags
+    4M; compaction N/8 + N*S + U*W + U (items and the digit plane); per radix pass that moved data
+    2*U*w + U (items of w bytes read and written, plane) and U (its digit count reads the plane);
+    run heads, scan, scatter and gather U*W + 4U + D*S; remap 12M.  Prefix sort: key masks N*S + N/8;
+    compaction into 16-byte records N/8 + N*S + 16U + U; its head scan 16U + 4U + 2*D*S (the run
+    heads' whole keys are read from the vertex array); the check N/8 + N*S + 4N + D*S; the full-key
+    sort's kernels after the gate count nothing (they return at once when the check passed).
+    Returns (bytes in all, launches counted as no-ops after the gate)."""
+    W = S + 4
+    total, gated_all = 0.0, 0
+    calls, cur = [], []
+    for r in recs:  # split into calls (each ends with its finalize launch)
+        cur.append(r)
+        if r["name"] == "finalize":
+            calls.append(cur)
+            cur = []
+    for call in calls:
+        prefix = any(r["name"] == "prefix_check" for r in call)
+        gated = False
+        for r in call:
+            n = r["name"]
+            if n == "prefix_gate":
+                gated = True
+                continue
+            if gated and n not in ("remap", "finalize"):
+                gated_all += 1
+                continue
+            total += _launch_bytes(r, n, prefix, N, S, W, M, U, D)
+    return total, gated_all
+
+
+def _launch_bytes(r, n, prefix, N, S, W, M, U, D):
+    """Algorithmic bytes of one launch (see path_model_bytes); 0 for a radix pass that moved nothing."""
+    if r["skipped"]:
+        return 0.0
+    if n == "used_flags":
+        return 4 * M
+    if n == "key_masks":
+        return N * S + N / 8
+    if n == "compact_hist":
+        return N / 8 + N * S + (16 * U if prefix else U * W) + U
+    if n == "tile_count":
+        return U
+    if n in ("tile_scatter", "chunk_scatter"):
+        return 2 * U * r["item_bytes"] + U
+    if n == "onesweep":
+        return 2 * U * r["item_bytes"]
+    if n == "head_scan":
+        return (16 * U + 4 * U + 2 * D * S) if prefix else (U * W + 4 * U + D * S)
+    if n == "prefix_check":
+        return N / 8 + N * S + 4 * N + D * S
+    if n == "remap":
+        return 12 * M
+    return 0.0
+
+
+def record_traffic(csv_path, kernel, capture, capture_items):
+    """Writes profiles/<kernel>_traffic.json from an ncu CSV log (metrics dram__bytes_read.sum and
+    dram__bytes_write.sum of one launch of the radix-pass kernel, captured on a workload sorting
+    capture_items 16-byte records), scaled to each full workload by the records it sorts, with the
+    digest of the kernel's current sources."""
+    import csv
+
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    vals = {}
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(f) if len(r) > 5]
+    head = rows[0]
+    mi, ui, vi = head.index("Metric Name"), head.index("Metric Unit"), head.index("Metric Value")
+    for r in rows[1:]:
+        if r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            vals[r[mi]] = float(r[vi].replace(",", "")) * scale[r[ui]]
+    per = vals["dram__bytes_read.sum"] + vals["dram__bytes_write.sum"]
+    full_items = {"heightfield2048": 25165824, "heightfield2048_s24": 25165824, "heightfield2048_s32": 25165824,
+                  "tet128": 41943040}
+    rec = {"kernel": kernel, "source_digest": source_digest(SORT_KERNEL_SOURCES[kernel]), "item_bytes": 16,
+           "capture": capture, "capture_items": capture_items,
+           "dram_read_bytes": vals["dram__bytes_read.sum"], "dram_write_bytes": vals["dram__bytes_write.sum"],
+           "per_launch_bytes_capture": per,
+           "per_launch_bytes_full": {w: round(per * u / capture_items) for w, u in full_items.items()},
+           "scaling": f"traffic grows with the records sorted: x U / {capture_items:,}"}
+    out = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    with open(out, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec))
 
 
 def merge_patches(P, T, seed=2, unused=0.05):
@@ -792,18 +875,44 @@ def run_ours(args, world, rank, local):
                 "traffic": ncu_traffic(kname, args.workload, item_bytes), "algorithmic_bytes_per_launch": alg_bytes,
                 "item_bytes": item_bytes, "avg_launch_ms": avg_ms, "passes_per_step": n_sweeps / args.steps}
 
-    # the whole step against the fixed byte model (8-bit digits, all S passes, W-byte items)
+    # the whole step against two byte models: the fixed one (8-bit digits, all S passes of W-byte
+    # items: the full-key method, whatever the call skips) and the bytes the kernels that ran move
     model = step_model_bytes(n_vtx, S, M, U, D)
-    step_model = {"bytes": model, "achieved": model / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                  "frac": model / (ms / 1e3) / 1e9 / peak,
-                  "compulsory_frac": (n_vtx * S + 8 * M + D * S) / (ms / 1e3) / 1e9 / peak,
-                  "basis": "bytes of the full-key method (8-bit digits, all S passes of (S+4)-byte items); "
-                           "the prefix sort of 16- to 32-byte keys moves fewer, so its frac can exceed 1"}
+    path_total, gated = path_model_bytes(recs, n_vtx, S, M, U, D)
+    path = path_total / args.steps
+    prefix_ran = any(r["name"] == "prefix_check" for r in recs)
+    fixed = {"bytes": model, "achieved": model / (ms / 1e3) / 1e9,
+             "frac": None if prefix_ran else model / (ms / 1e3) / 1e9 / peak,
+             "basis": "the full-key method: 8-bit digits, all S passes of (S+4)-byte items"}
+    if prefix_ran:
+        fixed["note"] = ("not a roofline here: the prefix sort moves far fewer bytes than the full-key method "
+                         "(see path)")
+    step_model = {"path": {"bytes": path, "achieved": path / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                           "frac": path / (ms / 1e3) / 1e9 / peak,
+                           "basis": "algorithmic bytes of the kernels that ran in this configuration (passes that "
+                                    "moved data, digit planes, prefix check; the gated full-key sort counts 0)",
+                           "noop_launches_after_gate_per_step": gated / args.steps},
+                  "fixed": fixed,
+                  "compulsory_frac": (n_vtx * S + 8 * M + D * S) / (ms / 1e3) / 1e9 / peak}
 
     # ---- end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(rx, torch, mesh, world, dev, args)
+
+    # ---- the batched path and the serving loop (the metric's other two parts), on this GPU
+    sub = {}
+    if world == 1 and args.workload == "heightfield2048" and not args.no_sub:
+        sub["batched"] = batched_measure(rx, torch, dev, local, max(3, min(args.steps, 10)), 3)
+        srv = serving_measure(rx, torch, dev, local, args.serving_requests, [0.7], calib_n=args.serving_requests)
+        load = srv["loads"]["0.70"]
+        sub["serving"] = {"requests": args.serving_requests, "load": 0.7, "mean_elements": srv["mean_elements"],
+                          "latency_ms": {"p50": load["p50_ms"], "p99": load["p99_ms"], "max": load["max_ms"]},
+                          "elements_per_s": load["elements_per_s"], "batches": load["batches"],
+                          "failed": load["failed"], "capacity_closed_loop": srv["capacity_closed_loop"],
+                          "stream": "the first requests of the 20,000-request stream (sizes log-uniform in "
+                                    "[1e3, 4e6] elements, 70% triangle / 30% tet soups), Poisson arrivals at 0.7 "
+                                    "of the closed-loop capacity measured on the same requests"}
     if rank != 0:
         return
     cpu = None
@@ -822,6 +931,7 @@ def run_ours(args, world, rank, local):
                    "idx_per_elem": k, "unique_out": D, "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 ({(n_vtx * S + M * 4) / 1e6:.0f} MB read per step)"},
         "roofline": roofline, "step_model": step_model, "cpu_baseline": cpu, "e2e": e2e, "tuning": tuning,
+        **sub,
         "gpu_launches": len(recs),
         "kernels": {k_: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k_, v in sorted(per_kernel.items())},
         "clocks": clocks.summary(),
@@ -861,7 +971,18 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--requests", type=int, default=20000, help="serving workload: number of requests")
     ap.add_argument("--loads", default="0.5,0.7,0.9", help="serving workload: offered loads (fractions of capacity)")
+    ap.add_argument("--no-sub", action="store_true", help="default workload: skip the batched and serving records")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="default workload: requests of the serving record")
+    ap.add_argument("--record-traffic", default=None,
+                    help="write profiles/<--traffic-kernel>_traffic.json from this ncu CSV log and exit")
+    ap.add_argument("--traffic-kernel", default="chunk_scatter")
+    ap.add_argument("--traffic-capture", default="heightfield1448, one pass")
+    ap.add_argument("--traffic-items", type=int, default=12580224)
     args = ap.parse_args()
+    if args.record_traffic:
+        record_traffic(args.record_traffic, args.traffic_kernel, args.traffic_capture, args.traffic_items)
+        return
     world, rank, local = dist_setup(args)
     try:
         if args.impl == "reference":

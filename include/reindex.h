@@ -352,7 +352,9 @@ typedef enum {
   REINDEX_K_KEY_MASKS = 13,    /* "tiles" variant: which key bits vary over the used vertices */
   REINDEX_K_PREFIX_GATE = 14,  /* prefix sort: skip the full-key sort unless two keys shared a prefix */
   REINDEX_K_PREFIX_CHECK = 15, /* prefix sort: every used vertex equals the unique vertex it was given */
-  REINDEX_K_COUNT = 16
+  REINDEX_K_CHUNK_SCATTER = 16, /* step 3, "chunk" variant: the pass's data movement (its count and
+                                   offset kernels report as TILE_COUNT and TILE_OFFSETS) */
+  REINDEX_K_COUNT = 17
 } reindex_kernel_id;
 
 void reindex_profile_enable(int on);

@@ -47,7 +47,7 @@ REINDEX_ERR_INTERNAL = 7
 
 KERNEL_NAMES = ["clear", "used_flags", "compact_hist", "sort_plan", "onesweep", "head_scan", "remap", "finalize",
                 "seg_prepare", "seg_offsets", "tile_count", "tile_offsets", "tile_scatter", "key_masks", "prefix_gate",
-                "prefix_check"]
+                "prefix_check", "chunk_scatter"]
 
 # Symbols declared in include/reindex.h (checked by the ABI test).
 EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "reindex_mesh_ws",

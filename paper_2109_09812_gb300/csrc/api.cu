@@ -21,8 +21,9 @@ namespace reindex {
 static std::mutex g_cfg_mu;
 static std::map<std::pair<int, int>, LaunchCfg> g_cfg;
 
-// Applies "sort=regs|pipe|tiles|auto,rank=ballot|match|vary,hist=uniform|peel|match,grid=persist|tile,
-// swaves=tile|1|4,pack=auto|on|off" (any subset, in any order).  Every variant computes the same result.
+// Applies "sort=regs|pipe|tiles|chunk|auto,rank=ballot|match|vary,hist=uniform|peel|match,grid=persist|tile,
+// swaves=tile|1|4,pack=auto|on|off,prefix=auto|on|off,chunk=big|small,cocc=max|1|2" (any subset, in any
+// order).  Every variant computes the same result.
 void apply_tuning(LaunchCfg& c, const char* spec) {
   if (!spec) return;
   if (std::strstr(spec, "grid=tile")) c.grid_per_tile = 1;
@@ -31,6 +32,15 @@ void apply_tuning(LaunchCfg& c, const char* spec) {
   if (std::strstr(spec, "sort=pipe") && c.occ_sort_pipe > 0) c.sort_kernel = kSortPipe;
   if (std::strstr(spec, "sort=tiles")) c.sort_kernel = kSortTiles;
   if (std::strstr(spec, "sort=auto")) c.sort_kernel = kSortAuto;
+  if (std::strstr(spec, "sort=chunk")) c.sort_kernel = kSortChunk;
+  if (std::strstr(spec, "chunk=big")) c.chunk_cfg = 0;
+  if (std::strstr(spec, "chunk=small")) c.chunk_cfg = 1;
+  if (std::strstr(spec, "chunk=wide")) c.chunk_cfg = 2;
+  if (std::strstr(spec, "chunk=deep")) c.chunk_cfg = 3;
+  if (std::strstr(spec, "cocc=max")) c.chunk_occ = 0;
+  if (std::strstr(spec, "cocc=1")) c.chunk_occ = 1;
+  if (std::strstr(spec, "cocc=2")) c.chunk_occ = 2;
+  if (const char* g = std::strstr(spec, "cgrid=")) c.chunk_grid_cap = std::atoi(g + 6);
   if (std::strstr(spec, "rank=match")) c.rank_mode = kRankMatchAny;
   if (std::strstr(spec, "rank=ballot")) c.rank_mode = kRankBallot;
   if (std::strstr(spec, "rank=vary")) c.rank_mode = kRankBallotVary;
@@ -49,7 +59,7 @@ void apply_tuning(LaunchCfg& c, const char* spec) {
 }
 
 std::string describe_tuning(const LaunchCfg& c) {
-  const char* sorts[] = {"sort=regs", "sort=pipe", "sort=tiles", "sort=auto"};
+  const char* sorts[] = {"sort=regs", "sort=pipe", "sort=tiles", "sort=auto", "sort=chunk"};
   std::string d = sorts[c.sort_kernel];
   d += c.rank_mode == kRankMatchAny ? ",rank=match" : (c.rank_mode == kRankBallotVary ? ",rank=vary" : ",rank=ballot");
   d += c.hist_mode == kHistMatchAny ? ",hist=match" : (c.hist_mode == kHistPeel ? ",hist=peel" : ",hist=uniform");
@@ -57,6 +67,10 @@ std::string describe_tuning(const LaunchCfg& c) {
   d += c.scatter_waves ? ",swaves=" + std::to_string(c.scatter_waves) : std::string(",swaves=tile");
   d += c.pack_keys < 0 ? ",pack=auto" : (c.pack_keys ? ",pack=on" : ",pack=off");
   d += c.prefix < 0 ? ",prefix=auto" : (c.prefix ? ",prefix=on" : ",prefix=off");
+  const char* shapes[] = {",chunk=big", ",chunk=small", ",chunk=wide", ",chunk=deep"};
+  d += shapes[c.chunk_cfg & 3];
+  d += c.chunk_occ ? ",cocc=" + std::to_string(c.chunk_occ) : std::string(",cocc=max");
+  if (c.chunk_grid_cap > 0) d += ",cgrid=" + std::to_string(c.chunk_grid_cap);
   return d;
 }
 
@@ -73,6 +87,7 @@ static LaunchCfg& launch_cfg_locked(int S) {
   c.occ_head = occupancy_head(S);
   c.occ_sort_pipe = occupancy_sort_pipe(S);
   c.occ_tiles = occupancy_tiles(S);
+  for (int k = 0; k < 4; ++k) c.occ_chunk[k] = occupancy_chunk(S, k);
   if (c.occ_sort_pipe < 1 && c.sort_kernel == kSortPipe) c.sort_kernel = kSortRegs;  // too little shared memory
   // 16- to 32-byte keys rank faster without the ballots of constant digit bits (register pressure
   // of the wider items); 4- to 12-byte keys with all eight (measured on GB300)
@@ -201,6 +216,21 @@ struct PipeExtras {
 // One radix pass (digit d) with the configured kernel variant.
 static cudaError_t sort_pass(int S, int d, const WsPtrs& p, const LaunchCfg& c, cudaStream_t st,
                              const uint8_t* skip) {
+  if (c.sort_kernel == kSortChunk) {
+    const int G = chunk_grid(S, c, p.Umax);  // the same chunks in the three kernels
+    {
+      prof::Scope s(REINDEX_K_TILE_COUNT, d, st, skip, S + 4);
+      cudaError_t e = launch_chunk_count(S, d, p, G, chunk_tile_items(S, c.chunk_cfg), st);
+      if (e != cudaSuccess) return e;
+    }
+    {
+      prof::Scope s(REINDEX_K_TILE_OFFSETS, d, st, skip, S + 4);
+      cudaError_t e = launch_tile_offsets(d, p, st, G);
+      if (e != cudaSuccess) return e;
+    }
+    prof::Scope s(REINDEX_K_CHUNK_SCATTER, d, st, skip, S + 4);
+    return launch_chunk_scatter(S, d, p, c, G, st);
+  }
   if (c.sort_kernel == kSortTiles) {
     {
       prof::Scope s(REINDEX_K_TILE_COUNT, d, st, skip, S + 4);
@@ -244,9 +274,11 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
   }
   if (extra && extra->vtx_ready) REINDEX_TRY(cudaStreamWaitEvent(st, extra->vtx_ready, 0));
   if (prefix) {
-    LaunchCfg cp = c;  // the passes sort 12-byte keys (8 varying bytes) with the tiles sort
-    cp.sort_kernel = kSortTiles;
-    cp.occ_tiles = launch_cfg(kPrefixItem).occ_tiles;
+    LaunchCfg cp = c;  // the passes sort 12-byte keys (8 varying bytes) with the tiles or chunk sort
+    cp.sort_kernel = c.sort_kernel == kSortChunk ? kSortChunk : kSortTiles;
+    const LaunchCfg c12 = launch_cfg(kPrefixItem);
+    cp.occ_tiles = c12.occ_tiles;
+    for (int k = 0; k < 4; ++k) cp.occ_chunk[k] = c12.occ_chunk[k];
     {
       prof::Scope s(REINDEX_K_KEY_MASKS, -1, st);
       REINDEX_TRY(launch_key_masks(S, vtx, nVtx, pp, c, nullptr, st));
@@ -281,7 +313,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
     REINDEX_TRY(launch_used_flags(idx, M, nVtx, p, c, st));
     c.scatter_waves = 1;  // the full-key sort's passes: few CTAs, cheap when skipped
   }
-  if (c.sort_kernel == kSortTiles && c.pack_keys) {  // bit masks -> plan (key packing) -> compaction
+  if (uses_plane(c.sort_kernel) && c.pack_keys) {  // bit masks -> plan (key packing) -> compaction
     {
       prof::Scope s(REINDEX_K_KEY_MASKS, -1, st);
       REINDEX_TRY(launch_key_masks(S, vtx, nVtx, p, c, nullptr, st));
@@ -298,7 +330,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
       REINDEX_TRY(launch_compact(S, vtx, nVtx, p, L.tilesV, c, nullptr, st));
     }
     prof::Scope s(REINDEX_K_SORT_PLAN, -1, st);
-    REINDEX_TRY(launch_sort_plan(S, p, c.sort_kernel == kSortTiles, false, st));
+    REINDEX_TRY(launch_sort_plan(S, p, uses_plane(c.sort_kernel), false, st));
   }
   const uint8_t* skip = prof::skip_buffer(p.plan, st);
   for (int d = 0; d < L.P; ++d) REINDEX_TRY(sort_pass(S, d, p, c, st, skip));
@@ -367,7 +399,7 @@ static reindex_status run_batched(const void* vtx, int64_t nVtx, int S, const in
   LaunchCfg cc = cS;  // the sort (configured for S + 4) decides whether histograms are taken
   cc.sort_kernel = c.sort_kernel;
   cc.pack_keys = c.pack_keys;
-  if (c.sort_kernel == kSortTiles && c.pack_keys) {  // bit masks -> plan (key packing) -> compaction
+  if (uses_plane(c.sort_kernel) && c.pack_keys) {  // bit masks -> plan (key packing) -> compaction
     {
       prof::Scope sc(REINDEX_K_KEY_MASKS, -1, st);
       REINDEX_TRY(launch_key_masks(S, vtx, nVtx, p, cc, &seg, st));
@@ -384,7 +416,7 @@ static reindex_status run_batched(const void* vtx, int64_t nVtx, int S, const in
       REINDEX_TRY(launch_compact(S, vtx, nVtx, p, SL.L.tilesV, cc, &seg, st));
     }
     prof::Scope sc(REINDEX_K_SORT_PLAN, -1, st);
-    REINDEX_TRY(launch_sort_plan(S + 4, p, c.sort_kernel == kSortTiles, false, st));
+    REINDEX_TRY(launch_sort_plan(S + 4, p, uses_plane(c.sort_kernel), false, st));
   }
   const uint8_t* skip = prof::skip_buffer(p.plan, st);
   for (int d = 0; d < S + 4; ++d) REINDEX_TRY(sort_pass(S + 4, d, p, c, st, skip));
@@ -746,7 +778,8 @@ const char* reindex_kernel_name(int kernel) {
   static const char* names[REINDEX_K_COUNT] = {"clear",     "used_flags", "compact_hist", "sort_plan",
                                                "onesweep",  "head_scan",  "remap",        "finalize",
                                                "seg_prepare", "seg_offsets", "tile_count", "tile_offsets",
-                                               "tile_scatter", "key_masks", "prefix_gate", "prefix_check"};
+                                               "tile_scatter", "key_masks", "prefix_gate", "prefix_check",
+                                               "chunk_scatter"};
   return (kernel >= 0 && kernel < REINDEX_K_COUNT) ? names[kernel] : "unknown";
 }
 

@@ -33,8 +33,9 @@ constexpr int kWideMin = 24;               // keys of 24 and 32 bytes (single me
 constexpr int kSortRegs = 0;      // radix pass with items in registers (k_onesweep)
 constexpr int kSortPipe = 1;      // radix pass pipelined through shared memory (k_onesweep_pipe)
 constexpr int kSortTiles = 2;     // radix pass with precounted tile offsets (k_radix_tiles.cu)
-constexpr int kSortAuto = 3;      // per call: kSortTiles for large meshes, else kSortRegs (the faster
-                                  // of the two on GB300 for each)
+constexpr int kSortAuto = 3;      // per call: kSortChunk for large meshes, else kSortRegs (the faster
+                                  // on GB300 for each)
+constexpr int kSortChunk = 4;     // radix pass over contiguous chunks with bulk-copied tiles (k_radix_chunk.cu)
 constexpr int64_t kTilesMinItems = 1 << 21;  // below this, launch count favours kSortRegs
 constexpr int kRankBallot = 0;    // digit peers from 8 ballots
 constexpr int kRankMatchAny = 1;  // digit peers from match.any

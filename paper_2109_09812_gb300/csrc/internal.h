@@ -18,7 +18,8 @@ struct LaunchCfg {
   int occ_head = 0;
   int occ_sort_pipe = 0;
   int occ_tiles = 0;
-  int sort_kernel = kSortAuto;  // kSortRegs (k_onesweep), kSortPipe (k_onesweep_pipe), kSortTiles, kSortAuto
+  int sort_kernel = kSortAuto;  // kSortRegs (k_onesweep), kSortPipe (k_onesweep_pipe), kSortTiles, kSortChunk,
+                                // kSortAuto
   int rank_mode = kRankBallot;  // digit matching of the radix passes (kRank*; onesweep: ballot or match)
   int hist_mode = kHistUniform; // compaction histogram method (kHist*)
   int grid_per_tile = 0;        // 1: one CTA per tile; 0: persistent CTAs (SMs x occupancy)
@@ -28,17 +29,31 @@ struct LaunchCfg {
   int prefix = -1;              // single meshes of 12- to 32-byte vertices: sort by the 64 most
                                 // significant varying key bits first (1 on, 0 off, -1 auto: 16 bytes
                                 // and wider)
+  int chunk_cfg = 2;            // "chunk" sort tile shape: 0 big (4096-item tiles, 512 threads; 2048
+                                // for items over 20 bytes), 1 small (2048-item tiles, 256 threads),
+                                // 2 wide (2048-item tiles, 512 threads, 2 CTAs per SM), 3 deep
+                                // (4096-item tiles, 1024 threads)
+  int chunk_occ = 0;            // "chunk" sort: resident CTAs per SM to launch (0: as many as fit)
+  int occ_chunk[4] = {0, 0, 0, 0};  // resident CTAs per SM of the chunk scatter, per tile shape
+  int chunk_grid_cap = 0;       // "chunk" sort: at most this many chunks (0: no cap; small caps give
+                                // every CTA many tiles, e.g. to test the pipeline on small meshes)
 };
+
+// The "tiles" and "chunk" sorts take no upfront histograms: the compaction writes the first pass's
+// digit plane (and the key bit masks), and each pass counts its digits itself.
+inline bool uses_plane(int sort_kernel) { return sort_kernel == kSortTiles || sort_kernel == kSortChunk; }
 
 // The configuration for one call: kSortAuto resolved for S-byte keys and up to Umax items.
 // batched: the call sorts (mesh id, vertex) keys, whose mesh-id bytes are mostly constant.
-// 24- and 32-byte keys always take the "tiles" sort with vary ranking (the only variants built).
+// Large meshes take the "chunk" sort, small ones the onesweep sort (fewer launches); 24- and
+// 32-byte keys take the "tiles" or "chunk" sort with vary ranking (the only variants built).
 inline LaunchCfg resolve_cfg(LaunchCfg c, int S, int64_t Umax, bool batched = false) {
   if (S >= kWideMin) {
-    c.sort_kernel = kSortTiles;
+    if (c.sort_kernel != kSortChunk && c.sort_kernel != kSortTiles)
+      c.sort_kernel = (c.sort_kernel == kSortAuto && Umax >= kTilesMinItems) ? kSortChunk : kSortTiles;
     c.rank_mode = kRankBallotVary;
   }
-  if (c.sort_kernel == kSortAuto) c.sort_kernel = Umax >= kTilesMinItems ? kSortTiles : kSortRegs;
+  if (c.sort_kernel == kSortAuto) c.sort_kernel = Umax >= kTilesMinItems ? kSortChunk : kSortRegs;
   if (c.pack_keys < 0) c.pack_keys = (batched || S <= 8) ? 1 : 0;
   if (batched || S <= kPrefixBytes)
     c.prefix = 0;
@@ -99,7 +114,13 @@ cudaError_t launch_onesweep(int S, int digit, WsPtrs ws, const LaunchCfg& c, cud
 cudaError_t launch_onesweep_pipe(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 // The "tiles" radix pass (k_radix_tiles.cu): per-tile digit counts, their scan, the scatter.
 cudaError_t launch_tile_count(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
-cudaError_t launch_tile_offsets(int digit, WsPtrs ws, cudaStream_t st);
+cudaError_t launch_tile_offsets(int digit, WsPtrs ws, cudaStream_t st, int chunks = 0);
+// The "chunk" radix pass (k_radix_chunk.cu): per-chunk digit counts, their scan (launch_tile_offsets
+// with chunks = G), the pipelined scatter.  G = chunk_grid(...) for the whole call.
+int chunk_tile_items(int S, int cfg);
+int chunk_grid(int S, const LaunchCfg& c, int64_t Umax);
+cudaError_t launch_chunk_count(int S, int digit, WsPtrs ws, int G, int T, cudaStream_t st);
+cudaError_t launch_chunk_scatter(int S, int digit, WsPtrs ws, const LaunchCfg& c, int G, cudaStream_t st);
 cudaError_t launch_tile_scatter(int S, int digit, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 // seg != nullptr: batched, S being the item key size (vertex stride + 4); writes seg->outOff.
 cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx, uint32_t nVtx,
@@ -127,6 +148,7 @@ int occupancy_compact(int S);
 int occupancy_sort(int S);
 int occupancy_sort_pipe(int S);
 int occupancy_tiles(int S);
+int occupancy_chunk(int S, int cfg);
 int occupancy_head(int S);
 
 // Device-wide sticky error word (read and cleared by reindex_stream_status).

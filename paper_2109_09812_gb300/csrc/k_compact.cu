@@ -426,7 +426,7 @@ cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int6
   const bool persistent = !c.grid_per_tile;
   const SegArgs none{};
   // the "tiles" sort counts digits per pass and needs no upfront histograms
-  const int mode = c.sort_kernel == kSortTiles ? (c.pack_keys ? kHistNone : kHistMasks) : c.hist_mode;
+  const int mode = uses_plane(c.sort_kernel) ? (c.pack_keys ? kHistNone : kHistMasks) : c.hist_mode;
   if (seg) {
     switch (S) {
       case 4: launch_s<4, true>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, *seg, st); break;

@@ -251,7 +251,7 @@ cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx,
   if (g > tiles) g = tiles;
   if (g < 1) g = 1;
   const SegArgs none{};
-  const bool may_pack = c.sort_kernel == kSortTiles && c.pack_keys != 0;
+  const bool may_pack = uses_plane(c.sort_kernel) && c.pack_keys != 0;
   if (seg) {
     switch (S) {
       case 8: launch_s<8, true>((int)g, ws, out_vtx, out_nVtx, nVtx, *seg, may_pack, st); break;

@@ -26,48 +26,6 @@ __device__ __forceinline__ uint32_t* tile_counts(const WsPtrs& ws, int v) {
   return ws.lb_sort + (size_t)v * (size_t)ws.tilesS;
 }
 
-// Per-pass values of the plan, read once by thread 0 and shared, together with the error word
-// (so that every thread of the CTA takes the same early exit).
-struct PassInfo {
-  uint32_t U, run, src, next, vary;
-  uint32_t keys;  // k_tile_count reads digit d from the keys: a first pass whose digit is not in the
-                  // compaction's plane (unpacked keys whose byte 0 is constant)
-};
-
-// A skipped pass exits without a barrier: every thread reads the skip flag through the read-only
-// cache (written by an earlier kernel), so the CTAs of a skipped pass cost almost nothing.
-template <bool kCount = false>
-__device__ __forceinline__ PassInfo pass_info(const WsPtrs& ws, int d) {
-  __shared__ PassInfo s_pi;
-  if (__ldg(ws.plan->skip + d)) return PassInfo{0, 0, 0, 0, 0, 0};
-  if (threadIdx.x == 0) {
-    const Plan* plan = ws.plan;
-    const uint32_t skip = plan->skip[d], U = plan->U, src = plan->src[d];
-    const int next = plan->next[d];
-    const uint32_t err = *(volatile const uint32_t*)&ws.ctrl->err;
-    s_pi.U = U;
-    s_pi.run = (!skip && err == 0) ? 1u : 0u;
-    s_pi.src = src;
-    s_pi.next = (uint32_t)(int32_t)next;
-    s_pi.vary = plan->vary[d];
-    if (kCount) {
-      const int first = plan->first;
-      s_pi.keys = (d == first && d != 0 && !plan->plane_first) ? 1u : 0u;
-    }
-  }
-  __syncthreads();
-  const PassInfo pi = s_pi;
-  __syncthreads();
-  return pi;
-}
-
-// Word `word` of item i's key, read from an item buffer.
-template <int S>
-__device__ __forceinline__ uint32_t item_key_word(const unsigned char* buf, int64_t i, int word) {
-  constexpr int kStride = soa_items(S) ? S / 4 : S / 4 + 1;  // words per item in the key array
-  return reinterpret_cast<const uint32_t*>(buf)[i * kStride + word];
-}
-
 // k_tile_count: a CTA counts 16 consecutive tiles, each warp two whole tiles into its own
 // histogram row (so warps never contend), then the CTA writes every digit's 16 counts as one
 // contiguous 64-byte run.  Rows are padded by one word so that reading a column is conflict-free.
@@ -140,19 +98,21 @@ constexpr int kOffWarps = kOffThreads / 32;
 constexpr int kOffBatch = 8;  // rows of 32 counts loaded together per warp
 
 // One CTA per digit value v: cnt[v][tile] -> (items with a digit below v) + sum of
-// cnt[v][0 .. tile).  Warp w owns a contiguous segment of the column and walks it in rows of 32
+// cnt[v][0 .. tile) (or the same over the chunks of the chunk sort).  Warp w owns a contiguous segment of the column and walks it in rows of 32
 // consecutive tiles (coalesced): a first sweep sums the segment, one barrier gives the segment
 // starts, and a second sweep scans each row and writes the offsets.
-__global__ void __launch_bounds__(kOffThreads, 2) k_tile_offsets(WsPtrs ws, int d) {
+__global__ void __launch_bounds__(kOffThreads, 2) k_tile_offsets(WsPtrs ws, int d, int cols) {
   __shared__ uint32_t s_seg[kOffWarps];
   __shared__ uint32_t s_below[kRadix / 32];
   pdl_wait();
   pdl_trigger();
   const PassInfo pi = pass_info(ws, d);
   if (!pi.run) return;
-  const uint32_t ntiles = (pi.U + kSortTile - 1) / kSortTile;
+  // tiles sort: one count per 4096-item tile, column v at v * tilesS; chunk sort (cols > 0): one
+  // count per chunk, column v at v * cols
+  const uint32_t ntiles = cols > 0 ? (uint32_t)cols : (pi.U + kSortTile - 1) / kSortTile;
   const int v = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
-  uint32_t* col = tile_counts(ws, v);
+  uint32_t* col = cols > 0 ? ws.lb_sort + (size_t)v * cols : tile_counts(ws, v);
   const uint32_t rows = (ntiles + 32 * kOffWarps - 1) / (32 * kOffWarps);  // rows of 32 per warp
   const uint32_t seg0 = (uint32_t)w * rows * 32;
   uint32_t below = (t < v) ? ws.hist[d * kRadix + t] : 0u;  // items whose digit is smaller than v
@@ -380,9 +340,9 @@ cudaError_t launch_tile_count(int S, int digit, WsPtrs ws, const LaunchCfg& c, c
   }
 }
 
-cudaError_t launch_tile_offsets(int digit, WsPtrs ws, cudaStream_t st) {
+cudaError_t launch_tile_offsets(int digit, WsPtrs ws, cudaStream_t st, int chunks) {
   if (ws.Umax < 1) return cudaSuccess;
-  return launch_pdl(k_tile_offsets, kRadix, kOffThreads, 0, st, ws, digit);
+  return launch_pdl(k_tile_offsets, kRadix, kOffThreads, 0, st, ws, digit, chunks);
 }
 
 // The pass over key word `word` (word 0 is the most significant), one instantiation per word.

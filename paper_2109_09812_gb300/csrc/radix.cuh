@@ -126,13 +126,17 @@ struct SortSmem {
 // match.any, from 8 ballots (one per digit bit), or (kRankBallotVary) from ballots on the bits in
 // `vary` only: the digit bits that differ between items anywhere in the array (the others are
 // equal in every valid lane; the branches are warp-uniform).
-template <int kMode>
+// kAllValid: every lane holds an item (a full row), so no validity vote is needed.
+template <int kMode, bool kAllValid = false>
 __device__ __forceinline__ uint32_t match_digit(uint32_t dig, bool valid, uint32_t vary) {
   if (kMode == kRankMatchAny) {
-    return __match_any_sync(0xffffffffu, valid ? dig : 0x100u);
+    return __match_any_sync(0xffffffffu, (kAllValid || valid) ? dig : 0x100u);
   } else {
-    uint32_t peers = __ballot_sync(0xffffffffu, valid);
-    if (!valid) peers = ~peers;
+    uint32_t peers = 0xffffffffu;
+    if (!kAllValid) {
+      peers = __ballot_sync(0xffffffffu, valid);
+      if (!valid) peers = ~peers;
+    }
 #pragma unroll
     for (int b = 0; b < kRadixBits; ++b) {
       if (kMode == kRankBallotVary && !((vary >> b) & 1u)) continue;
@@ -142,6 +146,48 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t dig, bool valid, uint32
     }
     return peers;
   }
+}
+
+// Per-pass values of the plan, read once by thread 0 and shared, together with the error word
+// (so that every thread of the CTA takes the same early exit).
+struct PassInfo {
+  uint32_t U, run, src, next, vary;
+  uint32_t keys;  // k_tile_count reads digit d from the keys: a first pass whose digit is not in the
+                  // compaction's plane (unpacked keys whose byte 0 is constant)
+};
+
+// A skipped pass exits without a barrier: every thread reads the skip flag through the read-only
+// cache (written by an earlier kernel), so the CTAs of a skipped pass cost almost nothing.
+template <bool kCount = false>
+__device__ __forceinline__ PassInfo pass_info(const WsPtrs& ws, int d) {
+  __shared__ PassInfo s_pi;
+  if (__ldg(ws.plan->skip + d)) return PassInfo{0, 0, 0, 0, 0, 0};
+  if (threadIdx.x == 0) {
+    const Plan* plan = ws.plan;
+    const uint32_t skip = plan->skip[d], U = plan->U, src = plan->src[d];
+    const int next = plan->next[d];
+    const uint32_t err = *(volatile const uint32_t*)&ws.ctrl->err;
+    s_pi.U = U;
+    s_pi.run = (!skip && err == 0) ? 1u : 0u;
+    s_pi.src = src;
+    s_pi.next = (uint32_t)(int32_t)next;
+    s_pi.vary = plan->vary[d];
+    if (kCount) {
+      const int first = plan->first;
+      s_pi.keys = (d == first && d != 0 && !plan->plane_first) ? 1u : 0u;
+    }
+  }
+  __syncthreads();
+  const PassInfo pi = s_pi;
+  __syncthreads();
+  return pi;
+}
+
+// Word `word` of item i's key, read from an item buffer.
+template <int S>
+__device__ __forceinline__ uint32_t item_key_word(const unsigned char* buf, int64_t i, int word) {
+  constexpr int kStride = soa_items(S) ? S / 4 : S / 4 + 1;  // words per item in the key array
+  return reinterpret_cast<const uint32_t*>(buf)[i * kStride + word];
 }
 
 }  // namespace reindex

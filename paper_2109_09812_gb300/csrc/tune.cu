@@ -1,9 +1,12 @@
 // Autotuner: picks, per device and vertex stride, the fastest of the library's kernel variants
 // for the caller's own mesh, by timing whole reindex_mesh_ws runs with CUDA events.
 //   knobs: radix-pass kernel (register-tiled onesweep, 4096-item tiles | TMA-pipelined through
-//          shared memory, 2048-4096-item tiles | precounted tile offsets), digit matching (8 ballots | match.any), histogram
-//          method (uniform check | peel | match.any), grid shape (persistent | one CTA per tile),
-//          CTAs of the "tiles" scatter (one per tile | 1 or 4 waves striding over the tiles)
+//          shared memory, 2048-4096-item tiles | precounted tile offsets | contiguous chunks with
+//          bulk-copied tiles), digit matching (8 ballots | match.any | ballots on varying bits),
+//          histogram method (uniform check | peel | match.any), grid shape (persistent | one CTA
+//          per tile), CTAs of the "tiles" scatter (one per tile | 1 or 4 waves striding over the
+//          tiles), tile size and threads of the chunk sort (2048 or 4096 items, 256-1024 threads)
+//          and its resident CTAs per SM (as many as fit | 1), key packing, prefix sort
 // Coordinate descent: each knob in turn takes the value with the lowest median time while the
 // others stay fixed.  The choice applies to every later call on the device and, if the
 // environment variable REINDEX_TUNE_CACHE names a file, is appended to it so that a later
@@ -99,17 +102,19 @@ reindex_status reindex_autotune(const void* vtx, int64_t nVtx, int S, const int3
   LaunchCfg best = start;
   float best_ms = 0.f;
   reindex_status rs = timed(&best_ms);
-  const char* knobs[][4] = {{"sort=regs", "sort=pipe", "sort=tiles", nullptr},
-                            {"rank=ballot", "rank=match", "rank=vary", nullptr},
-                            {"hist=uniform", "hist=peel", "hist=match", nullptr},
-                            {"grid=persist", "grid=tile", nullptr, nullptr},
-                            {"swaves=tile", "swaves=1", "swaves=4", nullptr},
-                            {"pack=auto", "pack=on", "pack=off", nullptr},
-                            {"prefix=auto", "prefix=on", "prefix=off", nullptr}};
-  for (int ki = 0; ki < 7; ++ki) {
+  const char* knobs[][5] = {{"sort=regs", "sort=pipe", "sort=tiles", "sort=chunk", nullptr},
+                            {"rank=ballot", "rank=match", "rank=vary", nullptr, nullptr},
+                            {"hist=uniform", "hist=peel", "hist=match", nullptr, nullptr},
+                            {"grid=persist", "grid=tile", nullptr, nullptr, nullptr},
+                            {"swaves=tile", "swaves=1", "swaves=4", nullptr, nullptr},
+                            {"chunk=wide", "chunk=big", "chunk=small", "chunk=deep", nullptr},
+                            {"cocc=max", "cocc=1", nullptr, nullptr, nullptr},
+                            {"pack=auto", "pack=on", "pack=off", nullptr, nullptr},
+                            {"prefix=auto", "prefix=on", "prefix=off", nullptr, nullptr}};
+  for (int ki = 0; ki < 9; ++ki) {
     const auto& knob = knobs[ki];
     if (rs != REINDEX_OK) break;
-    if (S >= kWideMin && ki < 3) continue;  // 24- and 32-byte keys: one sort and rank variant only
+    if (S >= kWideMin && ki < 3) continue;  // 24- and 32-byte keys: the tiles or chunk sort, vary ranking
     for (const char* v : knob) {
       if (!v) continue;
       LaunchCfg c = best;

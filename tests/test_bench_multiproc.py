@@ -80,3 +80,35 @@ def test_sort_pass_roofline_weighs_each_pass_by_its_item_size():
     assert per_launch == (8 * 2 * U * 16 + 2 * U * 36) / 9 and avg_ms == 10.0 / 9
     kname, *_ = bench.sort_pass_roofline([dict(name="onesweep", skipped=False, ms=1.0, item_bytes=16)], U)
     assert kname == "onesweep"
+
+
+def _rec(name, item_bytes=0, skipped=0):
+    return {"name": name, "item_bytes": item_bytes, "skipped": skipped, "ms": 0.1, "digit": -1}
+
+
+def test_path_model_counts_the_kernels_that_ran():
+    """The path byte model: a full-key call is the fixed model minus its skipped passes plus the
+    digit planes; a prefix-sort call counts its own kernels and nothing after the gate."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    N, S, M, U, D = 1000, 12, 900, 900, 300
+    W = S + 4
+    full = [_rec("clear"), _rec("used_flags"), _rec("compact_hist"), _rec("sort_plan")]
+    for p in range(12):
+        sk = int(p in (0, 4))
+        full += [_rec("tile_count", W, sk), _rec("tile_offsets", W, sk), _rec("chunk_scatter", W, sk)]
+    full += [_rec("head_scan"), _rec("remap"), _rec("finalize")]
+    got, gated = bench.path_model_bytes(full, N, S, M, U, D)
+    want = 4 * M + (N / 8 + N * S + U * W + U) + 10 * (U + 2 * U * W + U) + (U * W + 4 * U + D * S) + 12 * M
+    assert gated == 0 and abs(got - want) < 1e-6
+    S = 32
+    pre = [_rec("clear"), _rec("used_flags"), _rec("key_masks"), _rec("sort_plan"), _rec("compact_hist")]
+    pre += [_rec("tile_count", 16), _rec("tile_offsets", 16), _rec("chunk_scatter", 16)] * 8
+    pre += [_rec("head_scan"), _rec("prefix_check"), _rec("clear"), _rec("prefix_gate"), _rec("used_flags"),
+            _rec("compact_hist"), _rec("sort_plan"), _rec("chunk_scatter", 36), _rec("head_scan"), _rec("remap"),
+            _rec("finalize")]
+    got, gated = bench.path_model_bytes(pre * 2, N, S, M, U, D)  # two calls
+    want = 2 * (4 * M + (N * S + N / 8) + (N / 8 + N * S + 16 * U + U) + 8 * (U + 2 * U * 16 + U)
+                + (16 * U + 4 * U + 2 * D * S) + (N / 8 + N * S + 4 * N + D * S) + 12 * M)
+    assert gated == 2 * 5 and abs(got - want) < 1e-6

@@ -288,7 +288,10 @@ def test_profile_records_every_kernel(rx, sort):
 SORT_VARIANTS = ["sort=regs,rank=ballot,grid=persist,prefix=off", "sort=regs,rank=match,grid=tile",
                  "sort=pipe,rank=ballot,grid=persist,prefix=off", "sort=tiles,rank=ballot,swaves=1,pack=on",
                  "sort=tiles,rank=match,swaves=tile,pack=off,prefix=off", "sort=tiles,rank=ballot,swaves=4,pack=off",
-                 "sort=tiles,rank=vary,swaves=tile,pack=on,prefix=off", "sort=tiles,rank=ballot,pack=auto"]
+                 "sort=tiles,rank=vary,swaves=tile,pack=on,prefix=off", "sort=tiles,rank=ballot,pack=auto",
+                 "sort=chunk,chunk=big,pack=off,prefix=off", "sort=chunk,chunk=small,pack=on,prefix=off",
+                 "sort=chunk,chunk=big,cgrid=3,pack=auto", "sort=chunk,chunk=small,cgrid=5,cocc=1,pack=off",
+                 "sort=chunk,chunk=wide,cgrid=7,rank=match,pack=on", "sort=chunk,chunk=deep,cgrid=2,pack=off,prefix=off"]
 
 
 @pytest.mark.parametrize("spec", SORT_VARIANTS)
@@ -309,7 +312,8 @@ def test_sort_variants_bit_exact(rx, spec, S):
 
 
 WIDE_VARIANTS = ["pack=off,swaves=tile,prefix=off", "pack=on,swaves=tile,prefix=off", "pack=auto,swaves=1",
-                 "pack=on,swaves=4"]
+                 "pack=on,swaves=4", "sort=chunk,chunk=big,cgrid=4,prefix=off", "sort=chunk,chunk=small,prefix=auto",
+                 "sort=chunk,chunk=wide,cgrid=3,prefix=off", "sort=chunk,chunk=deep,prefix=auto"]
 
 
 @pytest.mark.parametrize("spec", WIDE_VARIANTS)
