@@ -53,8 +53,9 @@
  *     vector type: 4 bytes for S = 4, 12 and 20, 8 bytes for S = 8 and 24, 16 bytes for
  *     S = 16 and 32.  idx and out_idx must be 4-byte aligned (16-byte alignment enables
  *     128-bit vector loads and stores).
- *   - nVtx <= 2^30 - 1 and nElem * idxPerElem <= 2^31 - 1 (int32 indices; the look-back
- *     status words pack a 30-bit count).
+ *   - nVtx <= 2^31 - 1 (INT32_MAX; the look-back status words carry 31-bit counts and the old
+ *     vertex index travels as 32 bits) and nElem * idxPerElem <= 2^31 - 1 for int32 indices; the
+ *     int64-index entry points (reindex_mesh64*) take up to 2^40 index entries.
  *   - out_idx may alias idx (the remap reads and writes the same slot in one thread).  No
  *     other output may overlap an input.
  *   - Thread safety: calls may be issued concurrently from several host threads on different
@@ -118,6 +119,25 @@ reindex_status reindex_mesh_ws(const void* vtx, int64_t nVtx, int vtxStrideBytes
                                const int32_t* idx, int64_t nElem, int idxPerElem,
                                void* out_vtx, int64_t* out_nVtx, int32_t* out_idx,
                                void* ws, size_t wsBytes, reindex_stream_t stream);
+
+/* ---- int64 indices ----------------------------------------------------------------------------
+ * reindex_mesh / reindex_mesh_ws for 8-byte indices: idx and out_idx are DEVICE int64 arrays of
+ * nElem * idxPerElem entries (8-byte aligned; 16-byte alignment enables vector loads), which may
+ * alias.  Everything else -- vertices, result, workspace layout, errors -- is as for the int32
+ * entry points; the index arrays no longer cap the element count at 2^31 - 1 indices (up to 2^40
+ * here), while nVtx <= 2^31 - 1 still holds (indices beyond nVtx, however large, and negative
+ * indices are REINDEX_ERR_INDEX_RANGE; none is truncated to 32 bits).  Section 3.5 of the paper
+ * expects other formats to carry over; int64 index buffers are the common one besides int32.
+ * reindex_workspace_size64 gives the workspace of reindex_mesh64_ws (0 for unsupported sizes). */
+size_t reindex_workspace_size64(int64_t nVtx, int vtxStrideBytes, int64_t nElem, int idxPerElem);
+reindex_status reindex_mesh64(const void* vtx, int64_t nVtx, int vtxStrideBytes,
+                              const int64_t* idx, int64_t nElem, int idxPerElem,
+                              void* out_vtx, int64_t* out_nVtx, int64_t* out_idx,
+                              reindex_stream_t stream);
+reindex_status reindex_mesh64_ws(const void* vtx, int64_t nVtx, int vtxStrideBytes,
+                                  const int64_t* idx, int64_t nElem, int idxPerElem,
+                                  void* out_vtx, int64_t* out_nVtx, int64_t* out_idx,
+                                  void* ws, size_t wsBytes, reindex_stream_t stream);
 
 /* End-to-end variant on HOST buffers: copies vtx and idx to the device, runs the pipeline and
  * copies the D unique vertices, the indices and D back.  host_vtx / host_idx should be pinned

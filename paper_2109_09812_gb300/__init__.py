@@ -57,7 +57,8 @@ EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "
             "reindex_server_drain", "reindex_server_get_stats", "reindex_server_destroy", "reindex_debug_arena_check",
             "reindex_merge_workspace_size", "reindex_merge_meshes", "reindex_submesh_workspace_size",
             "reindex_submesh", "reindex_autotune", "reindex_tuning_get", "reindex_tuning_set",
-            "reindex_debug_stall_tile", "reindex_debug_prefix_pack", "reindex_debug_pack_keys"]
+            "reindex_debug_stall_tile", "reindex_debug_prefix_pack", "reindex_debug_pack_keys",
+            "reindex_workspace_size64", "reindex_mesh64", "reindex_mesh64_ws"]
 
 _lock = threading.Lock()
 _lib = None
@@ -116,6 +117,12 @@ def lib() -> ctypes.CDLL:
             L.reindex_mesh_ws.argtypes = mesh_args + [vp, ctypes.c_size_t, vp]
             L.reindex_mesh_ws.restype = ci
             L.reindex_mesh_host.argtypes = mesh_args + [vp]
+            L.reindex_mesh64.argtypes = mesh_args + [vp]
+            L.reindex_mesh64.restype = ci
+            L.reindex_mesh64_ws.argtypes = mesh_args + [vp, ctypes.c_size_t, vp]
+            L.reindex_mesh64_ws.restype = ci
+            L.reindex_workspace_size64.argtypes = [i64, ci, i64, ci]
+            L.reindex_workspace_size64.restype = ctypes.c_size_t
             L.reindex_mesh_host.restype = ci
             L.reindex_stream_status.argtypes = [vp]
             L.reindex_stream_status.restype = ci
@@ -194,14 +201,16 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _mesh_geometry(vtx, idx):
+def _mesh_geometry(vtx, idx, wide_ok=False):
     """(nVtx, strideBytes, nElem, k) from a (nVtx, ...) tensor with one vertex per row and an
-    (nElem, k) int32 index tensor."""
+    (nElem, k) int32 (or, where wide_ok, int64) index tensor."""
     torch = _torch()
     if vtx.dim() < 1 or not vtx.is_contiguous():
         raise ValueError("vtx must be a contiguous tensor with one vertex per row")
-    if idx.dtype != torch.int32 or idx.dim() != 2 or not idx.is_contiguous():
-        raise ValueError("idx must be a contiguous (nElem, idxPerElem) int32 tensor")
+    ok = (torch.int32, torch.int64) if wide_ok else (torch.int32,)
+    if idx.dtype not in ok or idx.dim() != 2 or not idx.is_contiguous():
+        raise ValueError("idx must be a contiguous (nElem, idxPerElem) " + (
+            "int32 or int64" if wide_ok else "int32") + " tensor")
     stride = math.prod(vtx.shape[1:]) * vtx.element_size()
     return int(vtx.shape[0]), int(stride), int(idx.shape[0]), int(idx.shape[1])
 
@@ -214,11 +223,12 @@ def reindex_mesh(vtx, idx, out_vtx=None, out_nVtx=None, out_idx=None, stream=Non
     """Asynchronously re-index one mesh on the GPU (workspace from the stream-ordered pool).
 
     vtx: CUDA tensor (nVtx, ...) with one vertex of 4, 8, 12, 16, 20, 24 or 32 bytes per row
-    (any dtype; the raw bits are the key).  idx: CUDA int32 tensor (nElem, k).  Returns (out_vtx, out_nVtx,
-    out_idx): out_vtx has min(nVtx, nElem*k) rows of which the first D = out_nVtx.item() are
-    valid; out_nVtx is a 1-element int64 CUDA tensor (negative status on a device error)."""
+    (any dtype; the raw bits are the key).  idx: CUDA int32 or int64 tensor (nElem, k) (int64:
+    reindex_mesh64).  Returns (out_vtx, out_nVtx, out_idx): out_vtx has min(nVtx, nElem*k) rows of
+    which the first D = out_nVtx.item() are valid; out_nVtx is a 1-element int64 CUDA tensor
+    (negative status on a device error); out_idx has idx's dtype."""
     torch = _torch()
-    n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx)
+    n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx, wide_ok=True)
     if not (vtx.is_cuda and idx.is_cuda):
         raise ValueError("vtx and idx must be CUDA tensors (use reindex_mesh_host for host buffers)")
     cap = min(n_vtx, n_elem * k)
@@ -228,8 +238,9 @@ def reindex_mesh(vtx, idx, out_vtx=None, out_nVtx=None, out_idx=None, stream=Non
         out_nVtx = torch.empty(1, dtype=torch.int64, device=vtx.device)
     if out_idx is None:
         out_idx = torch.empty_like(idx)
-    rc = lib().reindex_mesh(_ptr(vtx), n_vtx, S, _ptr(idx), n_elem, k, _ptr(out_vtx), _ptr(out_nVtx),
-                            _ptr(out_idx), _stream_handle(stream))
+    fn = lib().reindex_mesh64 if idx.dtype == torch.int64 else lib().reindex_mesh
+    rc = fn(_ptr(vtx), n_vtx, S, _ptr(idx), n_elem, k, _ptr(out_vtx), _ptr(out_nVtx), _ptr(out_idx),
+            _stream_handle(stream))
     if rc:
         raise ReindexError(rc, "reindex_mesh")
     return out_vtx, out_nVtx, out_idx
@@ -240,7 +251,7 @@ def reindex_mesh_ws(vtx, idx, ws, out_vtx=None, out_nVtx=None, out_idx=None, str
     reindex_workspace_size(...) bytes); performs no allocation, so it can be graph-captured
     when the outputs are preallocated."""
     torch = _torch()
-    n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx)
+    n_vtx, S, n_elem, k = _mesh_geometry(vtx, idx, wide_ok=True)
     cap = min(n_vtx, n_elem * k)
     if out_vtx is None:
         out_vtx = torch.empty((cap,) + tuple(vtx.shape[1:]), dtype=vtx.dtype, device=vtx.device)
@@ -248,8 +259,9 @@ def reindex_mesh_ws(vtx, idx, ws, out_vtx=None, out_nVtx=None, out_idx=None, str
         out_nVtx = torch.empty(1, dtype=torch.int64, device=vtx.device)
     if out_idx is None:
         out_idx = torch.empty_like(idx)
-    rc = lib().reindex_mesh_ws(_ptr(vtx), n_vtx, S, _ptr(idx), n_elem, k, _ptr(out_vtx), _ptr(out_nVtx),
-                               _ptr(out_idx), _ptr(ws), ws.numel() * ws.element_size(), _stream_handle(stream))
+    fn = lib().reindex_mesh64_ws if idx.dtype == torch.int64 else lib().reindex_mesh_ws
+    rc = fn(_ptr(vtx), n_vtx, S, _ptr(idx), n_elem, k, _ptr(out_vtx), _ptr(out_nVtx), _ptr(out_idx), _ptr(ws),
+            ws.numel() * ws.element_size(), _stream_handle(stream))
     if rc:
         raise ReindexError(rc, "reindex_mesh_ws")
     return out_vtx, out_nVtx, out_idx

@@ -70,7 +70,7 @@ std::string describe_tuning(const LaunchCfg& c) {
   const char* shapes[] = {",chunk=big", ",chunk=small", ",chunk=wide", ",chunk=deep"};
   d += shapes[c.chunk_cfg & 3];
   d += c.chunk_occ ? ",cocc=" + std::to_string(c.chunk_occ) : std::string(",cocc=max");
-  if (c.chunk_grid_cap > 0) d += ",cgrid=" + std::to_string(c.chunk_grid_cap);
+  d += ",cgrid=" + std::to_string(c.chunk_grid_cap);  // 0: no cap (always written, so specs round-trip)
   return d;
 }
 
@@ -193,12 +193,23 @@ static reindex_status check_args(int64_t nVtx, int S, int64_t nElem, int k, int6
   return REINDEX_OK;
 }
 
-static reindex_status check_ptrs(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t M,
-                                 const void* out_vtx, const int64_t* out_nVtx, const int32_t* out_idx) {
+// int64 indices: the same vertex limit; up to 2^40 index entries (nElem * idxPerElem).
+static reindex_status check_args64(int64_t nVtx, int S, int64_t nElem, int k, int64_t* M) {
+  if (S != 4 && S != 8 && S != 12 && S != 16 && S != 20 && S != 24 && S != 32) return REINDEX_ERR_UNSUPPORTED;
+  if (nVtx < 0 || nElem < 0 || k < 1) return REINDEX_ERR_INVALID_ARG;
+  if (nVtx > kMaxCount) return REINDEX_ERR_UNSUPPORTED;
+  if (nElem > (int64_t(1) << 40) / k) return REINDEX_ERR_UNSUPPORTED;
+  *M = nElem * (int64_t)k;
+  return REINDEX_OK;
+}
+
+static reindex_status check_ptrs(const void* vtx, int64_t nVtx, int S, const void* idx, int64_t M,
+                                 const void* out_vtx, const int64_t* out_nVtx, const void* out_idx,
+                                 uintptr_t idx_align = 4) {
   if (out_nVtx == nullptr || !aligned(out_nVtx, 8)) return REINDEX_ERR_INVALID_ARG;
   if (M == 0) return REINDEX_OK;
   if (!idx || !out_idx || !out_vtx || (nVtx > 0 && !vtx)) return REINDEX_ERR_INVALID_ARG;
-  if (!aligned(idx, 4) || !aligned(out_idx, 4)) return REINDEX_ERR_INVALID_ARG;
+  if (!aligned(idx, idx_align) || !aligned(out_idx, idx_align)) return REINDEX_ERR_INVALID_ARG;
   if ((nVtx > 0 && !aligned(vtx, vtx_alignment(S))) || !aligned(out_vtx, vtx_alignment(S)))
     return REINDEX_ERR_INVALID_ARG;
   return REINDEX_OK;
@@ -249,10 +260,28 @@ static cudaError_t sort_pass(int S, int d, const WsPtrs& p, const LaunchCfg& c, 
   return c.sort_kernel == kSortPipe ? launch_onesweep_pipe(S, d, p, c, st) : launch_onesweep(S, d, p, c, st);
 }
 
+// Index arrays of a call: int32 (every entry point but reindex_mesh64*) or int64.
+struct Indices {
+  const void* idx;
+  void* out;
+  bool wide;  // int64
+};
+
+static cudaError_t used_flags(const Indices& ix, int64_t M, int64_t nVtx, const WsPtrs& p, const LaunchCfg& c,
+                              cudaStream_t st) {
+  return ix.wide ? launch_used_flags64(static_cast<const int64_t*>(ix.idx), M, nVtx, p, c, st)
+                 : launch_used_flags(static_cast<const int32_t*>(ix.idx), M, nVtx, p, c, st);
+}
+
+static cudaError_t remap(const Indices& ix, int64_t M, const WsPtrs& p, const LaunchCfg& c, cudaStream_t st) {
+  return ix.wide ? launch_remap64(static_cast<const int64_t*>(ix.idx), static_cast<int64_t*>(ix.out), M, p, c, st)
+                 : launch_remap(static_cast<const int32_t*>(ix.idx), static_cast<int32_t*>(ix.out), M, p, c, st);
+}
+
 // The launch sequence (all on `st`, no host synchronisation).
-static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t M,
-                                   void* out_vtx, int64_t* out_nVtx, int32_t* out_idx, void* ws,
-                                   const WsLayout& L, cudaStream_t st, const PipeExtras* extra = nullptr) {
+static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const Indices& ix, int64_t M,
+                                   void* out_vtx, int64_t* out_nVtx, void* ws, const WsLayout& L, cudaStream_t st,
+                                   const PipeExtras* extra = nullptr) {
   LaunchCfg c = resolve_cfg(launch_cfg(S), S, L.Umax);  // one configuration for the whole call
   const WsPtrs p = ws_ptrs(ws, L);
   // Prefix sort first: items keep the 64 most significant varying key bits; the full-key sort
@@ -270,7 +299,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
   }
   if (!(extra && extra->flags_done)) {
     prof::Scope s(REINDEX_K_USED_FLAGS, -1, st);
-    REINDEX_TRY(launch_used_flags(idx, M, nVtx, pp, c, st));
+    REINDEX_TRY(used_flags(ix, M, nVtx, pp, c, st));
   }
   if (extra && extra->vtx_ready) REINDEX_TRY(cudaStreamWaitEvent(st, extra->vtx_ready, 0));
   if (prefix) {
@@ -310,7 +339,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
       REINDEX_TRY(launch_prefix_gate(pp, p, st));
     }
     prof::Scope s(REINDEX_K_USED_FLAGS, -1, st);
-    REINDEX_TRY(launch_used_flags(idx, M, nVtx, p, c, st));
+    REINDEX_TRY(used_flags(ix, M, nVtx, p, c, st));
     c.scatter_waves = 1;  // the full-key sort's passes: few CTAs, cheap when skipped
   }
   if (uses_plane(c.sort_kernel) && c.pack_keys) {  // bit masks -> plan (key packing) -> compaction
@@ -341,13 +370,19 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const i
   if (extra && extra->heads_done) REINDEX_TRY(cudaEventRecord(extra->heads_done, st));
   {
     prof::Scope s(REINDEX_K_REMAP, -1, st);
-    REINDEX_TRY(launch_remap(idx, out_idx, M, p, c, st));
+    REINDEX_TRY(remap(ix, M, p, c, st));
   }
   {
     prof::Scope s(REINDEX_K_FINALIZE, -1, st);
     REINDEX_TRY(launch_finalize(p, out_nVtx, st));
   }
   return REINDEX_OK;
+}
+
+static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const int32_t* idx, int64_t M,
+                                   void* out_vtx, int64_t* out_nVtx, int32_t* out_idx, void* ws,
+                                   const WsLayout& L, cudaStream_t st, const PipeExtras* extra = nullptr) {
+  return run_pipeline(vtx, nVtx, S, Indices{idx, out_idx, false}, M, out_vtx, out_nVtx, ws, L, st, extra);
 }
 
 // Workspace of the batched path: the single-mesh layout for (S + 4)-byte keys over all vertices
@@ -514,6 +549,51 @@ reindex_status reindex_mesh(const void* vtx, int64_t nVtx, int S, const int32_t*
   cudaError_t e = cudaMallocAsync(&ws, L.total, st);
   if (e != cudaSuccess) return cuda_status(e);
   r = run_pipeline(vtx, nVtx, S, idx, M, out_vtx, out_nVtx, out_idx, ws, L, st);
+  e = cudaFreeAsync(ws, st);
+  if (r == REINDEX_OK && e != cudaSuccess) r = cuda_status(e);
+  return r;
+}
+
+size_t reindex_workspace_size64(int64_t nVtx, int vtxStrideBytes, int64_t nElem, int idxPerElem) {
+  int64_t M = 0;
+  if (check_args64(nVtx, vtxStrideBytes, nElem, idxPerElem, &M) != REINDEX_OK) return 0;
+  WsLayout L;
+  L.compute(nVtx, vtxStrideBytes, M);
+  return L.total;
+}
+
+reindex_status reindex_mesh64_ws(const void* vtx, int64_t nVtx, int S, const int64_t* idx, int64_t nElem, int k,
+                                 void* out_vtx, int64_t* out_nVtx, int64_t* out_idx, void* ws, size_t wsBytes,
+                                 reindex_stream_t stream) {
+  int64_t M = 0;
+  reindex_status r = check_args64(nVtx, S, nElem, k, &M);
+  if (r != REINDEX_OK) return r;
+  if ((r = check_ptrs(vtx, nVtx, S, idx, M, out_vtx, out_nVtx, out_idx, 8)) != REINDEX_OK) return r;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (M == 0) return cuda_status(launch_set_count(out_nVtx, 0, st));
+  if (nVtx == 0) return REINDEX_ERR_INDEX_RANGE;
+  WsLayout L;
+  L.compute(nVtx, S, M);
+  if (ws == nullptr || !aligned(ws, 256) || wsBytes < L.total) return REINDEX_ERR_INVALID_ARG;
+  return run_pipeline(vtx, nVtx, S, Indices{idx, out_idx, true}, M, out_vtx, out_nVtx, ws, L, st);
+}
+
+reindex_status reindex_mesh64(const void* vtx, int64_t nVtx, int S, const int64_t* idx, int64_t nElem, int k,
+                              void* out_vtx, int64_t* out_nVtx, int64_t* out_idx, reindex_stream_t stream) {
+  int64_t M = 0;
+  reindex_status r = check_args64(nVtx, S, nElem, k, &M);
+  if (r != REINDEX_OK) return r;
+  if ((r = check_ptrs(vtx, nVtx, S, idx, M, out_vtx, out_nVtx, out_idx, 8)) != REINDEX_OK) return r;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (M == 0) return cuda_status(launch_set_count(out_nVtx, 0, st));
+  if (nVtx == 0) return REINDEX_ERR_INDEX_RANGE;
+  WsLayout L;
+  L.compute(nVtx, S, M);
+  set_pool_threshold();
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, L.total, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  r = run_pipeline(vtx, nVtx, S, Indices{idx, out_idx, true}, M, out_vtx, out_nVtx, ws, L, st);
   e = cudaFreeAsync(ws, st);
   if (r == REINDEX_OK && e != cudaSuccess) r = cuda_status(e);
   return r;

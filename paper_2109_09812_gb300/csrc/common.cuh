@@ -48,12 +48,24 @@ constexpr int kHistMasks = 4;     // no histograms: key bit masks and the plane 
                                   // (the "tiles" sort counts digits per pass itself)
 constexpr int kHistPrefix = 5;    // prefix sort: items carry the 64 most significant varying key bits
 
-// Look-back status word: 2-bit flag + 30-bit count.
-constexpr uint32_t kFlagAgg = 1u << 30;    // tile aggregate only
-constexpr uint32_t kFlagPre = 2u << 30;    // inclusive prefix through this tile
-constexpr uint32_t kFlagMask = 3u << 30;
-constexpr uint32_t kValMask = (1u << 30) - 1;
+// Look-back status word (one 32-bit word, zeroed before use):
+//   0                      not published yet;
+//   top bit clear, v > 0   the tile's aggregate only, v - 1 (an aggregate is at most a tile);
+//   top bit set            the inclusive prefix through the tile, in the low 31 bits.
+// Counts up to 2^31 - 1 fit, so meshes of up to INT32_MAX vertices can be re-indexed.
+constexpr uint32_t kPreBit = 1u << 31;
+constexpr uint32_t kValMask = kPreBit - 1;
 constexpr int64_t kMaxCount = (int64_t)kValMask;  // largest count a status word can carry
+__host__ __device__ constexpr uint32_t lb_agg(uint32_t count) { return count + 1u; }
+__host__ __device__ constexpr uint32_t lb_pre(uint32_t count) { return kPreBit | (count & kValMask); }
+__host__ __device__ constexpr bool lb_ready(uint32_t s) { return s != 0u; }
+__host__ __device__ constexpr bool lb_is_pre(uint32_t s) { return (s & kPreBit) != 0u; }
+__host__ __device__ constexpr uint32_t lb_val(uint32_t s) { return lb_is_pre(s) ? (s & kValMask) : s - 1u; }
+static_assert(!lb_ready(0u) && lb_ready(lb_agg(0)) && lb_ready(lb_pre(0)), "published statuses are non-zero");
+static_assert(lb_val(lb_agg(0)) == 0 && lb_val(lb_agg(65536)) == 65536 && !lb_is_pre(lb_agg(65536)), "aggregates");
+static_assert(lb_val(lb_pre(0)) == 0 && lb_val(lb_pre((uint32_t)kMaxCount)) == (uint32_t)kMaxCount &&
+                  lb_is_pre(lb_pre((uint32_t)kMaxCount)) && kMaxCount == 2147483647,
+              "inclusive prefixes up to INT32_MAX");
 
 // Bounded spin: every wait on another CTA gives up after this many polls, records
 // REINDEX_ERR_TIMEOUT and publishes a (meaningless) prefix so that no successor waits forever.
@@ -654,17 +666,17 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// Wait until *p carries a flag; bounded.  Returns the status word (flag + value), or on
-// timeout records the error and returns a prefix flag with value 0.  Failed polls back off
+// Wait until *p is published; bounded.  Returns the status word, or on timeout records the error
+// and returns a prefix of 0.  Failed polls back off
 // briefly so that waiting threads leave issue slots to the warps doing useful work.
 __device__ __forceinline__ uint32_t wait_status(const uint32_t* p, Control* c) {
   uint32_t s = ld_relaxed(p);
   uint32_t polls = 0;
-  while ((s & kFlagMask) == 0) {
+  while (!lb_ready(s)) {
     ++polls;
     if ((polls & 255u) == 0 && (polls >= kSpinLimit || ld_relaxed(&c->err) != 0)) {
       record_error(c, kErrTimeout);
-      return kFlagPre;
+      return lb_pre(0);
     }
     __nanosleep(polls < 4 ? 32 : 128);
     s = ld_relaxed(p);
@@ -688,21 +700,21 @@ __device__ __forceinline__ uint32_t warp_lookback(const uint32_t* lb, int64_t ti
 #pragma unroll
     for (int i = 0; i < W; ++i) {
       const int64_t q = hi - (int64_t)lane * W - i;
-      s[i] = q >= 0 ? ld_relaxed(lb + q * kLbPad) : kFlagPre;  // before tile 0: prefix 0
+      s[i] = q >= 0 ? ld_relaxed(lb + q * kLbPad) : lb_pre(0);  // before tile 0: prefix 0
     }
 #pragma unroll
     for (int i = 0; i < W; ++i) {
       const int64_t q = hi - (int64_t)lane * W - i;
-      if (q >= 0 && (s[i] & kFlagMask) == 0) s[i] = wait_status(lb + q * kLbPad, c);
+      if (q >= 0 && !lb_ready(s[i])) s[i] = wait_status(lb + q * kLbPad, c);
     }
     int stop = W;  // nearest predecessor of this lane carrying an inclusive prefix
 #pragma unroll
     for (int i = W - 1; i >= 0; --i)
-      if ((s[i] & kFlagMask) == kFlagPre) stop = i;
+      if (lb_is_pre(s[i])) stop = i;
     uint32_t part = 0;
 #pragma unroll
     for (int i = 0; i < W; ++i)
-      if (i <= stop) part += s[i] & kValMask;
+      if (i <= stop) part += lb_val(s[i]);
     const uint32_t pre_mask = __ballot_sync(0xffffffffu, stop < W);
     const int first = pre_mask ? __ffs(pre_mask) - 1 : 32;  // nearest lane with a prefix
     uint32_t v = lane <= first ? part : 0u;
@@ -734,14 +746,14 @@ __device__ __forceinline__ uint32_t warp_lookback_tiles(const uint32_t* lb, uint
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
       const int64_t q = top - 1 - (i * TPL + h);
-      v[i] = q >= 0 ? ld_relaxed(lb + (size_t)q * kRadix + d0 + dl) : kFlagPre;
+      v[i] = q >= 0 ? ld_relaxed(lb + (size_t)q * kRadix + d0 + dl) : lb_pre(0);
     }
     int mypos = 64;  // nearest predecessor (0 = tile top-1) carrying an inclusive prefix
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
       const int64_t q = top - 1 - (i * TPL + h);
-      if (q >= 0 && (v[i] & kFlagMask) == 0) v[i] = wait_status(lb + (size_t)q * kRadix + d0 + dl, c);
-      if ((v[i] & kFlagMask) == kFlagPre && mypos == 64) mypos = i * TPL + h;
+      if (q >= 0 && !lb_ready(v[i])) v[i] = wait_status(lb + (size_t)q * kRadix + d0 + dl, c);
+      if (lb_is_pre(v[i]) && mypos == 64) mypos = i * TPL + h;
     }
     int cut = mypos;
 #pragma unroll
@@ -749,7 +761,7 @@ __device__ __forceinline__ uint32_t warp_lookback_tiles(const uint32_t* lb, uint
     uint32_t sum = 0;
 #pragma unroll
     for (int i = 0; i < DPW; ++i)
-      if (i * TPL + h <= cut) sum += v[i] & kValMask;
+      if (i * TPL + h <= cut) sum += lb_val(v[i]);
 #pragma unroll
     for (int o = DPW; o < 32; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (!found) total += sum;

@@ -135,6 +135,11 @@ cudaError_t launch_seg_remap(int32_t* out_idx, int64_t M, const SegArgs& seg, Ws
                              cudaStream_t st);
 cudaError_t launch_remap(const int32_t* idx, int32_t* out_idx, int64_t M, WsPtrs ws, const LaunchCfg& c,
                          cudaStream_t st);
+// int64 indices (reindex_mesh64*): the same two steps on 8-byte indices.
+cudaError_t launch_used_flags64(const int64_t* idx, int64_t M, int64_t nVtx, WsPtrs ws, const LaunchCfg& c,
+                                cudaStream_t st);
+cudaError_t launch_remap64(const int64_t* idx, int64_t* out_idx, int64_t M, WsPtrs ws, const LaunchCfg& c,
+                           cudaStream_t st);
 cudaError_t launch_finalize(WsPtrs ws, int64_t* out_nVtx, cudaStream_t st);
 cudaError_t launch_gather_elements(const int32_t* idx, int k, int64_t nElem, const int32_t* list, int64_t nSel,
                                   int32_t* out, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);

@@ -127,11 +127,11 @@ __global__ void __launch_bounds__(kHeadThreads, (S >= 16 || SV > 0) ? 2 : 4)
       uint32_t prefix = 0;
       uint32_t* my = ws.lb_head + tile * kLbPad;
       if (tile == 0) {
-        if (lane == 0) st_relaxed(my, kFlagPre | total);
+        if (lane == 0) st_relaxed(my, lb_pre(total));
       } else {
-        if (lane == 0) st_relaxed(my, kFlagAgg | total);
+        if (lane == 0) st_relaxed(my, lb_agg(total));
         prefix = warp_lookback(ws.lb_head, tile, ctrl);
-        if (lane == 0) st_relaxed(my, kFlagPre | ((prefix + total) & kValMask));
+        if (lane == 0) st_relaxed(my, lb_pre(prefix + total));
       }
       if (lane == 0) {
         s_prefix = prefix;

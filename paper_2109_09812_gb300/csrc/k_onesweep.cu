@@ -92,11 +92,11 @@ __global__ void __launch_bounds__(kSortThreads, S >= 20 ? 1 : 2) k_onesweep(WsPt
     __syncthreads();
 
     // 3. per-digit tile count, aggregate publication, first look-back load, local digit start
-    uint32_t cnt = 0, s_prev = kFlagPre;
+    uint32_t cnt = 0, s_prev = lb_pre(0);
     if (digit_thread) {
 #pragma unroll
       for (int q = 0; q < kSortWarps; ++q) cnt += whist[q * kRadix + t];
-      st_relaxed(lb + (size_t)tile * kRadix + t, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
+      st_relaxed(lb + (size_t)tile * kRadix + t, tile == 0 ? lb_pre(cnt) : lb_agg(cnt));
       lb_next[(size_t)tile * kRadix + t] = 0;  // the next non-trivial pass uses the other area
       if (tile > 0) s_prev = ld_relaxed(lb + (size_t)(tile - 1) * kRadix + t);  // consumed after staging
     }
@@ -131,13 +131,13 @@ __global__ void __launch_bounds__(kSortThreads, S >= 20 ? 1 : 2) k_onesweep(WsPt
       uint32_t excl = 0;
       if (tile > 0) {
         uint32_t s = s_prev;
-        if ((s & kFlagMask) == 0) s = wait_status(lb + (size_t)(tile - 1) * kRadix + t, ctrl);
-        excl = s & kValMask;
-        for (int64_t q = (int64_t)tile - 2; (s & kFlagMask) != kFlagPre; --q) {
+        if (!lb_ready(s)) s = wait_status(lb + (size_t)(tile - 1) * kRadix + t, ctrl);
+        excl = lb_val(s);
+        for (int64_t q = (int64_t)tile - 2; !lb_is_pre(s); --q) {
           s = wait_status(lb + (size_t)q * kRadix + t, ctrl);
-          excl += s & kValMask;
+          excl += lb_val(s);
         }
-        st_relaxed(lb + (size_t)tile * kRadix + t, kFlagPre | ((excl + cnt) & kValMask));
+        st_relaxed(lb + (size_t)tile * kRadix + t, lb_pre(excl + cnt));
       }
       goff[t] = (int32_t)(gbase[t] + excl) - (int32_t)ts;
     }

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(Pipe<S>::kThreads, 1) k_onesweep_pipe(WsPtrs w
 #pragma unroll 8
       for (int q = 0; q < NW; ++q) cnt += whist[q * kRadix + t];
       tcnt[t] = cnt;
-      st_relaxed(lb + (size_t)cur * kRadix + t, (cur == 0 ? kFlagPre : kFlagAgg) | cnt);
+      st_relaxed(lb + (size_t)cur * kRadix + t, cur == 0 ? lb_pre(cnt) : lb_agg(cnt));
       lb_next[(size_t)cur * kRadix + t] = 0;  // the next non-trivial pass uses the other area
     }
     const uint32_t incl = warp_incl_scan(cnt);
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(Pipe<S>::kThreads, 1) k_onesweep_pipe(WsPtrs w
       const uint32_t excl = cur > 0 ? warp_lookback_tiles<DPW>(lb, cur, w * DPW, ctrl) : 0u;
       if (lane < DPW) {
         const int dd = w * DPW + lane;
-        if (cur > 0) st_relaxed(lb + (size_t)cur * kRadix + dd, kFlagPre | ((excl + tcnt[dd]) & kValMask));
+        if (cur > 0) st_relaxed(lb + (size_t)cur * kRadix + dd, lb_pre(excl + tcnt[dd]));
         goff[(k & 1) * kRadix + dd] = (int32_t)(gbase[dd] + excl) - (int32_t)tstart[dd];
       }
     }

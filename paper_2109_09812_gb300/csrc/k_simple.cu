@@ -66,6 +66,46 @@ __global__ void __launch_bounds__(kThreads) k_used_flags(const int32_t* idx, int
   if (bad) record_error(ctrl, kErrIndexRange);
 }
 
+// The same for int64 indices: any value outside [0, nVtx) -- negative or past the vertex array,
+// however large -- is an index-range error (no index is truncated to 32 bits).
+__device__ __forceinline__ void mark_used64(int64_t v, uint32_t nVtx, uint32_t* bitmask, bool& bad) {
+  if ((uint64_t)v >= (uint64_t)nVtx) {
+    bad = true;
+  } else {
+    atomicOr(bitmask + ((uint32_t)v >> 5), 1u << ((uint32_t)v & 31u));
+  }
+}
+
+template <bool kVec>
+__global__ void __launch_bounds__(kThreads) k_used_flags64(const int64_t* idx, int64_t M, uint32_t nVtx,
+                                                            uint32_t* bitmask, Control* ctrl) {
+  if (*(volatile const uint32_t*)&ctrl->err) return;
+  bool bad = false;
+  const int64_t t0 = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  int64_t done = 0;
+  if (kVec) {  // 16-byte vectors of two indices, kBatch vectors in flight per thread
+    const longlong2* v2 = reinterpret_cast<const longlong2*>(idx);
+    const int64_t n2 = M >> 1;
+    for (int64_t i = t0; i < n2; i += stride * kBatch) {
+      longlong2 q[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b)
+        if (i + b * stride < n2) q[b] = __ldcs(v2 + i + b * stride);
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        if (i + b * stride < n2) {
+          mark_used64(q[b].x, nVtx, bitmask, bad);
+          mark_used64(q[b].y, nVtx, bitmask, bad);
+        }
+      }
+    }
+    done = n2 << 1;
+  }
+  for (int64_t i = done + t0; i < M; i += stride) mark_used64(__ldcs(idx + i), nVtx, bitmask, bad);
+  if (bad) record_error(ctrl, kErrIndexRange);
+}
+
 // Digit offsets and pass plan (one CTA of 256 threads; thread t owns digit value t).
 // The radix-sort plan for the P byte positions of a P-byte key.  With upfront histograms
 // (onesweep sort): a byte is trivial if one value holds all U items; exclusive digit offsets from
@@ -299,6 +339,40 @@ __global__ void __launch_bounds__(kThreads) k_remap(const int32_t* idx, int32_t*
   for (int64_t i = done + t0; i < M; i += stride) out[i] = (int32_t)__ldg(o2n + idx[i]);
 }
 
+// out_idx[j] = oldToNew[idx[j]] for int64 indices (already range-checked by k_used_flags64).
+template <bool kVec>
+__global__ void __launch_bounds__(kThreads) k_remap64(const int64_t* idx, int64_t* out, int64_t M,
+                                                       const uint32_t* __restrict__ o2n, const Control* ctrl) {
+  const uint32_t err = ctrl->err;
+  if (err && err != kErrSkip) return;  // outputs are unspecified after a device-detected error
+  const int64_t t0 = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  int64_t done = 0;
+  if (kVec) {
+    const longlong2* in2 = reinterpret_cast<const longlong2*>(idx);
+    longlong2* out2 = reinterpret_cast<longlong2*>(out);
+    const int64_t n2 = M >> 1;
+    for (int64_t i = t0; i < n2; i += stride * kBatch) {
+      longlong2 q[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b)
+        if (i + b * stride < n2) q[b] = __ldcs(in2 + i + b * stride);
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        if (i + b * stride < n2) {
+          q[b].x = (long long)__ldg(o2n + q[b].x);
+          q[b].y = (long long)__ldg(o2n + q[b].y);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b)
+        if (i + b * stride < n2) __stcs(out2 + i + b * stride, q[b]);
+    }
+    done = n2 << 1;
+  }
+  for (int64_t i = done + t0; i < M; i += stride) out[i] = (int64_t)__ldg(o2n + idx[i]);
+}
+
 // Subset of a mesh (Section 3.4): out[s*k + q] = idx[list[s]*k + q] for the selected elements.
 __global__ void __launch_bounds__(kThreads) k_gather_elements(const int32_t* idx, int k, int64_t nElem,
                                                                const int32_t* list, int64_t nSel, int32_t* out,
@@ -356,6 +430,18 @@ cudaError_t launch_used_flags(const int32_t* idx, int64_t M, int64_t nVtx, WsPtr
   return cudaGetLastError();
 }
 
+cudaError_t launch_used_flags64(const int64_t* idx, int64_t M, int64_t nVtx, WsPtrs ws, const LaunchCfg& c,
+                                cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  const bool vec = (reinterpret_cast<uintptr_t>(idx) & 15) == 0;
+  const int g = grid_for(vec ? (M + 1) / 2 : M, c, 8);
+  if (vec)
+    k_used_flags64<true><<<g, kThreads, 0, st>>>(idx, M, (uint32_t)nVtx, ws.bitmask, ws.ctrl);
+  else
+    k_used_flags64<false><<<g, kThreads, 0, st>>>(idx, M, (uint32_t)nVtx, ws.bitmask, ws.ctrl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, bool allow_pack, cudaStream_t st) {
   k_sort_plan<<<1, kRadix, 0, st>>>(ws, S, from_masks ? 1 : 0, allow_pack ? 1 : 0, 0);
   return cudaGetLastError();
@@ -390,6 +476,18 @@ cudaError_t launch_remap(const int32_t* idx, int32_t* out_idx, int64_t M, WsPtrs
     k_remap<true><<<g, kThreads, 0, st>>>(idx, out_idx, M, ws.old2new, ws.ctrl);
   else
     k_remap<false><<<g, kThreads, 0, st>>>(idx, out_idx, M, ws.old2new, ws.ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_remap64(const int64_t* idx, int64_t* out_idx, int64_t M, WsPtrs ws, const LaunchCfg& c,
+                           cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  const bool vec = ((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(out_idx)) & 15) == 0;
+  const int g = grid_for(vec ? (M + 1) / 2 : M, c, 8);
+  if (vec)
+    k_remap64<true><<<g, kThreads, 0, st>>>(idx, out_idx, M, ws.old2new, ws.ctrl);
+  else
+    k_remap64<false><<<g, kThreads, 0, st>>>(idx, out_idx, M, ws.old2new, ws.ctrl);
   return cudaGetLastError();
 }
 

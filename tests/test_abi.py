@@ -68,8 +68,8 @@ def test_host_side_argument_checks(L):
     # negative sizes, zero arity
     assert L.reindex_mesh(fake, -1, 12, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_INVALID_ARG
     assert L.reindex_mesh(fake, 10, 12, fake, 3, 0, fake, fake, fake, z) == rx.REINDEX_ERR_INVALID_ARG
-    # too many vertices for 30-bit look-back counts; too many indices for int32
-    assert L.reindex_mesh(fake, 1 << 30, 12, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
+    # too many vertices for 31-bit look-back counts; too many indices for int32
+    assert L.reindex_mesh(fake, 1 << 31, 12, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
     assert L.reindex_mesh(fake, 10, 12, fake, 1 << 30, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
     # null output count, null idx
     assert L.reindex_mesh(fake, 10, 12, fake, 3, 3, fake, z, fake, z) == rx.REINDEX_ERR_INVALID_ARG
@@ -283,3 +283,22 @@ def test_noalloc_scratch_holds_the_largest_accepted_mesh(L):
             for n_elem in (1, max_vtx // k, max_vtx, 10 * max_vtx):
                 b = rx.reindex_workspace_size(max_vtx, S, n_elem, k)
                 assert 0 < b <= scratch, (S, k, n_elem, b, scratch)
+
+
+def test_int64_entry_points_host_checks(L):
+    """The int64-index entry points: same vertex limit, 8-byte aligned index arrays, no 2^31 cap on
+    the index count (the workspace grows with min(nVtx, indices) only)."""
+    z = ctypes.c_void_p(0)
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails its host checks
+    assert L.reindex_mesh64(fake, 1 << 31, 12, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
+    assert L.reindex_mesh64(fake, 10, 6, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
+    assert L.reindex_mesh64(fake, 10, 12, ctypes.c_void_p((1 << 20) + 4), 3, 3, fake, fake, fake, z) \
+        == rx.REINDEX_ERR_INVALID_ARG  # int64 indices must be 8-byte aligned
+    assert L.reindex_mesh64(fake, 10, 12, fake, (1 << 40) // 3 + 1, 3, fake, fake, fake, z) \
+        == rx.REINDEX_ERR_UNSUPPORTED
+    n = 1000
+    big = rx.lib().reindex_workspace_size64(n, 12, 1 << 33, 3)  # 2^33 elements: more than 2^31 indices
+    assert big == rx.reindex_workspace_size(n, 12, 1000, 3) > 0
+    assert rx.lib().reindex_workspace_size64((1 << 31) - 1, 4, 10, 3) > 0
+    assert rx.reindex_workspace_size((1 << 31) - 1, 4, 10, 3) > 0
+    assert rx.reindex_workspace_size(1 << 31, 4, 10, 3) == 0

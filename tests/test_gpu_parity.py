@@ -252,10 +252,12 @@ def test_host_buffer_variant_reports_device_errors(rx):
 
 
 SORT_KERNELS = {"regs": ["onesweep"], "tiles,pack=off": ["tile_count", "tile_offsets", "tile_scatter"],
-                "tiles,pack=on": ["tile_count", "tile_offsets", "tile_scatter", "key_masks"]}
+                "tiles,pack=on": ["tile_count", "tile_offsets", "tile_scatter", "key_masks"],
+                "chunk,pack=off": ["tile_count", "tile_offsets", "chunk_scatter"],
+                "chunk,pack=on": ["tile_count", "tile_offsets", "chunk_scatter", "key_masks"]}
 
 
-@pytest.mark.parametrize("sort", ["regs", "tiles,pack=off", "tiles,pack=on"])
+@pytest.mark.parametrize("sort", ["regs", "tiles,pack=off", "tiles,pack=on", "chunk,pack=off", "chunk,pack=on"])
 def test_profile_records_every_kernel(rx, sort):
     m = synth.config_mesh(1)
     v, i = to_dev(m.vtx, m.idx)

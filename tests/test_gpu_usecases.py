@@ -150,10 +150,15 @@ def test_autotune_keeps_results_exact_and_persists(rx, tmp_path):
     np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
     # explicit settings round-trip, and every variant stays exact
-    for spec in ["sort=pipe,rank=match,hist=peel,grid=tile,swaves=tile,pack=on,prefix=off",
-                 "sort=regs,rank=ballot,hist=match,grid=persist,swaves=4,pack=off,prefix=on",
-                 "sort=tiles,rank=ballot,hist=uniform,grid=persist,swaves=1,pack=off,prefix=auto",
-                 "sort=tiles,rank=vary,hist=uniform,grid=persist,swaves=tile,pack=on,prefix=off"]:
+    for spec in ["sort=pipe,rank=match,hist=peel,grid=tile,swaves=tile,pack=on,prefix=off,chunk=wide,cocc=max,cgrid=0",
+                 "sort=regs,rank=ballot,hist=match,grid=persist,swaves=4,pack=off,prefix=on,chunk=big,cocc=1,cgrid=0",
+                 "sort=tiles,rank=ballot,hist=uniform,grid=persist,swaves=1,pack=off,prefix=auto,chunk=small,cocc=max,"
+                 "cgrid=0",
+                 "sort=tiles,rank=vary,hist=uniform,grid=persist,swaves=tile,pack=on,prefix=off,chunk=deep,cocc=max,cgrid=0",
+                 "sort=chunk,rank=match,hist=uniform,grid=persist,swaves=tile,pack=on,prefix=off,chunk=wide,cocc=1,"
+                 "cgrid=4",
+                 "sort=chunk,rank=ballot,hist=uniform,grid=persist,swaves=tile,pack=off,prefix=auto,chunk=big,cocc=max,"
+                 "cgrid=0"]:
         rx.reindex_tuning_set(12, spec)
         assert rx.reindex_tuning_get(12) == spec
         out_v, out_n, out_i = rx.reindex_mesh(v, i)
