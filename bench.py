@@ -865,12 +865,15 @@ def run_ours(args, world, rank, local):
     kname, alg_bytes, avg_ms, item_bytes, n_sweeps = sort_pass_roofline(recs, U)
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
-    per_pass = {}
+    per_pass, count_pass = {}, {}
     for r in recs:
         if r["name"] == kname and not r["skipped"]:
             per_pass.setdefault(f'{r["digit"]}/{r["item_bytes"]}B', []).append(r["ms"])
+        if r["name"] == "tile_count" and not r["skipped"]:
+            count_pass.setdefault(f'{r["digit"]}/{r["item_bytes"]}B', []).append(r["ms"])
     roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "per_pass_ms": {d: round(sum(v) / len(v), 4) for d, v in sorted(per_pass.items())},
+                "count_per_pass_ms": {d: round(sum(v) / len(v), 4) for d, v in sorted(count_pass.items())},
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                 "traffic": ncu_traffic(kname, args.workload, item_bytes), "algorithmic_bytes_per_launch": alg_bytes,
                 "item_bytes": item_bytes, "avg_launch_ms": avg_ms, "passes_per_step": n_sweeps / args.steps}

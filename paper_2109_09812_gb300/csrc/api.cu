@@ -41,6 +41,10 @@ void apply_tuning(LaunchCfg& c, const char* spec) {
   if (std::strstr(spec, "cocc=1")) c.chunk_occ = 1;
   if (std::strstr(spec, "cocc=2")) c.chunk_occ = 2;
   if (const char* g = std::strstr(spec, "cgrid=")) c.chunk_grid_cap = std::atoi(g + 6);
+  if (const char* g = std::strstr(spec, "dbits=")) {
+    const int b = std::atoi(g + 6);
+    if (b >= 6 && b <= 8) c.digit_bits = b;
+  }
   if (std::strstr(spec, "rank=match")) c.rank_mode = kRankMatchAny;
   if (std::strstr(spec, "rank=ballot")) c.rank_mode = kRankBallot;
   if (std::strstr(spec, "rank=vary")) c.rank_mode = kRankBallotVary;
@@ -71,6 +75,7 @@ std::string describe_tuning(const LaunchCfg& c) {
   d += shapes[c.chunk_cfg & 3];
   d += c.chunk_occ ? ",cocc=" + std::to_string(c.chunk_occ) : std::string(",cocc=max");
   d += ",cgrid=" + std::to_string(c.chunk_grid_cap);  // 0: no cap (always written, so specs round-trip)
+  d += ",dbits=" + std::to_string(c.digit_bits);
   return d;
 }
 
@@ -314,14 +319,14 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const I
     }
     {
       prof::Scope s(REINDEX_K_SORT_PLAN, -1, st);
-      REINDEX_TRY(launch_prefix_plan(S, pp, st));
+      REINDEX_TRY(launch_prefix_plan(S, pp, st, cp.digit_bits));
     }
     {
       prof::Scope s(REINDEX_K_COMPACT, -1, st);
       REINDEX_TRY(launch_compact_prefix(S, vtx, nVtx, pp, L.tilesV, c, st));
     }
     const uint8_t* pskip = prof::skip_buffer(pp.plan, st);
-    for (int d = 0; d < kPrefixBytes; ++d) REINDEX_TRY(sort_pass(kPrefixItem, d, pp, cp, st, pskip));
+    for (int d = 0; d < prefix_passes(cp.digit_bits); ++d) REINDEX_TRY(sort_pass(kPrefixItem, d, pp, cp, st, pskip));
     {
       prof::Scope s(REINDEX_K_HEAD_SCAN, -1, st);
       REINDEX_TRY(launch_head_scan_prefix(S, pp, vtx, out_vtx, out_nVtx, (uint32_t)nVtx, c, st));
@@ -349,7 +354,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const I
     }
     {
       prof::Scope s(REINDEX_K_SORT_PLAN, -1, st);
-      REINDEX_TRY(launch_sort_plan(S, p, true, true, st));
+      REINDEX_TRY(launch_sort_plan(S, p, true, true, st, c.digit_bits));
     }
     prof::Scope s(REINDEX_K_COMPACT, -1, st);
     REINDEX_TRY(launch_compact(S, vtx, nVtx, p, L.tilesV, c, nullptr, st));
@@ -362,7 +367,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const I
     REINDEX_TRY(launch_sort_plan(S, p, uses_plane(c.sort_kernel), false, st));
   }
   const uint8_t* skip = prof::skip_buffer(p.plan, st);
-  for (int d = 0; d < L.P; ++d) REINDEX_TRY(sort_pass(S, d, p, c, st, skip));
+  for (int d = 0; d < sort_passes(S, c.digit_bits); ++d) REINDEX_TRY(sort_pass(S, d, p, c, st, skip));
   {
     prof::Scope s(REINDEX_K_HEAD_SCAN, -1, st);
     REINDEX_TRY(launch_head_scan(S, p, out_vtx, out_nVtx, (uint32_t)nVtx, c, nullptr, st));
@@ -441,7 +446,7 @@ static reindex_status run_batched(const void* vtx, int64_t nVtx, int S, const in
     }
     {
       prof::Scope sc(REINDEX_K_SORT_PLAN, -1, st);
-      REINDEX_TRY(launch_sort_plan(S + 4, p, true, true, st));
+      REINDEX_TRY(launch_sort_plan(S + 4, p, true, true, st, c.digit_bits));
     }
     prof::Scope sc(REINDEX_K_COMPACT, -1, st);
     REINDEX_TRY(launch_compact(S, vtx, nVtx, p, SL.L.tilesV, cc, &seg, st));
@@ -454,7 +459,7 @@ static reindex_status run_batched(const void* vtx, int64_t nVtx, int S, const in
     REINDEX_TRY(launch_sort_plan(S + 4, p, uses_plane(c.sort_kernel), false, st));
   }
   const uint8_t* skip = prof::skip_buffer(p.plan, st);
-  for (int d = 0; d < S + 4; ++d) REINDEX_TRY(sort_pass(S + 4, d, p, c, st, skip));
+  for (int d = 0; d < sort_passes(S + 4, c.digit_bits); ++d) REINDEX_TRY(sort_pass(S + 4, d, p, c, st, skip));
   {
     prof::Scope sc(REINDEX_K_HEAD_SCAN, -1, st);
     REINDEX_TRY(launch_head_scan(S + 4, p, out_vtx, total, (uint32_t)nVtx, c, &seg, st));

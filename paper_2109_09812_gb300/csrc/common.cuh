@@ -22,7 +22,7 @@ constexpr int kHeadThreads = 256;          // threads per CTA of the head scan
 constexpr int kHeadIpt = 8;                // items per thread in the head scan
 constexpr int kHeadTile = kHeadThreads * kHeadIpt;         // 2048 items per tile
 constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;    // 256 digit values
+constexpr int kRadix = 1 << kRadixBits;    // 256 digit values (narrower digits use the low bins)
 constexpr int kMaxDigits = 32;             // 32-byte keys -> 32 byte digits
 constexpr int kPrefixBytes = 8;           // prefix sort: keys cut to their 64 most significant varying bits,
 constexpr int kPrefixItem = 12;           // held in 12-byte item keys (word 0 zero: 16-byte records)
@@ -129,7 +129,8 @@ struct Plan {                // written by the sort-plan kernel
   int8_t first;              // the first non-trivial digit, or -1
   uint8_t plane_first;       // tiles sort: the compaction's digit plane holds the first pass's digit
                              // (else key byte 0)
-  uint8_t pad[10];
+  uint8_t dbits;             // digit width: 8 (key bytes), or 6 / 7 bits of a packed key (chunk sort)
+  uint8_t pad[9];
   uint8_t vary[kMaxDigits];  // bits of digit d that differ between items (the others are constant)
   uint8_t pad2[12];
   KeyPack pack;                      // packing of the keys (pack.on == 0: not packed)
@@ -161,7 +162,7 @@ struct WsLayout {
     tilesH = (Umax + kHeadTile - 1) / kHeadTile;
     size_t o = 0;
     off_ctrl = o;        o += sizeof(Control);
-    off_hist = o;        o = align_up(o + (size_t)P * kRadix * 4, 256);
+    off_hist = o;        o = align_up(o + (size_t)kMaxDigits * kRadix * 4, 256);  // a row per pass
     off_lb_compact = o;  o = align_up(o + (size_t)tilesV * 4 * kLbPad, 256);
     off_lb_head = o;     o = align_up(o + (size_t)tilesH * 4 * kLbPad, 256);
     off_lb_sort = o;     o = align_up(o + (size_t)2 * tilesS * kRadix * 4, 256);
@@ -196,7 +197,7 @@ constexpr size_t ws_bytes(int64_t n, int s, int64_t m) {
 // Device views of the workspace, passed by value to the kernels.
 struct WsPtrs {
   Control* ctrl;
-  uint32_t* hist;        // [P][256]
+  uint32_t* hist;        // [kMaxDigits][256]: digit totals of each pass
   uint32_t* lb_compact;  // [tilesV * kLbPad]: status of tile q at q * kLbPad
   uint32_t* lb_head;     // [tilesH * kLbPad]
   uint32_t* lb_sort;     // [2][tilesS][256]

@@ -35,6 +35,9 @@ struct LaunchCfg {
                                 // (4096-item tiles, 1024 threads)
   int chunk_occ = 0;            // "chunk" sort: resident CTAs per SM to launch (0: as many as fit)
   int occ_chunk[4] = {0, 0, 0, 0};  // resident CTAs per SM of the chunk scatter, per tile shape
+  int digit_bits = 8;           // "chunk" sort: radix digit width, 6, 7 or 8 bits (narrower digits take
+                                // bit fields of the packed key: more passes, fewer ballots per pass,
+                                // longer output runs); every other sort uses 8
   int chunk_grid_cap = 0;       // "chunk" sort: at most this many chunks (0: no cap; small caps give
                                 // every CTA many tiles, e.g. to test the pipeline on small meshes)
 };
@@ -54,6 +57,8 @@ inline LaunchCfg resolve_cfg(LaunchCfg c, int S, int64_t Umax, bool batched = fa
     c.rank_mode = kRankBallotVary;
   }
   if (c.sort_kernel == kSortAuto) c.sort_kernel = Umax >= kTilesMinItems ? kSortChunk : kSortRegs;
+  if (c.sort_kernel != kSortChunk || c.digit_bits < 6 || c.digit_bits > 8) c.digit_bits = 8;
+  if (c.digit_bits < 8) c.pack_keys = 1;  // narrower digits are bit fields of the packed key
   if (c.pack_keys < 0) c.pack_keys = (batched || S <= 8) ? 1 : 0;
   if (batched || S <= kPrefixBytes)
     c.prefix = 0;
@@ -95,11 +100,16 @@ cudaError_t launch_used_flags(const int32_t* idx, int64_t M, int64_t nVtx, WsPtr
 cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
                            const SegArgs* seg, cudaStream_t st);
 // from_masks: trivial passes from the key bit masks (the "tiles" sort takes no upfront histograms).
-cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, bool allow_pack, cudaStream_t st);
+// dbits < 8: digits of dbits bits of the packed key (chunk sort only; packing is forced).
+cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, bool allow_pack, cudaStream_t st, int dbits = 8);
+// Radix passes the host launches for keyBytes-byte keys at a digit width (passes past the plan's
+// last digit exit at once), and for the prefix sort's 64-bit prefixes.
+int sort_passes(int keyBytes, int dbits);
+inline int prefix_passes(int dbits) { return dbits >= 8 ? kPrefixBytes : (8 * kPrefixBytes + dbits - 1) / dbits; }
 // Prefix sort (single meshes, S > 8): the plan keeping the 64 most significant varying key bits,
 // the compaction into (prefix, old index) items, the head scan that checks whole keys, and the
 // gate that skips the full-key sort unless two different keys shared a prefix.
-cudaError_t launch_prefix_plan(int S, WsPtrs ws, cudaStream_t st);
+cudaError_t launch_prefix_plan(int S, WsPtrs ws, cudaStream_t st, int dbits = 8);
 cudaError_t launch_compact_prefix(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int64_t tilesV, const LaunchCfg& c,
                                   cudaStream_t st);
 cudaError_t launch_head_scan_prefix(int S, WsPtrs ws, const void* vtx, void* out_vtx, int64_t* out_nVtx,

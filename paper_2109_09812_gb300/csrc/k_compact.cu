@@ -41,10 +41,12 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ KeyPack s_pack;
   __shared__ int s_first;
+  __shared__ uint32_t s_dmask;
   Control* ctrl = ws.ctrl;
   if (kPacks && threadIdx.x == 0) {
     s_pack = ws.plan->pack;
     s_first = ws.plan->first;
+    s_dmask = (1u << ws.plan->dbits) - 1u;  // the first digit: the packed key's low dbits bits
   }
   if (block_error(ctrl)) return;  // an invalid index was seen: nothing downstream is meaningful
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -156,7 +158,9 @@ __global__ void __launch_bounds__(kThreads) k_compact(const void* __restrict__ v
             else
               pack_key<K>(it.k, s_pack);
           }
-          if (first >= 0) ws.digits[obase + pos[r]] = (uint8_t)(key_word<K>(it.k, fword) >> fshift);
+          if (first >= 0)
+            ws.digits[obase + pos[r]] =
+                (uint8_t)((key_word<K>(it.k, fword) >> fshift) & (kPacks ? s_dmask : 0xFFu));
         }
         if constexpr (kMasks) {
 #pragma unroll

@@ -165,16 +165,17 @@ __device__ __forceinline__ void chunk_item(const unsigned char* buf, int i, Item
 // with equal digits from the digit matcher, each group counted into the warp's histogram in row
 // order (rank = the warp's earlier count of that digit + lanes below with the same digit).
 template <int S, int kMode, int T, int NT, int NB, bool kFull>
-__device__ __forceinline__ void chunk_rank(const unsigned char* cb, int n, int w, int lane, int word, int shift,
+__device__ __forceinline__ void chunk_rank(const unsigned char* cb, int n, int w, int lane, const DigitLoc& dl,
                                            uint32_t vary, uint32_t* wh, uint32_t (&dig)[T / NT],
                                            uint32_t (&rk)[T / NT]) {
   using P = ChunkSmem<S, T, NT, NB>;
   constexpr int R = T / NT;
-  const unsigned char* base = cb + (size_t)(w * R * 32 + lane) * P::stride + 4 * word;
+  const unsigned char* base = cb + (size_t)(w * R * 32 + lane) * P::stride + 4 * dl.word;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const bool valid = kFull || (w * R + r) * 32 + lane < n;
-    dig[r] = valid ? (*reinterpret_cast<const uint32_t*>(base + (size_t)r * 32 * P::stride) >> shift) & 0xFFu : 0u;
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(base + (size_t)r * 32 * P::stride);
+    dig[r] = valid ? digit_from(q[0], dl.straddle ? q[-1] : 0u, dl) : 0u;
     const uint32_t peers = match_digit<kMode, kFull>(dig[r], valid, vary);
     const uint32_t lt = peers & lanemask_lt();
     uint32_t old = 0;
@@ -188,7 +189,7 @@ __device__ __forceinline__ void chunk_rank(const unsigned char* cb, int n, int w
 template <int S, int T, int NT, bool kFull>
 __device__ __forceinline__ void chunk_write(const unsigned char* cb, const uint32_t* inv, const uint32_t* goff, int n,
                                             int t, uint32_t U, unsigned char* dst, const WsPtrs& ws, int nd,
-                                            int nword, int nshift, Control* ctrl) {
+                                            const DigitLoc& ndl, Control* ctrl) {
   constexpr int K = S / 4, R = T / NT;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -200,7 +201,7 @@ __device__ __forceinline__ void chunk_write(const unsigned char* cb, const uint3
       const uint32_t gpos = goff[e & 0xFFu] + (uint32_t)i;
       if (gpos < U) {
         ItemIO<S>::store(dst, ws.idoff, (int64_t)gpos, o);
-        if (nd >= 0) ws.digits[gpos] = (uint8_t)(key_word<K>(o.k, nword) >> nshift);
+        if (nd >= 0) ws.digits[gpos] = (uint8_t)key_digit_loc<K>(o.k, ndl);
       } else {
         record_error(ctrl, kErrInternal);  // counts/ranking inconsistency: never write out of range
       }
@@ -233,8 +234,7 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_scatter(WsPtrs ws, int d, in
   const unsigned char* src = pi.src ? ws.itemsB : ws.itemsA;
   unsigned char* dst = pi.src ? ws.itemsA : ws.itemsB;
   const int nd = (int)pi.next;
-  const int nword = nd >= 0 ? K - 1 - (nd >> 2) : 0, nshift = nd >= 0 ? (nd & 3) * 8 : 0;
-  const int word = K - 1 - (d >> 2), shift = (d & 3) * 8;
+  const DigitLoc dl = digit_loc<K>(d, pi.bits), ndl = digit_loc<K>(nd >= 0 ? nd : 0, pi.bits);
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const bool digit_thread = t < kRadix;
   if (digit_thread) run[t] = ws.lb_sort[(size_t)t * G + blockIdx.x];  // the chunk's offset of digit t
@@ -260,9 +260,9 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_scatter(WsPtrs ws, int d, in
     __syncwarp();
     uint32_t dig[R], rk[R];
     if (n == T)
-      chunk_rank<S, kMode, T, NT, NB, true>(cb, n, w, lane, word, shift, pi.vary, wh, dig, rk);
+      chunk_rank<S, kMode, T, NT, NB, true>(cb, n, w, lane, dl, pi.vary, wh, dig, rk);
     else
-      chunk_rank<S, kMode, T, NT, NB, false>(cb, n, w, lane, word, shift, pi.vary, wh, dig, rk);
+      chunk_rank<S, kMode, T, NT, NB, false>(cb, n, w, lane, dl, pi.vary, wh, dig, rk);
     __syncthreads();
 
     // 2. tile counts -> tile-local digit starts -> per-(warp, digit) starts; output offsets
@@ -301,9 +301,9 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_scatter(WsPtrs ws, int d, in
     // 4. write out in digit order (consecutive threads write consecutive slots of a digit run),
     //    with the next pass's digit into the byte plane
     if (n == T)
-      chunk_write<S, T, NT, true>(cb, inv, goff, n, t, U, dst, ws, nd, nword, nshift, ctrl);
+      chunk_write<S, T, NT, true>(cb, inv, goff, n, t, U, dst, ws, nd, ndl, ctrl);
     else
-      chunk_write<S, T, NT, false>(cb, inv, goff, n, t, U, dst, ws, nd, nword, nshift, ctrl);
+      chunk_write<S, T, NT, false>(cb, inv, goff, n, t, U, dst, ws, nd, ndl, ctrl);
     __syncthreads();  // buffer b and inv are free
 
     // 5. start the copy of the tile NB ahead into the freed buffer
@@ -338,17 +338,18 @@ struct ChunkCfg<S, 3> {
   static constexpr int T = S + 4 <= 20 ? 4096 : 2048, NT = 1024, NB = 2, MINB = 1;
 };
 
-// Digit matching: 8 ballots (or match.any) for keys up to 12 bytes, ballots on the varying digit
-// bits only for wider keys (the per-stride defaults of the other radix passes).
+// Digit matching: for keys up to 12 bytes 8 ballots, match.any, or ballots on the varying digit
+// bits only (the one that skips the ballots of bits a narrower digit does not have); wider keys
+// always the last (the per-stride default of the other radix passes).
 template <int S>
-constexpr int chunk_mode(bool match) {
-  return S >= 16 ? kRankBallotVary : (match ? kRankMatchAny : kRankBallot);
+constexpr int chunk_mode(int mode) {
+  return S >= 16 ? kRankBallotVary : mode;
 }
 
-template <int S, int C, bool kMatch = false>
+template <int S, int C, int kMode = kRankBallot>
 static auto chunk_kernel() {
   using F = ChunkCfg<S, C>;
-  return k_chunk_scatter<S, chunk_mode<S>(kMatch), F::T, F::NT, F::NB, F::MINB>;
+  return k_chunk_scatter<S, chunk_mode<S>(kMode), F::T, F::NT, F::NB, F::MINB>;
 }
 
 template <int S, int C>
@@ -360,8 +361,9 @@ static size_t chunk_smem() {
 template <int S, int C>
 static int chunk_occ_one() {
   int best = 0;
-  for (int m = 0; m < (S <= 12 ? 2 : 1); ++m) {  // both matchers for keys up to 12 bytes
-    auto k = m ? chunk_kernel<S, C, true>() : chunk_kernel<S, C, false>();
+  for (int m = 0; m < (S <= 12 ? 3 : 1); ++m) {  // every matcher for keys up to 12 bytes
+    auto k = m == 0 ? chunk_kernel<S, C, kRankBallot>()
+                    : (m == 1 ? chunk_kernel<S, C, kRankMatchAny>() : chunk_kernel<S, C, kRankBallotVary>());
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chunk_smem<S, C>()) != cudaSuccess)
       return 0;
     int n = 0;
@@ -425,34 +427,38 @@ cudaError_t launch_chunk_count(int S, int digit, WsPtrs ws, int G, int T, cudaSt
 }
 
 template <int S, int C>
-static cudaError_t scatter_c(bool match, int G, int digit, WsPtrs ws, cudaStream_t st) {
-  if (S <= 12 && match)
-    return launch_pdl(chunk_kernel<S, C, true>(), G, ChunkCfg<S, C>::NT, chunk_smem<S, C>(), st, ws, digit, G);
-  return launch_pdl(chunk_kernel<S, C, false>(), G, ChunkCfg<S, C>::NT, chunk_smem<S, C>(), st, ws, digit, G);
+static cudaError_t scatter_c(int mode, int G, int digit, WsPtrs ws, cudaStream_t st) {
+  constexpr int NT = ChunkCfg<S, C>::NT;
+  if (S <= 12 && mode == kRankMatchAny)
+    return launch_pdl(chunk_kernel<S, C, kRankMatchAny>(), G, NT, chunk_smem<S, C>(), st, ws, digit, G);
+  if (S <= 12 && mode == kRankBallotVary)
+    return launch_pdl(chunk_kernel<S, C, kRankBallotVary>(), G, NT, chunk_smem<S, C>(), st, ws, digit, G);
+  return launch_pdl(chunk_kernel<S, C, kRankBallot>(), G, NT, chunk_smem<S, C>(), st, ws, digit, G);
 }
 
 template <int S>
-static cudaError_t scatter_s(int cfg, bool match, int G, int digit, WsPtrs ws, cudaStream_t st) {
+static cudaError_t scatter_s(int cfg, int mode, int G, int digit, WsPtrs ws, cudaStream_t st) {
   switch (cfg) {
-    case 1: return scatter_c<S, 1>(match, G, digit, ws, st);
-    case 2: return scatter_c<S, 2>(match, G, digit, ws, st);
-    case 3: return scatter_c<S, 3>(match, G, digit, ws, st);
-    default: return scatter_c<S, 0>(match, G, digit, ws, st);
+    case 1: return scatter_c<S, 1>(mode, G, digit, ws, st);
+    case 2: return scatter_c<S, 2>(mode, G, digit, ws, st);
+    case 3: return scatter_c<S, 3>(mode, G, digit, ws, st);
+    default: return scatter_c<S, 0>(mode, G, digit, ws, st);
   }
 }
 
 cudaError_t launch_chunk_scatter(int S, int digit, WsPtrs ws, const LaunchCfg& c, int G, cudaStream_t st) {
   if (ws.Umax < 1) return cudaSuccess;
   const int cfg = c.chunk_cfg;
-  const bool match = c.rank_mode == kRankMatchAny;
+  // narrower digits: ballots on the digit's bits only
+  const int mode = (c.digit_bits < 8 && c.rank_mode == kRankBallot) ? kRankBallotVary : c.rank_mode;
   switch (S) {
-    case 4: return scatter_s<4>(cfg, match, G, digit, ws, st);
-    case 8: return scatter_s<8>(cfg, match, G, digit, ws, st);
-    case 12: return scatter_s<12>(cfg, match, G, digit, ws, st);
-    case 16: return scatter_s<16>(cfg, match, G, digit, ws, st);
-    case 20: return scatter_s<20>(cfg, match, G, digit, ws, st);
-    case 24: return scatter_s<24>(cfg, match, G, digit, ws, st);
-    case 32: return scatter_s<32>(cfg, match, G, digit, ws, st);
+    case 4: return scatter_s<4>(cfg, mode, G, digit, ws, st);
+    case 8: return scatter_s<8>(cfg, mode, G, digit, ws, st);
+    case 12: return scatter_s<12>(cfg, mode, G, digit, ws, st);
+    case 16: return scatter_s<16>(cfg, mode, G, digit, ws, st);
+    case 20: return scatter_s<20>(cfg, mode, G, digit, ws, st);
+    case 24: return scatter_s<24>(cfg, mode, G, digit, ws, st);
+    case 32: return scatter_s<32>(cfg, mode, G, digit, ws, st);
     default: return cudaErrorInvalidValue;
   }
 }

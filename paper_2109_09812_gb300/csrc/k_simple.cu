@@ -5,6 +5,7 @@
 //                 trivial (digit constant over all items) and the buffer each pass reads
 //   k_remap       Section 2.4: out_idx[j] = oldToNew[idx[j]]
 //   k_finalize    propagate a device-detected error into *out_nVtx and the sticky word
+#include <algorithm>
 #include <cstring>
 
 #include "internal.h"
@@ -165,11 +166,15 @@ __host__ __device__ void plan_prefix_pack(const uint32_t* kor, const uint32_t* k
   nbits = pos;
 }
 
+// dbits: digit width when the keys are packed (8; 6 or 7 for the chunk sort: digit d is then bits
+// [d * dbits, (d + 1) * dbits) of the packed key); npass: the passes the host launches (>= P when
+// digits are narrower than bytes).
 __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from_masks, int allow_pack,
-                                                      int prefix_words) {
+                                                      int prefix_words, int dbits, int npass) {
   __shared__ uint32_t s_warp[kRadix / 32];
   __shared__ uint32_t s_or[kRadix / 32], s_and[kRadix / 32];
-  __shared__ int s_np;  // bytes of the packed key, or -1 (keys not packed)
+  __shared__ int s_np;  // digits of the packed key, or -1 (keys not packed)
+  __shared__ int s_b;   // digit width
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const uint32_t U = ws.ctrl->U;
   Plan* plan = ws.plan;
@@ -183,18 +188,19 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from
       plan->first = -1;
       plan->pack.on = 0;
       plan->U = 0;
+      plan->dbits = 8;
     }
     return;
   }
   if (t == 0) {
-    int np = -1;
+    int np = -1, b = dbits;
     plan->pack.on = 0;
     if (prefix_words > 0) {
       KeyPack kp;
       int nbits = 0;
       plan_prefix_pack(ws.ctrl->kor, ws.ctrl->knand, prefix_words, kp, nbits);
       plan->pack = kp;
-      np = (nbits + 7) / 8;
+      np = (nbits + b - 1) / b;
     } else if (from_masks && allow_pack) {
       KeyPack kp{};
       int pos = 0, nraw = 0;
@@ -230,27 +236,41 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from
         kp.wlen[wd] = runs_here == 1 ? kp.len[first_run] : 0;
       }
       kp.nbits = (uint8_t)pos;
-      const int packed = (pos + 7) / 8;
-      if (allow_pack && fits && packed < nraw) {  // packing saves at least one pass
+      const int packed = (pos + b - 1) / b;
+      // packing when it saves at least one pass; always for digits narrower than bytes (else they
+      // fall back to bytes of the unpacked key)
+      if (allow_pack && fits && (b < 8 || packed < nraw)) {
         kp.on = 1;
         plan->pack = kp;
         np = packed;
+      } else {
+        b = 8;
       }
+    } else {
+      b = 8;
+    }
+    if (np > npass) {  // cannot happen for the pass counts the host launches; keep the passes exact
+      np = -1;
+      b = 8;
+      plan->pack.on = 0;
     }
     s_np = np;
+    s_b = b;
+    plan->dbits = (uint8_t)b;
   }
   __syncthreads();
   const int np = s_np;
-  const uint32_t nbits = np >= 0 ? plan->pack.nbits : 0u;
+  const uint32_t nbits = np >= 0 ? plan->pack.nbits : 0u, b = (uint32_t)s_b;
   uint32_t sel = 0, q = 0;  // identical in every thread
-  for (int d = 0; d < P; ++d) {
+  const int nloop = np >= 0 ? npass : P;  // byte digits of the unpacked key, or the packed key's digits
+  for (int d = 0; d < nloop; ++d) {
     const uint32_t c = ws.hist[d * kRadix + t];
     // A digit whose value is the same for all U items: that pass is the identity.
     int trivial;
     uint32_t vary;  // digit bits that are not the same in every item
     if (from_masks && np >= 0) {
       trivial = d >= np;
-      vary = trivial ? 0u : ((d == np - 1 && (nbits & 7u)) ? (1u << (nbits & 7u)) - 1u : 0xFFu);
+      vary = trivial ? 0u : ((d == np - 1 && (nbits % b)) ? (1u << (nbits % b)) - 1u : (1u << b) - 1u);
       __syncthreads();
     } else if (from_masks) {
       const int q = P / 4 - 1 - (d >> 2);
@@ -287,7 +307,7 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from
     }
   }
   if (t == 0) {
-    for (int d = P; d < kMaxDigits; ++d) plan->skip[d] = 1;
+    for (int d = nloop; d < kMaxDigits; ++d) plan->skip[d] = 1;
     int nxt = -1;
     for (int d = kMaxDigits - 1; d >= 0; --d) {
       plan->next[d] = (int8_t)nxt;
@@ -442,13 +462,16 @@ cudaError_t launch_used_flags64(const int64_t* idx, int64_t M, int64_t nVtx, WsP
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, bool allow_pack, cudaStream_t st) {
-  k_sort_plan<<<1, kRadix, 0, st>>>(ws, S, from_masks ? 1 : 0, allow_pack ? 1 : 0, 0);
+int sort_passes(int keyBytes, int dbits) { return dbits >= 8 ? keyBytes : std::min(kMaxDigits, (8 * keyBytes + dbits - 1) / dbits); }
+
+cudaError_t launch_sort_plan(int S, WsPtrs ws, bool from_masks, bool allow_pack, cudaStream_t st, int dbits) {
+  k_sort_plan<<<1, kRadix, 0, st>>>(ws, S, from_masks ? 1 : 0, allow_pack ? 1 : 0, 0, dbits,
+                                    sort_passes(S, dbits));
   return cudaGetLastError();
 }
 
-cudaError_t launch_prefix_plan(int S, WsPtrs ws, cudaStream_t st) {
-  k_sort_plan<<<1, kRadix, 0, st>>>(ws, kPrefixItem, 1, 1, S / 4);
+cudaError_t launch_prefix_plan(int S, WsPtrs ws, cudaStream_t st, int dbits) {
+  k_sort_plan<<<1, kRadix, 0, st>>>(ws, kPrefixItem, 1, 1, S / 4, dbits, prefix_passes(dbits));
   return cudaGetLastError();
 }
 

@@ -152,6 +152,7 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t dig, bool valid, uint32
 // (so that every thread of the CTA takes the same early exit).
 struct PassInfo {
   uint32_t U, run, src, next, vary;
+  uint32_t bits;  // digit width (8, or 6 / 7 bits of a packed key)
   uint32_t keys;  // k_tile_count reads digit d from the keys: a first pass whose digit is not in the
                   // compaction's plane (unpacked keys whose byte 0 is constant)
 };
@@ -161,7 +162,7 @@ struct PassInfo {
 template <bool kCount = false>
 __device__ __forceinline__ PassInfo pass_info(const WsPtrs& ws, int d) {
   __shared__ PassInfo s_pi;
-  if (__ldg(ws.plan->skip + d)) return PassInfo{0, 0, 0, 0, 0, 0};
+  if (__ldg(ws.plan->skip + d)) return PassInfo{0, 0, 0, 0, 0, 8, 0};
   if (threadIdx.x == 0) {
     const Plan* plan = ws.plan;
     const uint32_t skip = plan->skip[d], U = plan->U, src = plan->src[d];
@@ -172,6 +173,7 @@ __device__ __forceinline__ PassInfo pass_info(const WsPtrs& ws, int d) {
     s_pi.src = src;
     s_pi.next = (uint32_t)(int32_t)next;
     s_pi.vary = plan->vary[d];
+    s_pi.bits = plan->dbits;
     if (kCount) {
       const int first = plan->first;
       s_pi.keys = (d == first && d != 0 && !plan->plane_first) ? 1u : 0u;
@@ -188,6 +190,34 @@ template <int S>
 __device__ __forceinline__ uint32_t item_key_word(const unsigned char* buf, int64_t i, int word) {
   constexpr int kStride = soa_items(S) ? S / 4 : S / 4 + 1;  // words per item in the key array
   return reinterpret_cast<const uint32_t*>(buf)[i * kStride + word];
+}
+
+// Where digit d of a K-word key lies: bits [d * bits, d * bits + bits) counted from the least
+// significant bit of word K - 1 (word 0 is the most significant).  A digit of fewer than 8 bits may
+// straddle two words: its high part is then the low bits of the next more significant word.
+struct DigitLoc {
+  int word, shift;
+  bool straddle;
+  uint32_t mask;
+};
+template <int K>
+__device__ __forceinline__ DigitLoc digit_loc(int d, uint32_t bits) {
+  const int o = d * (int)bits;
+  DigitLoc L;
+  L.word = K - 1 - (o >> 5);
+  L.shift = o & 31;
+  L.straddle = L.shift + (int)bits > 32 && L.word > 0;
+  L.mask = (1u << bits) - 1u;
+  return L;
+}
+// The digit from its low word and the next more significant one (used only when straddling).
+__device__ __forceinline__ uint32_t digit_from(uint32_t lo, uint32_t hi, const DigitLoc& L) {
+  return (L.straddle ? __funnelshift_r(lo, hi, L.shift) : lo >> L.shift) & L.mask;
+}
+// Digit d of a key held in registers.
+template <int K>
+__device__ __forceinline__ uint32_t key_digit_loc(const uint32_t (&k)[K], const DigitLoc& L) {
+  return digit_from(key_word<K>(k, L.word), L.straddle ? key_word<K>(k, L.word - 1) : 0u, L);
 }
 
 }  // namespace reindex

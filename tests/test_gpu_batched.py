@@ -74,7 +74,9 @@ def test_batched_equals_oracle_per_mesh(rx, S):
     check_against_oracle(meshes, out_v, out_off, out_i)
 
 
-@pytest.mark.parametrize("spec", ["sort=regs,grid=persist", "sort=tiles,swaves=1,pack=off", "sort=tiles,swaves=tile,pack=on"])
+@pytest.mark.parametrize("spec", ["sort=regs,grid=persist", "sort=tiles,swaves=1,pack=off", "sort=tiles,swaves=tile,pack=on",
+                                  "sort=chunk,chunk=wide,cgrid=3,dbits=8", "sort=chunk,chunk=small,cgrid=2,dbits=7",
+                                  "sort=chunk,chunk=big,dbits=6,rank=match"])
 @pytest.mark.parametrize("S", [4, 16])
 def test_batched_sort_variants(rx, spec, S):
     """The batched path sorts (S + 4)-byte keys with the variant configured for that key size."""

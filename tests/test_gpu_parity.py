@@ -293,7 +293,9 @@ SORT_VARIANTS = ["sort=regs,rank=ballot,grid=persist,prefix=off", "sort=regs,ran
                  "sort=tiles,rank=vary,swaves=tile,pack=on,prefix=off", "sort=tiles,rank=ballot,pack=auto",
                  "sort=chunk,chunk=big,pack=off,prefix=off", "sort=chunk,chunk=small,pack=on,prefix=off",
                  "sort=chunk,chunk=big,cgrid=3,pack=auto", "sort=chunk,chunk=small,cgrid=5,cocc=1,pack=off",
-                 "sort=chunk,chunk=wide,cgrid=7,rank=match,pack=on", "sort=chunk,chunk=deep,cgrid=2,pack=off,prefix=off"]
+                 "sort=chunk,chunk=wide,cgrid=7,rank=match,pack=on", "sort=chunk,chunk=deep,cgrid=2,pack=off,prefix=off",
+                 "sort=chunk,chunk=wide,cgrid=3,dbits=7,rank=ballot,prefix=off",
+                 "sort=chunk,chunk=small,dbits=6,rank=vary,prefix=auto", "sort=chunk,chunk=big,cgrid=5,dbits=6,rank=match"]
 
 
 @pytest.mark.parametrize("spec", SORT_VARIANTS)
@@ -315,7 +317,8 @@ def test_sort_variants_bit_exact(rx, spec, S):
 
 WIDE_VARIANTS = ["pack=off,swaves=tile,prefix=off", "pack=on,swaves=tile,prefix=off", "pack=auto,swaves=1",
                  "pack=on,swaves=4", "sort=chunk,chunk=big,cgrid=4,prefix=off", "sort=chunk,chunk=small,prefix=auto",
-                 "sort=chunk,chunk=wide,cgrid=3,prefix=off", "sort=chunk,chunk=deep,prefix=auto"]
+                 "sort=chunk,chunk=wide,cgrid=3,prefix=off", "sort=chunk,chunk=deep,prefix=auto",
+                 "sort=chunk,chunk=big,cgrid=4,dbits=7,prefix=auto", "sort=chunk,chunk=wide,dbits=6,prefix=off"]
 
 
 @pytest.mark.parametrize("spec", WIDE_VARIANTS)
