@@ -290,6 +290,37 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def tet_measure(rx, torch, dev, local, steps):
+    """The 128^3 tetrahedral soup (16-byte vertices, 4 indices per element), generated on the
+    device (bit-identical to the host generator): device-resident step time with the default
+    configuration (the prefix sort for 16-byte keys), unique count checked against the closed form."""
+    from paper_2109_09812_gb300 import synth
+
+    v, i = synth.tet_soup_gpu(128, 0.03, 3, device=dev)
+    v = v.view(torch.int32)
+    n_vtx, n_elem = int(v.shape[0]), int(i.shape[0])
+    ws = torch.empty(rx.reindex_workspace_size(n_vtx, 16, n_elem, 4), dtype=torch.uint8, device=dev)
+    out_v, out_n, out_i = torch.empty_like(v), torch.empty(1, dtype=torch.int64, device=dev), torch.empty_like(i)
+    for _ in range(3):
+        rx.reindex_mesh_ws(v, i, ws, out_v, out_n, out_i)
+    torch.cuda.synchronize(dev)
+    D = int(out_n.item())
+    if D != 129 ** 3:
+        raise SystemExit(f"tet soup: unexpected unique count {D}")
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            rx.reindex_mesh_ws(v, i, ws, out_v, out_n, out_i)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": WORKLOADS["tet128"][0], "ms_per_step": ms, "value": n_elem / (ms / 1e3), "unit": UNIT,
+            "unique_out": D, "steps": steps, "tuning": rx.reindex_tuning_get(16), "clocks": clocks.summary()}
+
+
 def batched_measure(rx, torch, dev, local, steps, warmup):
     """Batched path on the 4096-mesh workload (generated on the device, bit-identical to the host
     generator): one CUDA-graph replay of reindex_meshes over all meshes vs one reindex_mesh_ws
@@ -906,6 +937,7 @@ def run_ours(args, world, rank, local):
     # ---- the batched path and the serving loop (the metric's other two parts), on this GPU
     sub = {}
     if world == 1 and args.workload == "heightfield2048" and not args.no_sub:
+        sub["tet128"] = tet_measure(rx, torch, dev, local, max(3, min(args.steps, 10)))
         sub["batched"] = batched_measure(rx, torch, dev, local, max(3, min(args.steps, 10)), 3)
         srv = serving_measure(rx, torch, dev, local, args.serving_requests, [0.7], calib_n=args.serving_requests)
         load = srv["loads"]["0.70"]

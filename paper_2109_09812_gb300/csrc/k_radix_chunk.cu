@@ -42,6 +42,7 @@ __device__ __forceinline__ void chunk_tiles(uint32_t U, uint32_t T, uint32_t G, 
 constexpr int kChunkCountThreads = 512;
 constexpr int kChunkCountWarps = kChunkCountThreads / 32;
 constexpr int kCPad = kRadix + 1;
+constexpr int kCountBatch = 4;
 
 template <int S>
 __global__ void __launch_bounds__(kChunkCountThreads) k_chunk_count(WsPtrs ws, int d, int G, int T) {
@@ -64,16 +65,27 @@ __global__ void __launch_bounds__(kChunkCountThreads) k_chunk_count(WsPtrs ws, i
     for (uint32_t i = lo + t; i < hi; i += kChunkCountThreads)
       atomicAdd(hr + ((item_key_word<S>(items, (int64_t)i, word) >> sh) & 0xFFu), 1u);
   } else {  // lo is a multiple of T (>= 2048), so 16-byte vectors of the plane are aligned
-    for (uint32_t p = lo + 16u * t; p < hi; p += 16u * kChunkCountThreads) {
-      const uint4 v = __ldcs(reinterpret_cast<const uint4*>(ws.digits + p));
-      const uint32_t q4[4] = {v.x, v.y, v.z, v.w};
-      if (p + 16 <= hi) {
+    // kCountBatch vectors in flight per thread (one at a time left the loads' latency exposed)
+    constexpr uint32_t kStep = 16u * kChunkCountThreads;
+    for (uint32_t p0 = lo + 16u * t; p0 < hi; p0 += kStep * kCountBatch) {
+      uint4 v[kCountBatch];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) atomicAdd(hr + ((q4[i >> 2] >> ((i & 3) * 8)) & 0xFFu), 1u);
-      } else {
+      for (int b = 0; b < kCountBatch; ++b) {
+        const uint32_t p = p0 + b * kStep;
+        v[b] = p < hi ? __ldcs(reinterpret_cast<const uint4*>(ws.digits + p)) : make_uint4(0, 0, 0, 0);
+      }
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (p + i < hi) atomicAdd(hr + ((q4[i >> 2] >> ((i & 3) * 8)) & 0xFFu), 1u);
+      for (int b = 0; b < kCountBatch; ++b) {
+        const uint32_t p = p0 + b * kStep;
+        const uint32_t q4[4] = {v[b].x, v[b].y, v[b].z, v[b].w};
+        if (p + 16 <= hi) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) atomicAdd(hr + ((q4[i >> 2] >> ((i & 3) * 8)) & 0xFFu), 1u);
+        } else if (p < hi) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (p + i < hi) atomicAdd(hr + ((q4[i >> 2] >> ((i & 3) * 8)) & 0xFFu), 1u);
+        }
       }
     }
   }

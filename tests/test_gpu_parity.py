@@ -220,20 +220,25 @@ def test_cuda_graph_capture_of_workspace_variant(rx):
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
 
 
-@pytest.mark.parametrize("G,pinned", [(200, True), (1200, True), (64, False)])
-def test_host_buffer_variant(rx, G, pinned):
-    """Host buffers in and out; the vertex upload and the unique-vertex download overlap kernels on
-    a second stream.  1200^2 cells: large enough for the tiles sort."""
-    m = synth.heightfield_soup(G, (3 * G) // 4, 0.05, seed=6)
+@pytest.mark.parametrize("G,pinned_in,pinned_out,tets", [(200, True, True, False), (1200, True, True, False),
+                                                          (64, False, True, False), (300, True, False, False),
+                                                          (24, True, True, True)])
+def test_host_buffer_variant(rx, G, pinned_in, pinned_out, tets):
+    """Host buffers in and out, page-locked or not: staged through device memory, the vertex upload
+    and the unique-vertex download overlapping kernels on a second stream.  1200^2 cells: large
+    enough for the large-mesh sort; tet soups take the prefix sort."""
+    m = synth.tet_soup(G, 0.03, seed=6) if tets else synth.heightfield_soup(G, (3 * G) // 4, 0.05, seed=6)
     ov, oi = oracle.reindex_sort(m.vtx, m.idx)
     hv = torch.from_numpy(m.vtx.view(np.int32))
     hi = torch.from_numpy(m.idx)
-    if pinned:
+    if pinned_in:
         hv, hi = hv.pin_memory(), hi.pin_memory()
     for _ in range(2):  # twice: nothing left over from the first call
-        out_v, out_i = rx.reindex_mesh_host(hv, hi)
-        np.testing.assert_array_equal(out_v.numpy().view(np.uint32), ov)
-        np.testing.assert_array_equal(out_i.numpy().reshape(-1), oi)
+        out_v = torch.empty((min(m.n_vtx, m.idx.size), hv.shape[1]), dtype=torch.int32, pin_memory=pinned_out)
+        out_i = torch.empty_like(hi, pin_memory=pinned_out)
+        got_v, got_i = rx.reindex_mesh_host(hv, hi, out_v, out_i)
+        np.testing.assert_array_equal(got_v.numpy().view(np.uint32), ov)
+        np.testing.assert_array_equal(got_i.numpy().reshape(-1), oi)
 
 
 def test_host_buffer_variant_reports_device_errors(rx):
