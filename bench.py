@@ -70,6 +70,14 @@ WORKLOADS = {
     "heightfield2048_s24": ("heightfield triangle soup 2048x2048 cells with 24-byte vertices (float32 xyz + 3 "
                             "normal-like words in [-1,1), each a hash of the position; 25,165,824 soup vertices "
                             "+ 5% unused, permuted), int32 idx x3, seed 2", (2048, 0.05, 2, 24)),
+    "heightfield2048_s64": ("heightfield triangle soup 2048x2048 cells with 64-byte vertices (float32 xyz + 3 "
+                            "normal-like words in [-1,1) + 10 more attribute words in [0,1) (texture coordinates, "
+                            "tangent...), each a hash of the position; 25,165,824 soup vertices + 5% unused, permuted), "
+                            "int32 idx x3, seed 2", (2048, 0.05, 2, 64)),
+    "heightfield2048_s48": ("heightfield triangle soup 2048x2048 cells with 48-byte vertices (float32 xyz + 3 "
+                            "normal-like words in [-1,1) + 6 more attribute words in [0,1), each a hash of the "
+                            "position; 25,165,824 soup vertices + 5% unused, permuted), int32 idx x3, seed 2",
+                            (2048, 0.05, 2, 48)),
     "heightfield1448_s32": ("heightfield triangle soup 1448x1448 cells with 32-byte vertices (as heightfield2048_s32), "
                             "for profiler captures", (1448, 0.05, 2, 32)),
     # a half-size case of the 2048^2 workload, for profiler captures (still larger than L2)

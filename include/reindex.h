@@ -46,12 +46,12 @@
  *     reported after the stream is synchronised in two ways: *out_nVtx holds the NEGATED
  *     status code (e.g. -REINDEX_ERR_INDEX_RANGE), and reindex_stream_status() returns it.
  *     When one occurs the contents of out_vtx and out_idx are unspecified.
- *   - Supported strides: vtxStrideBytes in {4, 8, 12, 16, 20, 24, 32} for single meshes
+ *   - Supported strides: vtxStrideBytes in {4, 8, 12, 16, 20, 24, 32, 48, 64} for single meshes
  *     (Section 3.5 expects other vertex formats to carry over directly: e.g. a position with a
- *     normal, 24 bytes, or with a normal and texture coordinates, 32 bytes); the batched entry
- *     point takes {4, 8, 12, 16}.  vtx and out_vtx must be aligned to the stride's natural
+ *     normal, 24 bytes, with a normal and texture coordinates, 32 bytes, and with a tangent and
+ *     further attributes, 48 or 64 bytes); the batched entry point takes {4, 8, 12, 16}.  vtx and out_vtx must be aligned to the stride's natural
  *     vector type: 4 bytes for S = 4, 12 and 20, 8 bytes for S = 8 and 24, 16 bytes for
- *     S = 16 and 32.  idx and out_idx must be 4-byte aligned (16-byte alignment enables
+ *     S = 16, 32, 48 and 64.  idx and out_idx must be 4-byte aligned (16-byte alignment enables
  *     128-bit vector loads and stores).
  *   - nVtx <= 2^31 - 1 (INT32_MAX; the look-back status words carry 31-bit counts and the old
  *     vertex index travels as 32 bits) and nElem * idxPerElem <= 2^31 - 1 for int32 indices; the
@@ -157,8 +157,10 @@ reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int vtxStri
  * a plugin whose host application forbids allocations behind its back.
  *   Arguments, result and error reporting are those of reindex_mesh (inputs and outputs are
  *   still the caller's device buffers).
- *   Limit: nVtx <= REINDEX_NOALLOC_MAX_VTX (262,144 vertices, any supported stride and any
- *   number of elements); a larger mesh returns REINDEX_ERR_UNSUPPORTED and nothing is launched.
+ *   Limit: nVtx <= REINDEX_NOALLOC_MAX_VTX (262,144 vertices, any number of elements) for
+ *   vertices of up to 32 bytes; 48- and 64-byte vertices are taken while their workspace fits
+ *   the scratch (every mesh of up to 188,949 or 146,472 vertices does).  A larger mesh returns
+ *   REINDEX_ERR_UNSUPPORTED and nothing is launched.
  *   Scratch: one array of REINDEX_NOALLOC_SCRATCH_BYTES (20 MiB) of device memory inside the
  *   library, held on a device from the time the CUDA runtime loads the library's device code
  *   there until the process exits.  With lazy module loading (the CUDA default) that happens at
@@ -299,17 +301,17 @@ void reindex_debug_stall_tile(int64_t tile);
  * number of inconsistencies (0 = correct).  Needs no GPU. */
 int reindex_debug_arena_check(uint64_t seed, int ops, size_t size);
 
-/* Host-only test hook: the bit selection of the prefix sort for keys of K (1..8) 32-bit words,
+/* Host-only test hook: the bit selection of the prefix sort for keys of K (1..16) 32-bit words,
  * given per word the OR of the word over the used vertices (kor) and of its complement (knand): a
  * bit varies iff it is set in both.  The prefix is the 64 most significant varying bits (at most
- * 16 runs of consecutive bits), word 0 most significant.  Writes the packing description (88
+ * 16 runs of consecutive bits), word 0 most significant.  Writes the packing description (104
  * bytes: on, nbits, nruns, word[16], shift[16], len[16], pos[16] -- runs least significant first,
- * pos = the run's offset in the prefix --, simple, wshift[8], wlen[8], 4 bytes padding) to `out`
+ * pos = the run's offset in the prefix --, simple, wshift[16], wlen[16], 4 bytes padding) to `out`
  * and returns the number of prefix bits, or -1 for bad arguments.  Needs no GPU. */
 int reindex_debug_prefix_pack(const uint32_t* kor, const uint32_t* knand, int K, void* out, int outBytes);
 
 /* Host-only test hook: the key packing arithmetic of the kernels (the same inline functions),
- * applied on the host to n keys of K (1..8) words, row-major in `keys`, with a packing
+ * applied on the host to n keys of K (1..8, 12 or 16) words, row-major in `keys`, with a packing
  * description in the layout written by reindex_debug_prefix_pack.  mode 0: pack (general runs),
  * 1: pack (at most one run per word), 2: unpack packed keys, filling the constant bits from
  * kconst[K]; all three write n*K words to `out`.  mode 3: word 0 of each unpacked key (n words),

@@ -45,6 +45,9 @@ REINDEX_ERR_TIMEOUT = 5
 REINDEX_ERR_CUDA = 6
 REINDEX_ERR_INTERNAL = 7
 
+# Size of the key-packing description the debug hooks exchange (see reindex_debug_prefix_pack).
+KEYPACK_BYTES = 104
+
 KERNEL_NAMES = ["clear", "used_flags", "compact_hist", "sort_plan", "onesweep", "head_scan", "remap", "finalize",
                 "seg_prepare", "seg_offsets", "tile_count", "tile_offsets", "tile_scatter", "key_masks", "prefix_gate",
                 "prefix_check", "chunk_scatter"]
@@ -517,15 +520,16 @@ def debug_prefix_pack(kor, knand) -> dict:
 
     kor = np.ascontiguousarray(kor, dtype=np.uint32)
     knand = np.ascontiguousarray(knand, dtype=np.uint32)
-    buf = ctypes.create_string_buffer(88)
-    nbits = lib().reindex_debug_prefix_pack(kor.ctypes.data, knand.ctypes.data, int(kor.shape[0]), buf, 88)
+    buf = ctypes.create_string_buffer(KEYPACK_BYTES)
+    nbits = lib().reindex_debug_prefix_pack(kor.ctypes.data, knand.ctypes.data, int(kor.shape[0]), buf,
+                                            KEYPACK_BYTES)
     if nbits < 0:
         raise ValueError("bad masks")
     b = buf.raw
     n = b[2]
     return dict(on=b[0], nbits=b[1], nruns=n, word=list(b[3:3 + n]), shift=list(b[19:19 + n]),
-                len=list(b[35:35 + n]), pos=list(b[51:51 + n]), simple=b[67], wshift=list(b[68:76]),
-                wlen=list(b[76:84]), returned=nbits, raw=b)
+                len=list(b[35:35 + n]), pos=list(b[51:51 + n]), simple=b[67], wshift=list(b[68:84]),
+                wlen=list(b[84:100]), returned=nbits, raw=b)
 
 
 def debug_pack_keys(pack: bytes, keys, mode: int, kconst=None):

@@ -189,8 +189,14 @@ static bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintp
 static uintptr_t vtx_alignment(int S) { return S % 16 == 0 ? 16 : (S % 8 == 0 ? 8 : 4); }
 
 // Host-side checks shared by every entry point.  Sets M.
+// Vertex strides of single meshes: 4-32 bytes on every sort, 48 and 64 bytes through the prefix
+// sort with the chunk sort as its full-key fallback.
+static bool stride_supported(int S) {
+  return S == 4 || S == 8 || S == 12 || S == 16 || S == 20 || S == 24 || S == 32 || S == 48 || S == 64;
+}
+
 static reindex_status check_args(int64_t nVtx, int S, int64_t nElem, int k, int64_t* M) {
-  if (S != 4 && S != 8 && S != 12 && S != 16 && S != 20 && S != 24 && S != 32) return REINDEX_ERR_UNSUPPORTED;
+  if (!stride_supported(S)) return REINDEX_ERR_UNSUPPORTED;
   if (nVtx < 0 || nElem < 0 || k < 1) return REINDEX_ERR_INVALID_ARG;
   if (nVtx > kMaxCount) return REINDEX_ERR_UNSUPPORTED;
   if (nElem > (int64_t)INT32_MAX / k) return REINDEX_ERR_UNSUPPORTED;
@@ -200,7 +206,7 @@ static reindex_status check_args(int64_t nVtx, int S, int64_t nElem, int k, int6
 
 // int64 indices: the same vertex limit; up to 2^40 index entries (nElem * idxPerElem).
 static reindex_status check_args64(int64_t nVtx, int S, int64_t nElem, int k, int64_t* M) {
-  if (S != 4 && S != 8 && S != 12 && S != 16 && S != 20 && S != 24 && S != 32) return REINDEX_ERR_UNSUPPORTED;
+  if (!stride_supported(S)) return REINDEX_ERR_UNSUPPORTED;
   if (nVtx < 0 || nElem < 0 || k < 1) return REINDEX_ERR_INVALID_ARG;
   if (nVtx > kMaxCount) return REINDEX_ERR_UNSUPPORTED;
   if (nElem > (int64_t(1) << 40) / k) return REINDEX_ERR_UNSUPPORTED;
@@ -296,7 +302,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const I
   const WsPtrs pp = prefix ? ws_ptrs_prefix(ws, L) : p;
   {
     prof::Scope s(REINDEX_K_CLEAR, -1, st);
-    REINDEX_TRY(launch_clear(ws, L.zero_bytes + (prefix ? 256 : 0), c, st));  // + the prefix control block
+    REINDEX_TRY(launch_clear(ws, L.zero_bytes + (prefix ? sizeof(Control) : 0), c, st));  // + the prefix control block
   }
   if (extra && extra->pre) {
     prof::Scope s(extra->flags_done ? REINDEX_K_USED_FLAGS : REINDEX_K_SEG_PREPARE, -1, st);

@@ -23,7 +23,9 @@ constexpr int kHeadIpt = 8;                // items per thread in the head scan
 constexpr int kHeadTile = kHeadThreads * kHeadIpt;         // 2048 items per tile
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;    // 256 digit values (narrower digits use the low bins)
-constexpr int kMaxDigits = 32;             // 32-byte keys -> 32 byte digits
+constexpr int kMaxDigits = 64;             // 64-byte keys -> 64 byte digits
+constexpr int kMaxKeyWords = kMaxDigits / 4;  // 16 words per key at most
+constexpr int kHugeMin = 48;               // keys of 48 and 64 bytes: prefix sort, chunk-sort fallback only
 constexpr int kPrefixBytes = 8;           // prefix sort: keys cut to their 64 most significant varying bits,
 constexpr int kPrefixItem = 12;           // held in 12-byte item keys (word 0 zero: 16-byte records)
 constexpr int kWideMin = 24;               // keys of 24 and 32 bytes (single meshes) use the "tiles"
@@ -90,12 +92,12 @@ struct Control {             // zeroed at the start of every call
   uint32_t U;                // number of used vertices (written by the last compaction tile)
   uint32_t ctr[2 + kMaxDigits];  // atomic tile counters: [0] compaction, [1 + d] sort digit d,
                                  // [1 + kMaxDigits] head scan
-  uint32_t kor[kMaxDigits / 4];   // OR of key word q over the used vertices (compaction, kHistNone)
-  uint32_t knand[kMaxDigits / 4]; // OR of the complement: bit b varies iff set in both masks
+  uint32_t kor[kMaxKeyWords];     // OR of key word q over the used vertices (compaction, kHistNone)
+  uint32_t knand[kMaxKeyWords];   // OR of the complement: bit b varies iff set in both masks
   uint32_t amb;                   // prefix sort: two different keys share a prefix (1)
-  uint32_t pad[11];
+  uint32_t pad[27];
 };
-static_assert(sizeof(Control) == 256, "Control block is one 256-byte line");
+static_assert(sizeof(Control) == 512, "Control block is two 256-byte lines");
 
 // Key packing for the "tiles" sort.  Bits that are equal in every item do not affect the order,
 // so the compaction can pack the varying bits of each key (runs of consecutive bits, least
@@ -113,11 +115,11 @@ struct KeyPack {
   uint8_t len[kMaxPackRuns];       // run length in bits
   uint8_t pos[kMaxPackRuns];       // where the run starts in the packed key
   uint8_t simple;                  // 1: at most one run per word (wshift / wlen describe them)
-  uint8_t wshift[kMaxDigits / 4];  // word q's run: lowest bit
-  uint8_t wlen[kMaxDigits / 4];    //               and length (0: no varying bit)
+  uint8_t wshift[kMaxKeyWords];    // word q's run: lowest bit
+  uint8_t wlen[kMaxKeyWords];      //               and length (0: no varying bit)
   uint8_t pad[4];
 };
-static_assert(sizeof(KeyPack) == 88, "KeyPack layout");
+static_assert(sizeof(KeyPack) == 104, "KeyPack layout");
 
 struct Plan {                // written by the sort-plan kernel
   uint32_t U;
@@ -134,7 +136,7 @@ struct Plan {                // written by the sort-plan kernel
   uint8_t vary[kMaxDigits];  // bits of digit d that differ between items (the others are constant)
   uint8_t pad2[12];
   KeyPack pack;                      // packing of the keys (pack.on == 0: not packed)
-  uint32_t kconst[kMaxDigits / 4];   // values of the constant key bits (to restore packed keys)
+  uint32_t kconst[kMaxKeyWords];     // values of the constant key bits (to restore packed keys)
   uint32_t base[kMaxDigits][kRadix];  // exclusive prefix of the digit histogram
 };
 
@@ -168,7 +170,7 @@ struct WsLayout {
     off_lb_sort = o;     o = align_up(o + (size_t)2 * tilesS * kRadix * 4, 256);
     off_bitmask = o;     o = align_up(o + (size_t)((n + 31) / 32) * 4, 256);
     zero_bytes = o;
-    off_ctrl_pre = o;    o += 256;  // control block of the prefix sort (outside the full sort's zeroing)
+    off_ctrl_pre = o;    o += sizeof(Control);  // the prefix sort's control block (outside the full sort's zeroing)
     off_plan = o;        o = align_up(o + sizeof(Plan), 256);
     // SoA layouts keep the id plane 256-byte aligned; 256 spare bytes let bulk copies of a
     // ragged last tile round their size up to 16 bytes without leaving the buffer.
@@ -418,6 +420,41 @@ struct ItemIO<32> {
   }
 };
 
+// 48- and 64-byte keys: structure of arrays, three or four 16-byte vectors per key, then the id plane.
+template <int S>
+struct ItemIOWide {
+  static_assert(S % 16 == 0 && S > 32, "wide key layouts");
+  static constexpr int V = S / 16;
+  static __device__ __forceinline__ void load(const unsigned char* buf, int64_t idoff, int64_t i, Item<S>& it) {
+    const uint4* p = reinterpret_cast<const uint4*>(buf) + V * i;
+#pragma unroll
+    for (int h = 0; h < V; ++h) {
+      const uint4 v = p[h];
+      it.k[4 * h] = v.x; it.k[4 * h + 1] = v.y; it.k[4 * h + 2] = v.z; it.k[4 * h + 3] = v.w;
+    }
+    it.id = reinterpret_cast<const uint32_t*>(buf + idoff)[i];
+  }
+  static __device__ __forceinline__ void load_cs(const unsigned char* buf, int64_t idoff, int64_t i, Item<S>& it) {
+    const uint4* p = reinterpret_cast<const uint4*>(buf) + V * i;
+#pragma unroll
+    for (int h = 0; h < V; ++h) {
+      const uint4 v = __ldcs(p + h);
+      it.k[4 * h] = v.x; it.k[4 * h + 1] = v.y; it.k[4 * h + 2] = v.z; it.k[4 * h + 3] = v.w;
+    }
+    it.id = __ldcs(reinterpret_cast<const uint32_t*>(buf + idoff) + i);
+  }
+  static __device__ __forceinline__ void store(unsigned char* buf, int64_t idoff, int64_t i, const Item<S>& it) {
+    uint4* p = reinterpret_cast<uint4*>(buf) + V * i;
+#pragma unroll
+    for (int h = 0; h < V; ++h) p[h] = make_uint4(it.k[4 * h], it.k[4 * h + 1], it.k[4 * h + 2], it.k[4 * h + 3]);
+    reinterpret_cast<uint32_t*>(buf + idoff)[i] = it.id;
+  }
+};
+template <>
+struct ItemIO<48> : ItemIOWide<48> {};
+template <>
+struct ItemIO<64> : ItemIOWide<64> {};
+
 // Vertex key loads from the caller's vertex array (stride S, natural alignment).
 // (streaming: the caller's vertex array is read once per call)
 template <int S>
@@ -437,10 +474,13 @@ __device__ __forceinline__ void load_key(const void* vtx, int64_t i, uint32_t (&
     const uint2* p = reinterpret_cast<const uint2*>(vtx) + 3 * i;
     const uint2 a = __ldcs(p), b = __ldcs(p + 1), c = __ldcs(p + 2);
     k[0] = a.x; k[1] = a.y; k[2] = b.x; k[3] = b.y; k[4] = c.x; k[5] = c.y;
-  } else if constexpr (S == 32) {
-    const uint4* p = reinterpret_cast<const uint4*>(vtx) + 2 * i;
-    const uint4 a = __ldcs(p), b = __ldcs(p + 1);
-    k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w; k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+  } else if constexpr (S % 16 == 0) {  // 32, 48, 64 bytes: 16-byte vectors
+    const uint4* p = reinterpret_cast<const uint4*>(vtx) + (S / 16) * i;
+#pragma unroll
+    for (int h = 0; h < S / 16; ++h) {
+      const uint4 a = __ldcs(p + h);
+      k[4 * h] = a.x; k[4 * h + 1] = a.y; k[4 * h + 2] = a.z; k[4 * h + 3] = a.w;
+    }
   } else {
     const uint32_t* p = reinterpret_cast<const uint32_t*>(vtx) + i * (S / 4);
 #pragma unroll
@@ -451,7 +491,7 @@ __device__ __forceinline__ void load_key(const void* vtx, int64_t i, uint32_t (&
 // Vertex key load through the read-only cache, for random accesses (natural alignment).
 template <int S>
 __device__ __forceinline__ void load_key_ro(const void* vtx, uint32_t i, uint32_t (&k)[S / 4]) {
-  if constexpr (S == 16 || S == 32) {
+  if constexpr (S % 16 == 0) {
     const uint4* p = reinterpret_cast<const uint4*>(vtx) + (size_t)i * (S / 16);
 #pragma unroll
     for (int h = 0; h < S / 16; ++h) {
@@ -487,9 +527,10 @@ __device__ __forceinline__ void store_key(void* out, int64_t i, const uint32_t (
   } else if constexpr (S == 24) {
     uint2* p = reinterpret_cast<uint2*>(out) + 3 * i;
     __stcs(p, make_uint2(k[0], k[1])); __stcs(p + 1, make_uint2(k[2], k[3])); __stcs(p + 2, make_uint2(k[4], k[5]));
-  } else if constexpr (S == 32) {
-    uint4* p = reinterpret_cast<uint4*>(out) + 2 * i;
-    __stcs(p, make_uint4(k[0], k[1], k[2], k[3])); __stcs(p + 1, make_uint4(k[4], k[5], k[6], k[7]));
+  } else if constexpr (S % 16 == 0) {  // 32, 48, 64 bytes
+    uint4* p = reinterpret_cast<uint4*>(out) + (S / 16) * i;
+#pragma unroll
+    for (int h = 0; h < S / 16; ++h) __stcs(p + h, make_uint4(k[4 * h], k[4 * h + 1], k[4 * h + 2], k[4 * h + 3]));
   } else {
     uint32_t* p = reinterpret_cast<uint32_t*>(out) + i * (S / 4);
 #pragma unroll

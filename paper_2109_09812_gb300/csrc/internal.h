@@ -56,6 +56,11 @@ inline LaunchCfg resolve_cfg(LaunchCfg c, int S, int64_t Umax, bool batched = fa
       c.sort_kernel = (c.sort_kernel == kSortAuto && Umax >= kTilesMinItems) ? kSortChunk : kSortTiles;
     c.rank_mode = kRankBallotVary;
   }
+  if (S >= kHugeMin) {  // 48- and 64-byte keys: chunk sort of unpacked byte digits only
+    c.sort_kernel = kSortChunk;
+    c.pack_keys = 0;
+    c.digit_bits = 8;
+  }
   if (c.sort_kernel == kSortAuto) c.sort_kernel = Umax >= kTilesMinItems ? kSortChunk : kSortRegs;
   if (c.sort_kernel != kSortChunk || c.digit_bits < 6 || c.digit_bits > 8) c.digit_bits = 8;
   if (c.digit_bits < 8) c.pack_keys = 1;  // narrower digits are bit fields of the packed key

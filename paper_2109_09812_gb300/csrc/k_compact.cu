@@ -356,9 +356,14 @@ __global__ void __launch_bounds__(kThreads) k_prefix_check(const void* __restric
 template <int S>
 static int occ() {
   int a = 0, b = 0, c = 0;
+  int n = 0;
+  if constexpr (S >= kHugeMin) {  // 48- and 64-byte keys: unpacked keys, masks mode only
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_compact<S, kHistMasks, false>, kThreads, 0);
+    return n < 1 ? 1 : n;
+  }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistNone, false>, kThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistMasks, false>, kThreads, 0);
-  int n = min(a, b);
+  n = min(a, b);
   if constexpr (S < kWideMin) {  // upfront histograms (onesweep sort) for keys of up to 20 bytes
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_compact<S, kHistUniform, false>, kThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<S, kHistPeel, false>, kThreads, 0);
@@ -382,6 +387,8 @@ int occupancy_compact(int S) {
     case 16: return occ<16>();
     case 20: return occ<20>();
     case 24: return occ<24>();
+    case 48: return occ<48>();
+    case 64: return occ<64>();
     default: return occ<32>();
   }
 }
@@ -447,6 +454,8 @@ cudaError_t launch_compact(int S, const void* vtx, int64_t nVtx, WsPtrs ws, int6
       case 20: launch_s<20, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
       case 24: launch_s<24, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
       case 32: launch_s<32, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, mode, none, st); break;
+      case 48: launch_v<48, kHistMasks, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
+      case 64: launch_v<64, kHistMasks, false>(g, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
       default: return cudaErrorInvalidValue;
     }
   }
@@ -464,6 +473,8 @@ cudaError_t launch_compact_prefix(int S, const void* vtx, int64_t nVtx, WsPtrs w
     case 20: launch_v<20, kHistPrefix, false>(tilesV, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
     case 24: launch_v<24, kHistPrefix, false>(tilesV, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
     case 32: launch_v<32, kHistPrefix, false>(tilesV, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
+    case 48: launch_v<48, kHistPrefix, false>(tilesV, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
+    case 64: launch_v<64, kHistPrefix, false>(tilesV, c.sms, persistent, vtx, nVtx, ws, tilesV, none, st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -485,6 +496,8 @@ cudaError_t launch_prefix_check(int S, const void* vtx, int64_t nVtx, const void
     case 20: REINDEX_PC(20); break;
     case 24: REINDEX_PC(24); break;
     case 32: REINDEX_PC(32); break;
+    case 48: REINDEX_PC(48); break;
+    case 64: REINDEX_PC(64); break;
     default: return cudaErrorInvalidValue;
   }
 #undef REINDEX_PC
@@ -518,6 +531,8 @@ cudaError_t launch_key_masks(int S, const void* vtx, int64_t nVtx, WsPtrs ws, co
       case 20: REINDEX_KM(20, false); break;
       case 24: REINDEX_KM(24, false); break;
       case 32: REINDEX_KM(32, false); break;
+      case 48: REINDEX_KM(48, false); break;
+      case 64: REINDEX_KM(64, false); break;
       default: return cudaErrorInvalidValue;
     }
   }

@@ -34,6 +34,9 @@ __global__ void __launch_bounds__(kHeadThreads, (S >= 16 || SV > 0) ? 2 : 4)
   constexpr int K = S / 4;
   constexpr bool kVerify = SV > 0;
   constexpr int KV = kVerify ? SV / 4 : 1;
+  // the heads' whole keys are loaded before the scan (their latency hidden by the look-back) up to
+  // 32-byte vertices; wider ones are read when stored (eight 16-word keys would not fit in registers)
+  constexpr bool kPrefetchKeys = kVerify && SV <= 32;
   __shared__ uint32_t s_warp[kHeadWarps];
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ KeyPack s_pack;
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(kHeadThreads, (S >= 16 || SV > 0) ? 2 : 4)
 
     uint32_t within[kHeadIpt];
     uint32_t heads = 0, cnt = 0, firsts = 0;
-    uint32_t hkey[kHeadIpt][KV];  // kVerify: whole keys of the heads
+    uint32_t hkey[kPrefetchKeys ? kHeadIpt : 1][KV];  // whole keys of the heads (prefetched)
 #pragma unroll
     for (int r = 0; r < kHeadIpt; ++r) {
       const int64_t j = wbase + r * 32 + lane;
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(kHeadThreads, (S >= 16 || SV > 0) ? 2 : 4)
                            : it[r].k[0] != pks[0];
       }
       const bool head = (j < U) && (j == 0 || diff);
-      if constexpr (kVerify)  // the head's whole key, loaded now: in flight during the scan
+      if constexpr (kPrefetchKeys)  // the head's whole key, loaded now: in flight during the scan
         if (head && it[r].id < nVtx) load_key_ro<SV>(vtx, it[r].id, hkey[r]);
       const uint32_t m = __ballot_sync(0xffffffffu, head);
       within[r] = cnt + __popc(m & lanemask_lt());
@@ -149,8 +152,13 @@ __global__ void __launch_bounds__(kHeadThreads, (S >= 16 || SV > 0) ? 2 : 4)
         const uint32_t nid = head ? e : e - 1u;
         if (it[r].id < nVtx) {
           st_u32_hint(ws.old2new + it[r].id, nid, keep);
-          if constexpr (kVerify) {
+          if constexpr (kPrefetchKeys) {
             if (head) store_key<SV>(out_vtx, nid, hkey[r]);  // the unique vertex
+          } else if constexpr (kVerify) {
+            if (head) {
+              load_key_ro<SV>(vtx, it[r].id, hkey[0]);
+              store_key<SV>(out_vtx, nid, hkey[0]);
+            }
           } else if (head || (kSeg && ((firsts >> r) & 1u))) {
             uint32_t key[K];
 #pragma unroll
@@ -186,6 +194,13 @@ static int occ() {
   return n < 1 ? 1 : n;
 }
 
+template <int S>
+static int occ_unpacked() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_head_scan<S, false, false>, kHeadThreads, 0);
+  return n < 1 ? 1 : n;
+}
+
 // Resident CTAs per SM of the prefix-sort variant (queried once per stride).
 template <int SV>
 static int occ_verify() {
@@ -218,6 +233,8 @@ cudaError_t launch_head_scan_prefix(int S, WsPtrs ws, const void* vtx, void* out
     case 20: launch_verify<20>(tiles, c, ws, vtx, out_vtx, out_nVtx, nVtx, st); break;
     case 24: launch_verify<24>(tiles, c, ws, vtx, out_vtx, out_nVtx, nVtx, st); break;
     case 32: launch_verify<32>(tiles, c, ws, vtx, out_vtx, out_nVtx, nVtx, st); break;
+    case 48: launch_verify<48>(tiles, c, ws, vtx, out_vtx, out_nVtx, nVtx, st); break;
+    case 64: launch_verify<64>(tiles, c, ws, vtx, out_vtx, out_nVtx, nVtx, st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -231,6 +248,8 @@ int occupancy_head(int S) {
     case 16: return occ<16>();
     case 20: return occ<20>();
     case 24: return occ<24>();
+    case 48: return occ_unpacked<48>();
+    case 64: return occ_unpacked<64>();
     default: return occ<32>();
   }
 }
@@ -268,6 +287,12 @@ cudaError_t launch_head_scan(int S, WsPtrs ws, void* out_vtx, int64_t* out_nVtx,
       case 20: launch_s<20, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
       case 24: launch_s<24, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
       case 32: launch_s<32, false>((int)g, ws, out_vtx, out_nVtx, nVtx, none, may_pack, st); break;
+      case 48:  // 48- and 64-byte keys are never packed
+        k_head_scan<48, false, false><<<(int)g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx, none, nullptr);
+        break;
+      case 64:
+        k_head_scan<64, false, false><<<(int)g, kHeadThreads, 0, st>>>(ws, out_vtx, out_nVtx, nVtx, none, nullptr);
+        break;
       default: return cudaErrorInvalidValue;
     }
   }

@@ -333,21 +333,24 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_scatter(WsPtrs ws, int d, in
 //   cfg 3 "deep":  4096-item tiles (2048 over 20 bytes), 1024 threads, 1 CTA per SM (64 registers).
 template <int S, int C>
 struct ChunkCfg;
+// Largest tile of S-byte keys whose two buffers fit beside the tables: 4096 items up to 20-byte
+// items, 2048 up to 36 bytes, 1024 for the 52- and 68-byte items of 48- and 64-byte keys.
+constexpr int chunk_tile_max(int S) { return S + 4 <= 20 ? 4096 : (S + 4 <= 36 ? 2048 : 1024); }
 template <int S>
 struct ChunkCfg<S, 0> {
-  static constexpr int T = S + 4 <= 20 ? 4096 : 2048, NT = 512, NB = 2, MINB = 1;
+  static constexpr int T = chunk_tile_max(S), NT = 512, NB = 2, MINB = 1;
 };
 template <int S>
 struct ChunkCfg<S, 1> {
-  static constexpr int T = 2048, NT = 256, NB = 2, MINB = 1;
+  static constexpr int T = chunk_tile_max(S) < 2048 ? chunk_tile_max(S) : 2048, NT = 256, NB = 2, MINB = 1;
 };
 template <int S>
 struct ChunkCfg<S, 2> {
-  static constexpr int T = 2048, NT = 512, NB = 2, MINB = 2;
+  static constexpr int T = chunk_tile_max(S) < 2048 ? chunk_tile_max(S) : 2048, NT = 512, NB = 2, MINB = 2;
 };
 template <int S>
 struct ChunkCfg<S, 3> {
-  static constexpr int T = S + 4 <= 20 ? 4096 : 2048, NT = 1024, NB = 2, MINB = 1;
+  static constexpr int T = chunk_tile_max(S), NT = 1024, NB = 2, MINB = 1;
 };
 
 // Digit matching: for keys up to 12 bytes 8 ballots, match.any, or ballots on the varying digit
@@ -404,13 +407,15 @@ int occupancy_chunk(int S, int cfg) {
     case 20: return chunk_occ_s<20>(cfg);
     case 24: return chunk_occ_s<24>(cfg);
     case 32: return chunk_occ_s<32>(cfg);
+    case 48: return chunk_occ_s<48>(cfg);
+    case 64: return chunk_occ_s<64>(cfg);
     default: return 0;
   }
 }
 
 int chunk_tile_items(int S, int cfg) {
-  if (cfg == 1 || cfg == 2) return 2048;
-  return S + 4 <= 20 ? 4096 : 2048;
+  const int t = chunk_tile_max(S);
+  return (cfg == 1 || cfg == 2) ? std::min(t, 2048) : t;
 }
 
 int chunk_grid(int S, const LaunchCfg& c, int64_t Umax) {
@@ -434,6 +439,8 @@ cudaError_t launch_chunk_count(int S, int digit, WsPtrs ws, int G, int T, cudaSt
     case 20: return launch_pdl(k_chunk_count<20>, G, kChunkCountThreads, 0, st, ws, digit, G, T);
     case 24: return launch_pdl(k_chunk_count<24>, G, kChunkCountThreads, 0, st, ws, digit, G, T);
     case 32: return launch_pdl(k_chunk_count<32>, G, kChunkCountThreads, 0, st, ws, digit, G, T);
+    case 48: return launch_pdl(k_chunk_count<48>, G, kChunkCountThreads, 0, st, ws, digit, G, T);
+    case 64: return launch_pdl(k_chunk_count<64>, G, kChunkCountThreads, 0, st, ws, digit, G, T);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -471,6 +478,8 @@ cudaError_t launch_chunk_scatter(int S, int digit, WsPtrs ws, const LaunchCfg& c
     case 20: return scatter_s<20>(cfg, mode, G, digit, ws, st);
     case 24: return scatter_s<24>(cfg, mode, G, digit, ws, st);
     case 32: return scatter_s<32>(cfg, mode, G, digit, ws, st);
+    case 48: return scatter_s<48>(cfg, mode, G, digit, ws, st);
+    case 64: return scatter_s<64>(cfg, mode, G, digit, ws, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(kRadix) k_sort_plan(WsPtrs ws, int P, int from
         kp.wshift[wd] = runs_here == 1 ? kp.shift[first_run] : 0;
         kp.wlen[wd] = runs_here == 1 ? kp.len[first_run] : 0;
       }
+      if (pos > 255) fits = false;  // run positions are bytes
       kp.nbits = (uint8_t)pos;
       const int packed = (pos + b - 1) / b;
       // packing when it saves at least one pass; always for digits narrower than bytes (else they
@@ -545,7 +546,7 @@ cudaError_t read_and_clear_sticky(uint32_t* value, cudaStream_t st) {
 // Host test hook (include/reindex.h): the prefix sort's packing for given key masks.
 extern "C" int reindex_debug_prefix_pack(const uint32_t* kor, const uint32_t* knand, int K, void* out, int outBytes) {
   using namespace reindex;
-  if (K < 1 || K > kMaxDigits / 4 || !kor || !knand || !out || outBytes < (int)sizeof(KeyPack)) return -1;
+  if (K < 1 || K > kMaxKeyWords || !kor || !knand || !out || outBytes < (int)sizeof(KeyPack)) return -1;
   KeyPack kp;
   int nbits = 0;
   plan_prefix_pack(kor, knand, K, kp, nbits);
@@ -581,7 +582,7 @@ void debug_pack_k(const reindex::KeyPack& P, const uint32_t* kconst, const uint3
 extern "C" int reindex_debug_pack_keys(const void* pack, int packBytes, int K, const uint32_t* kconst,
                                        const uint32_t* keys, int64_t n, int mode, uint32_t* out) {
   using namespace reindex;
-  if (!pack || packBytes < (int)sizeof(KeyPack) || K < 1 || K > kMaxDigits / 4 || n < 0 || mode < 0 || mode > 3 ||
+  if (!pack || packBytes < (int)sizeof(KeyPack) || K < 1 || K > kMaxKeyWords || n < 0 || mode < 0 || mode > 3 ||
       (n > 0 && (!keys || !out)) || ((mode >= 2) && !kconst))
     return -1;
   KeyPack P;
@@ -595,7 +596,10 @@ extern "C" int reindex_debug_pack_keys(const void* pack, int packBytes, int K, c
     case 5: debug_pack_k<5>(P, kconst, keys, n, mode, out); break;
     case 6: debug_pack_k<6>(P, kconst, keys, n, mode, out); break;
     case 7: debug_pack_k<7>(P, kconst, keys, n, mode, out); break;
-    default: debug_pack_k<8>(P, kconst, keys, n, mode, out); break;
+    case 8: debug_pack_k<8>(P, kconst, keys, n, mode, out); break;
+    case 12: debug_pack_k<12>(P, kconst, keys, n, mode, out); break;
+    case 16: debug_pack_k<16>(P, kconst, keys, n, mode, out); break;
+    default: return -1;  // key sizes the library does not use
   }
   return 0;
 }

@@ -53,7 +53,10 @@ def test_workspace_size_model(L):
     for S in (24, 32):  # wide vertices: the same model
         b = rx.reindex_workspace_size(n, S, ne, k)
         assert 2 * U * (S + 4) + U + 4 * n <= b <= 2 * U * (S + 4) + U + 4 * n + 64 * 2**20
-    for S in (5, 28, 36, 64):  # unsupported strides
+    for S in (48, 64):  # position + normal + texture coordinates + tangent: the same model
+        b = rx.reindex_workspace_size(n, S, ne, k)
+        assert 2 * U * (S + 4) + U + 4 * n <= b <= 2 * U * (S + 4) + U + 4 * n + 64 * 2**20
+    for S in (5, 28, 36, 40, 128):  # unsupported strides
         assert rx.reindex_workspace_size(n, S, ne, k) == 0
     assert rx.reindex_meshes_workspace_size(2, n, 24, ne, k) == 0  # batched: up to 16 bytes
     assert rx.reindex_workspace_size(-1, 12, ne, k) == 0
@@ -173,7 +176,7 @@ def _masks_and_keys(rnd, K, n, max_runs=16):
                 m = rnd.getrandbits(32) & rnd.getrandbits(32)
             masks.append(m)
         runs = [(w, lo, ln) for w in range(K - 1, -1, -1) for (lo, ln) in _runs_of(masks[w])]
-        if len(runs) <= max_runs:
+        if len(runs) <= max_runs and sum(r[2] for r in runs) <= 255:  # positions are bytes
             break
     const = [rnd.getrandbits(32) & ~m & 0xFFFFFFFF for m in masks]
     pool = [[const[w] | (rnd.getrandbits(32) & masks[w]) for w in range(K)] for _ in range(max(1, n // 3))]
@@ -196,9 +199,9 @@ def _runs_of(m):
 
 
 def _keypack_bytes(runs, K):
-    """The 88-byte packing description (layout of reindex_debug_prefix_pack) for runs listed least
+    """The 104-byte packing description (layout of reindex_debug_prefix_pack) for runs listed least
     significant first as (word, lowest bit, length)."""
-    b = bytearray(88)
+    b = bytearray(104)
     b[0] = 1
     b[1] = sum(r[2] for r in runs) & 0xFF
     b[2] = len(runs)
@@ -211,11 +214,11 @@ def _keypack_bytes(runs, K):
     b[67] = int(all(len(v) == 1 for v in per_word.values()))
     for w, v in per_word.items():
         if len(v) == 1:
-            b[68 + w], b[76 + w] = v[0]
+            b[68 + w], b[84 + w] = v[0]
     return bytes(b)
 
 
-@pytest.mark.parametrize("K", [1, 2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 5, 6, 8, 12, 16])
 def test_key_packing_roundtrip_and_order(L, K):
     """The kernels' key packing, run on the host: packing keeps only the varying bits and keeps
     their order, so packed keys compare exactly like the keys (equal iff equal); unpacking with
@@ -302,3 +305,14 @@ def test_int64_entry_points_host_checks(L):
     assert rx.lib().reindex_workspace_size64((1 << 31) - 1, 4, 10, 3) > 0
     assert rx.reindex_workspace_size((1 << 31) - 1, 4, 10, 3) > 0
     assert rx.reindex_workspace_size(1 << 31, 4, 10, 3) == 0
+
+
+def test_noalloc_limits_stated_for_48_and_64_byte_vertices(L):
+    """The header's stated no-allocation limits for 48- and 64-byte vertices are the largest meshes
+    whose workspace (with as many indices as vertices: the largest case) fits the scratch."""
+    src = open(HEADER).read()
+    m = re.search(r"every mesh of up to ([\d,]+) or ([\d,]+) vertices does", src)
+    stated = [int(m.group(1).replace(",", "")), int(m.group(2).replace(",", ""))]
+    scratch = 20 << 20
+    for S, n in zip((48, 64), stated):
+        assert rx.reindex_workspace_size(n, S, n, 1) <= scratch < rx.reindex_workspace_size(n + 1, S, n + 1, 1)

@@ -74,7 +74,7 @@ SIZES = [(1, 3), (2, 4), (33, 30), (2047, 2047), (2049, 6000), (4096, 4096), (40
          (70001, 70001), (150_000, 40_000)]
 
 
-@pytest.mark.parametrize("S", [4, 8, 12, 16, 20, 24, 32])
+@pytest.mark.parametrize("S", [4, 8, 12, 16, 20, 24, 32, 48, 64])
 @pytest.mark.parametrize("mode", ["random", "dups", "floats", "const"])
 def test_random_meshes(rx, S, mode):
     rng = np.random.default_rng(1000 + S * 10 + ["random", "dups", "floats", "const"].index(mode))
@@ -327,7 +327,7 @@ WIDE_VARIANTS = ["pack=off,swaves=tile,prefix=off", "pack=on,swaves=tile,prefix=
 
 
 @pytest.mark.parametrize("spec", WIDE_VARIANTS)
-@pytest.mark.parametrize("S", [24, 32])
+@pytest.mark.parametrize("S", [24, 32, 48, 64])
 def test_wide_vertices_bit_exact(rx, spec, S):
     """24- and 32-byte vertices (always the "tiles" sort): random words, many duplicates, constant
     low bytes, and a heightfield whose vertices carry normal and texture-coordinate words."""
@@ -344,7 +344,7 @@ def test_wide_vertices_bit_exact(rx, spec, S):
         rx.reindex_tuning_set(S, saved)
 
 
-@pytest.mark.parametrize("S", [24, 32])
+@pytest.mark.parametrize("S", [24, 32, 48, 64])
 def test_wide_vertices_large_heightfield(rx, S):
     """A 1448^2-cell heightfield with attribute words (12.6 M soup vertices of 24 or 32 bytes, the
     prefix sort's default path): D = 1449^2, and every unique vertex and every index equals the
@@ -408,7 +408,7 @@ def _sort_records(rx, S, spec, vtx, idx):
     return rx.profile_collect(), int(out_n.item()), out_v, out_i
 
 
-@pytest.mark.parametrize("S", [12, 16, 24, 32])
+@pytest.mark.parametrize("S", [12, 16, 24, 32, 48, 64])
 def test_prefix_sort_skips_the_full_key_sort(rx, S):
     """Vertices whose 64 most significant varying bits already tell them apart (a heightfield's x, y
     and the top of z): the prefix sort gives the result and every pass of the full-key sort is
@@ -418,11 +418,12 @@ def test_prefix_sort_skips_the_full_key_sort(rx, S):
     if S == 16:
         m = synth.Mesh(vtx=m.vtx[:, :4], idx=m.idx)
     ov, oi = oracle.reindex_sort(m.vtx, m.idx.reshape(-1))
-    recs, D, out_v, out_i = _sort_records(rx, S, "prefix=on,sort=tiles", m.vtx, m.idx)
+    sort, kname = ("chunk", "chunk_scatter") if S >= 48 else ("tiles", "tile_scatter")  # 48, 64: chunk only
+    recs, D, out_v, out_i = _sort_records(rx, S, f"prefix=on,sort={sort}", m.vtx, m.idx)
     assert D == ov.shape[0]
     np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
-    sc = [r for r in recs if r["name"] == "tile_scatter"]  # in launch order: the prefix sort's 8 passes first
+    sc = [r for r in recs if r["name"] == kname]  # in launch order: the prefix sort's 8 passes first
     pre, full = sc[:8], sc[8:]
     assert len(full) == S and all(r["item_bytes"] == 16 for r in pre) and all(r["item_bytes"] == S + 4 for r in full)
     assert sum(not r["skipped"] for r in pre) >= 6
@@ -433,12 +434,12 @@ def test_prefix_sort_skips_the_full_key_sort(rx, S):
     rng = np.random.default_rng(S)
     vtx, idx = random_mesh(rng, 30000, 30000, S // 4, "dups")  # 7 values per word: prefixes collide
     ov, oi = oracle.reindex_sort(vtx, idx)
-    recs, D, out_v, out_i = _sort_records(rx, S, "prefix=on,sort=tiles", vtx, idx[: 30000 // 3 * 3])
+    recs, D, out_v, out_i = _sort_records(rx, S, f"prefix=on,sort={sort}", vtx, idx[: 30000 // 3 * 3])
     ov, oi = oracle.reindex_sort(vtx, idx[: 30000 // 3 * 3])
     assert D == ov.shape[0]
     np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
-    full = [r for r in recs if r["name"] == "tile_scatter"][8:]
+    full = [r for r in recs if r["name"] == kname][8:]
     assert sum(not r["skipped"] for r in full) >= 8
 
 

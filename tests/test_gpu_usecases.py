@@ -27,7 +27,7 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("S", [4, 8, 12, 16, 20, 24, 32])
+@pytest.mark.parametrize("S", [4, 8, 12, 16, 20, 24, 32, 48, 64])
 def test_merge_equals_concatenate_offset_dedup(rx, S):
     """Section 3.2: concatenate the vertex arrays, add each mesh's vertex offset to its indices,
     then remove duplicates -- here across meshes."""
@@ -150,15 +150,18 @@ def test_autotune_keeps_results_exact_and_persists(rx, tmp_path):
     np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
     # explicit settings round-trip, and every variant stays exact
-    for spec in ["sort=pipe,rank=match,hist=peel,grid=tile,swaves=tile,pack=on,prefix=off,chunk=wide,cocc=max,cgrid=0",
-                 "sort=regs,rank=ballot,hist=match,grid=persist,swaves=4,pack=off,prefix=on,chunk=big,cocc=1,cgrid=0",
+    for spec in ["sort=pipe,rank=match,hist=peel,grid=tile,swaves=tile,pack=on,prefix=off,chunk=wide,cocc=max,cgrid=0,"
+                 "dbits=8",
+                 "sort=regs,rank=ballot,hist=match,grid=persist,swaves=4,pack=off,prefix=on,chunk=big,cocc=1,cgrid=0,"
+                 "dbits=8",
                  "sort=tiles,rank=ballot,hist=uniform,grid=persist,swaves=1,pack=off,prefix=auto,chunk=small,cocc=max,"
-                 "cgrid=0",
-                 "sort=tiles,rank=vary,hist=uniform,grid=persist,swaves=tile,pack=on,prefix=off,chunk=deep,cocc=max,cgrid=0",
+                 "cgrid=0,dbits=8",
+                 "sort=tiles,rank=vary,hist=uniform,grid=persist,swaves=tile,pack=on,prefix=off,chunk=deep,cocc=max,"
+                 "cgrid=0,dbits=8",
                  "sort=chunk,rank=match,hist=uniform,grid=persist,swaves=tile,pack=on,prefix=off,chunk=wide,cocc=1,"
-                 "cgrid=4",
+                 "cgrid=4,dbits=7",
                  "sort=chunk,rank=ballot,hist=uniform,grid=persist,swaves=tile,pack=off,prefix=auto,chunk=big,cocc=max,"
-                 "cgrid=0"]:
+                 "cgrid=0,dbits=6"]:
         rx.reindex_tuning_set(12, spec)
         assert rx.reindex_tuning_get(12) == spec
         out_v, out_n, out_i = rx.reindex_mesh(v, i)

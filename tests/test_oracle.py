@@ -143,7 +143,7 @@ def test_brute_force_tiny(oracle_lib, K, trial):
     np.testing.assert_array_equal(r["idxNew"], bi)
 
 
-@pytest.mark.parametrize("stride", [24, 32])
+@pytest.mark.parametrize("stride", [24, 32, 48, 64])
 def test_wide_vertices_extend_the_narrow_result(oracle_lib, stride):
     """Attribute words that are a function of the position words change neither the order nor the
     equality of the vertices: the wide result is the 12-byte result with its attributes appended

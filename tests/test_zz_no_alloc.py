@@ -159,3 +159,26 @@ def test_noalloc_refuses_meshes_over_the_limit(rx):
     i = torch.zeros((10, 3), dtype=torch.int32, device="cuda")
     rc, *_ = _noalloc(rx, v, i)
     assert rc == rx.REINDEX_ERR_UNSUPPORTED
+
+
+def _largest_fitting(rx, S, scratch=20 << 20):
+    """The largest nVtx whose workspace (with as many indices as vertices) fits the scratch."""
+    lo, hi = 1, MAX_VTX
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if rx.reindex_workspace_size(mid, S, mid, 1) <= scratch:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+@pytest.mark.parametrize("words", [12, 16])
+def test_noalloc_48_and_64_byte_vertices(rx, words):
+    """48- and 64-byte vertices: taken up to the largest mesh whose workspace fits the scratch."""
+    n = _largest_fitting(rx, 4 * words)
+    _check(rx, *_mesh(6, n, n // 3, 3, words))
+    v = torch.zeros((n + 2000, words), dtype=torch.int32, device="cuda")
+    i = torch.zeros(((n + 2000) // 3 + 1, 3), dtype=torch.int32, device="cuda")
+    rc, *_ = _noalloc(rx, v, i)
+    assert rc == rx.REINDEX_ERR_UNSUPPORTED
