@@ -115,6 +115,8 @@ SORT_KERNEL_SOURCES = {
                      "paper_2109_09812_gb300/csrc/common.cuh"],
     "chunk_scatter": ["paper_2109_09812_gb300/csrc/k_radix_chunk.cu", "paper_2109_09812_gb300/csrc/radix.cuh",
                       "paper_2109_09812_gb300/csrc/tma.cuh", "paper_2109_09812_gb300/csrc/common.cuh"],
+    # the duplicate-removal kernel (the dominant kernel when it runs)
+    "hash_dedup": ["paper_2109_09812_gb300/csrc/k_dedup.cu", "paper_2109_09812_gb300/csrc/common.cuh"],
 }
 
 
@@ -578,7 +580,8 @@ def sort_pass_roofline(recs, U):
     """The radix scatter's roofline from the per-launch records: (kernel, algorithmic bytes per
     launch, average launch ms, item bytes, launches).  One pass reads and writes every (key, old
     index) item once: 2 * U * item bytes, averaged over the passes that moved data (a call that
-    sorts by key prefix first has 12-byte items in those passes)."""
+    sorts by key prefix first has 12-byte items in those passes).  U is the number of items sorted:
+    the used vertices, or the distinct keys when duplicates were removed first."""
     names = {r["name"] for r in recs}
     kname = next((k for k in ("chunk_scatter", "tile_scatter") if k in names), "onesweep")
     sw = [r for r in recs if r["name"] == kname and not r["skipped"]]
@@ -588,6 +591,60 @@ def sort_pass_roofline(recs, U):
     avg_ms = sum(r["ms"] for r in sw) / len(sw)
     sizes = sorted({r["item_bytes"] for r in sw})
     return kname, total_bytes / len(sw), avg_ms, sizes[0] if len(sizes) == 1 else sizes, len(sw)
+
+
+def dedup_table_slots(N, M):
+    """Slots of the duplicate-removal hash table, as the library sizes it: the smallest power of two
+    of at least 1.25 slots per possible used vertex (min(N, M)), and at least 64."""
+    umax = min(N, M)
+    need, p = umax + umax // 4 + 1, 64
+    while p < need:
+        p *= 2
+    return p
+
+
+def hash_dedup_bytes(N, S, U, D):
+    """Compulsory bytes of one hash_dedup launch: the bitmask N/8 and the vertex array N*S read;
+    oldToNew of every copy 4(U-D), the representatives' items D(S+4) and their digit plane D written."""
+    return N / 8 + N * S + 4 * (U - D) + D * (S + 4) + D
+
+
+def step_roofline(recs, N, S, M, U, D, steps, workload, peak, peak_kind):
+    """The dominant kernel's roofline: the radix scatter, or hash_dedup when duplicates are removed
+    before the sort and it takes longer than all the radix passes together."""
+    dedup = any(r["name"] == "hash_dedup" for r in recs)
+    items = D if dedup else U
+    kname, alg_bytes, avg_ms, item_bytes, n_sweeps = sort_pass_roofline(recs, items)
+    per_pass, count_pass = {}, {}
+    for r in recs:
+        if r["name"] == kname and not r["skipped"]:
+            per_pass.setdefault(f'{r["digit"]}/{r["item_bytes"]}B', []).append(r["ms"])
+        if r["name"] == "tile_count" and not r["skipped"]:
+            count_pass.setdefault(f'{r["digit"]}/{r["item_bytes"]}B', []).append(r["ms"])
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    sort = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "per_pass_ms": {d: round(sum(v) / len(v), 4) for d, v in sorted(per_pass.items())},
+            "count_per_pass_ms": {d: round(sum(v) / len(v), 4) for d, v in sorted(count_pass.items())},
+            "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+            "traffic": None if dedup else ncu_traffic(kname, workload, item_bytes),
+            "algorithmic_bytes_per_launch": alg_bytes, "item_bytes": item_bytes, "items_sorted": items,
+            "avg_launch_ms": avg_ms, "passes_per_step": n_sweeps / steps}
+    hd = [r for r in recs if r["name"] == "hash_dedup" and not r["skipped"]]
+    sort_ms = sum(r["ms"] for r in recs if r["name"] == kname and not r["skipped"])
+    if not hd or sum(r["ms"] for r in hd) <= sort_ms:
+        return sort
+    h_ms = sum(r["ms"] for r in hd) / len(hd)
+    h_bytes = hash_dedup_bytes(N, S, U, D)
+    h_ach = h_bytes / (h_ms / 1e3) / 1e9
+    return {"kernel": "hash_dedup", "bound": "hbm", "achieved": h_ach, "peak": peak, "unit": "GB/s",
+            "frac": h_ach / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+            "traffic": ncu_traffic("hash_dedup", workload), "algorithmic_bytes_per_launch": h_bytes,
+            "avg_launch_ms": h_ms, "launches_per_step": len(hd) / steps,
+            "random_sector_bytes_per_launch": 32 * (2 * U - D),
+            "basis": "compulsory bytes (bitmask and vertex array read, copies' oldToNew, representatives' items "
+                     "and digit plane written); the table probes and key compares add at least one random "
+                     "32-byte sector per used vertex and per copy (random_sector_bytes_per_launch)",
+            "sort_pass": sort}
 
 
 def step_model_bytes(N, S, M, U, D):
@@ -618,6 +675,13 @@ def path_model_bytes(recs, N, S, M, U, D):
             cur = []
     for call in calls:
         prefix = any(r["name"] == "prefix_check" for r in call)
+        if any(r["name"] == "hash_dedup" for r in call):
+            clears = 0
+            for r in call:
+                table = r["name"] == "clear" and clears > 0  # the first clear zeroes the counters
+                clears += r["name"] == "clear"
+                total += _dedup_launch_bytes(r, table, N, S, W, M, U, D)
+            continue
         gated = False
         for r in call:
             n = r["name"]
@@ -629,6 +693,23 @@ def path_model_bytes(recs, N, S, M, U, D):
                 continue
             total += _launch_bytes(r, n, prefix, N, S, W, M, U, D)
     return total, gated_all
+
+
+def _dedup_launch_bytes(r, table, N, S, W, M, U, D):
+    """Algorithmic bytes of one launch of a call that removed duplicates before the sort: the table
+    clear 4*slots (written), hash_dedup (compulsory bytes, hash_dedup_bytes), the sort and the head
+    scan on the D distinct keys, resolve N/8 + 4U + 8(U-D) (bitmask, used oldToNew entries, each
+    copy's representative read and its entry rewritten), remap 12M."""
+    n = r["name"]
+    if r["skipped"]:
+        return 0.0
+    if n == "clear":
+        return 4 * dedup_table_slots(N, M) if table else 0.0
+    if n == "hash_dedup":
+        return hash_dedup_bytes(N, S, U, D)
+    if n == "resolve":
+        return N / 8 + 4 * U + 8 * (U - D)
+    return _launch_bytes(r, n, False, N, S, W, M, D, D)
 
 
 def _launch_bytes(r, n, prefix, N, S, W, M, U, D):
@@ -659,8 +740,9 @@ def _launch_bytes(r, n, prefix, N, S, W, M, U, D):
 def record_traffic(csv_path, kernel, capture, capture_items):
     """Writes profiles/<kernel>_traffic.json from an ncu CSV log (metrics dram__bytes_read.sum and
     dram__bytes_write.sum of one launch of the radix-pass kernel, captured on a workload sorting
-    capture_items 16-byte records), scaled to each full workload by the records it sorts, with the
-    digest of the kernel's current sources."""
+    capture_items 16-byte records, or of hash_dedup on a workload of capture_items used vertices),
+    scaled to each full workload by its used vertices, with the digest of the kernel's current
+    sources."""
     import csv
 
     scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
@@ -675,7 +757,8 @@ def record_traffic(csv_path, kernel, capture, capture_items):
     per = vals["dram__bytes_read.sum"] + vals["dram__bytes_write.sum"]
     full_items = {"heightfield2048": 25165824, "heightfield2048_s24": 25165824, "heightfield2048_s32": 25165824,
                   "tet128": 41943040}
-    rec = {"kernel": kernel, "source_digest": source_digest(SORT_KERNEL_SOURCES[kernel]), "item_bytes": 16,
+    rec = {"kernel": kernel, "source_digest": source_digest(SORT_KERNEL_SOURCES[kernel]),
+           "item_bytes": None if kernel == "hash_dedup" else 16,
            "capture": capture, "capture_items": capture_items,
            "dram_read_bytes": vals["dram__bytes_read.sum"], "dram_write_bytes": vals["dram__bytes_write.sum"],
            "per_launch_bytes_capture": per,
@@ -805,12 +888,8 @@ def run_usecase(args, world, rank, local):
         a = per_kernel.setdefault(key, [0, 0.0])
         a[0] += 1
         a[1] += r["ms"]
-    kname, alg_bytes, avg_ms, item_bytes, n_sweeps = sort_pass_roofline(recs, U)
     peak, peak_kind = load_peaks()
-    roofline = {"kernel": kname, "bound": "hbm", "achieved": alg_bytes / (avg_ms / 1e3) / 1e9, "peak": peak,
-                "unit": "GB/s", "frac": alg_bytes / (avg_ms / 1e3) / 1e9 / peak,
-                "peak_kind": f"{peak_kind} hbm_gbs (copy)", "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
-                "item_bytes": item_bytes, "avg_launch_ms": avg_ms, "passes_per_step": n_sweeps / args.steps}
+    roofline = step_roofline(recs, n_vtx, S, 3 * n_elem, U, D, args.steps, args.workload, peak, peak_kind)
     if rank != 0:
         return
     cpu = None
@@ -901,21 +980,8 @@ def run_ours(args, world, rank, local):
         a = per_kernel.setdefault(key, [0, 0.0])
         a[0] += 1
         a[1] += r["ms"]
-    kname, alg_bytes, avg_ms, item_bytes, n_sweeps = sort_pass_roofline(recs, U)
     peak, peak_kind = load_peaks()
-    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
-    per_pass, count_pass = {}, {}
-    for r in recs:
-        if r["name"] == kname and not r["skipped"]:
-            per_pass.setdefault(f'{r["digit"]}/{r["item_bytes"]}B', []).append(r["ms"])
-        if r["name"] == "tile_count" and not r["skipped"]:
-            count_pass.setdefault(f'{r["digit"]}/{r["item_bytes"]}B', []).append(r["ms"])
-    roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "per_pass_ms": {d: round(sum(v) / len(v), 4) for d, v in sorted(per_pass.items())},
-                "count_per_pass_ms": {d: round(sum(v) / len(v), 4) for d, v in sorted(count_pass.items())},
-                "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                "traffic": ncu_traffic(kname, args.workload, item_bytes), "algorithmic_bytes_per_launch": alg_bytes,
-                "item_bytes": item_bytes, "avg_launch_ms": avg_ms, "passes_per_step": n_sweeps / args.steps}
+    roofline = step_roofline(recs, n_vtx, S, M, U, D, args.steps, args.workload, peak, peak_kind)
 
     # the whole step against two byte models: the fixed one (8-bit digits, all S passes of W-byte
     # items: the full-key method, whatever the call skips) and the bytes the kernels that ran move

@@ -326,16 +326,27 @@ int reindex_debug_pack_keys(const void* pack, int packBytes, int K, const uint32
 reindex_status reindex_stream_status(reindex_stream_t stream);
 
 /* ---- autotuning ---------------------------------------------------------------------------------
- * The library has several kernel variants with identical results: the radix pass (register-tiled
- * with 4096-item tiles, or pipelined through shared memory by the Tensor Memory Accelerator with
- * 2048-4096-item tiles), the digit matching inside a warp (8 ballots or match.any), the compaction
- * histogram method (warp-uniform check, peel, or match.any) and the grid shape (persistent CTAs or
- * one CTA per tile).  reindex_autotune times them on the caller's mesh with whole reindex_mesh_ws
- * runs (coordinate descent, median of `reps` runs each; BLOCKING: it synchronises `stream`) and
- * keeps the fastest for this device and stride, for every later call of this process; if the
- * environment variable REINDEX_TUNE_CACHE names a file, the choice is appended to it and read back
- * by later processes.  out_idx must not alias idx.  desc (optional) receives the chosen
- * configuration, e.g. "sort=regs,rank=ballot,hist=uniform,grid=persist". */
+ * The library has several kernel variants with identical results.  Each is a knob of a
+ * comma-separated spec "name=value,...":
+ *   sort    the radix pass: regs (register-tiled onesweep, 4096-item tiles), pipe (tiles pipelined
+ *           through shared memory by the Tensor Memory Accelerator), tiles (precounted tile
+ *           offsets), chunk (contiguous chunks of bulk-copied tiles), auto
+ *   rank    digit matching inside a warp: ballot, match (match.any), vary (ballots on varying bits)
+ *   hist    compaction histogram: uniform, peel, match;   grid: persist | tile
+ *   swaves  CTAs of the "tiles" scatter: tile (one per tile), 1 or 4 (waves striding over tiles)
+ *   chunk   chunk-sort tile shape: big, small, wide, deep;   cocc: max | 1 | 2 (CTAs per SM)
+ *   cgrid   chunk-sort chunk count cap (0: none);   dbits: radix digit width, 6, 7 or 8 bits
+ *   dedup   hash (remove duplicate vertices with a hash table before the sort, which then orders
+ *           the distinct keys only; single meshes of 8-byte vertices and wider) | off
+ *   dpub    on | off: with dedup=hash, representatives publish their item positions in the table
+ *   pack    key packing: auto, on, off;   prefix: the 64-bit prefix sort for wide keys: auto, on, off
+ * reindex_autotune times them on the caller's mesh with whole reindex_mesh_ws runs (coordinate
+ * descent, median of `reps` runs each; BLOCKING: it synchronises `stream`) and keeps the fastest
+ * for this device and stride, for every later call of this process; if the environment variable
+ * REINDEX_TUNE_CACHE names a file, the choice is appended to it and read back by later processes.
+ * out_idx must not alias idx.  desc (optional) receives the chosen configuration, every knob
+ * named (under 300 characters), cut to descLen - 1 characters and NUL-terminated.  A spec given
+ * to reindex_tuning_set may name any subset; unknown names and values are ignored. */
 reindex_status reindex_autotune(const void* vtx, int64_t nVtx, int vtxStrideBytes,
                                 const int32_t* idx, int64_t nElem, int idxPerElem,
                                 void* out_vtx, int64_t* out_nVtx, int32_t* out_idx,
@@ -376,7 +387,10 @@ typedef enum {
   REINDEX_K_PREFIX_CHECK = 15, /* prefix sort: every used vertex equals the unique vertex it was given */
   REINDEX_K_CHUNK_SCATTER = 16, /* step 3, "chunk" variant: the pass's data movement (its count and
                                    offset kernels report as TILE_COUNT and TILE_OFFSETS) */
-  REINDEX_K_COUNT = 17
+  REINDEX_K_HASH_DEDUP = 17,   /* "hash" variant of steps 2-4: distinct keys by hash table before the
+                                  sort (one representative per key is sorted; copies are tagged) */
+  REINDEX_K_RESOLVE = 18,      /* "hash" variant: copies take their representative's new index */
+  REINDEX_K_COUNT = 19
 } reindex_kernel_id;
 
 void reindex_profile_enable(int on);

@@ -50,7 +50,7 @@ KEYPACK_BYTES = 104
 
 KERNEL_NAMES = ["clear", "used_flags", "compact_hist", "sort_plan", "onesweep", "head_scan", "remap", "finalize",
                 "seg_prepare", "seg_offsets", "tile_count", "tile_offsets", "tile_scatter", "key_masks", "prefix_gate",
-                "prefix_check", "chunk_scatter"]
+                "prefix_check", "chunk_scatter", "hash_dedup", "resolve"]
 
 # Symbols declared in include/reindex.h (checked by the ABI test).
 EXPORTED = ["reindex_status_string", "reindex_workspace_size", "reindex_mesh", "reindex_mesh_ws",
@@ -386,17 +386,17 @@ def reindex_autotune(vtx, idx, ws=None, reps: int = 3, stream=None) -> str:
     out_vtx = torch.empty((min(n_vtx, n_elem * k),) + tuple(vtx.shape[1:]), dtype=vtx.dtype, device=vtx.device)
     out_n = torch.empty(1, dtype=torch.int64, device=vtx.device)
     out_idx = torch.empty_like(idx)
-    buf = ctypes.create_string_buffer(128)
+    buf = ctypes.create_string_buffer(512)
     rc = lib().reindex_autotune(_ptr(vtx), n_vtx, S, _ptr(idx), n_elem, k, _ptr(out_vtx), _ptr(out_n), _ptr(out_idx),
-                                _ptr(ws), ws.numel() * ws.element_size(), reps, _stream_handle(stream), buf, 128)
+                                _ptr(ws), ws.numel() * ws.element_size(), reps, _stream_handle(stream), buf, len(buf))
     if rc:
         raise ReindexError(rc, "reindex_autotune")
     return buf.value.decode()
 
 
 def reindex_tuning_get(stride_bytes: int) -> str:
-    buf = ctypes.create_string_buffer(128)
-    lib().reindex_tuning_get(stride_bytes, buf, 128)
+    buf = ctypes.create_string_buffer(512)
+    lib().reindex_tuning_get(stride_bytes, buf, len(buf))
     return buf.value.decode()
 
 

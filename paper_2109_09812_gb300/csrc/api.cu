@@ -22,8 +22,9 @@ static std::mutex g_cfg_mu;
 static std::map<std::pair<int, int>, LaunchCfg> g_cfg;
 
 // Applies "sort=regs|pipe|tiles|chunk|auto,rank=ballot|match|vary,hist=uniform|peel|match,grid=persist|tile,
-// swaves=tile|1|4,pack=auto|on|off,prefix=auto|on|off,chunk=big|small,cocc=max|1|2" (any subset, in any
-// order).  Every variant computes the same result.
+// swaves=tile|1|4,pack=auto|on|off,prefix=auto|on|off,chunk=big|small|wide|deep,cocc=max|1|2,cgrid=N,
+// dbits=6|7|8,dedup=hash|off,dpub=on|off" (any subset, in any order).  Every variant computes the same
+// result.
 void apply_tuning(LaunchCfg& c, const char* spec) {
   if (!spec) return;
   if (std::strstr(spec, "grid=tile")) c.grid_per_tile = 1;
@@ -45,6 +46,10 @@ void apply_tuning(LaunchCfg& c, const char* spec) {
     const int b = std::atoi(g + 6);
     if (b >= 6 && b <= 8) c.digit_bits = b;
   }
+  if (std::strstr(spec, "dedup=hash")) c.dedup = 1;
+  if (std::strstr(spec, "dedup=off")) c.dedup = 0;
+  if (std::strstr(spec, "dpub=on")) c.dedup_pub = 1;
+  if (std::strstr(spec, "dpub=off")) c.dedup_pub = 0;
   if (std::strstr(spec, "rank=match")) c.rank_mode = kRankMatchAny;
   if (std::strstr(spec, "rank=ballot")) c.rank_mode = kRankBallot;
   if (std::strstr(spec, "rank=vary")) c.rank_mode = kRankBallotVary;
@@ -76,6 +81,8 @@ std::string describe_tuning(const LaunchCfg& c) {
   d += c.chunk_occ ? ",cocc=" + std::to_string(c.chunk_occ) : std::string(",cocc=max");
   d += ",cgrid=" + std::to_string(c.chunk_grid_cap);  // 0: no cap (always written, so specs round-trip)
   d += ",dbits=" + std::to_string(c.digit_bits);
+  d += c.dedup ? ",dedup=hash" : ",dedup=off";
+  d += c.dedup_pub ? ",dpub=on" : ",dpub=off";
   return d;
 }
 
@@ -313,6 +320,39 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const I
     REINDEX_TRY(used_flags(ix, M, nVtx, pp, c, st));
   }
   if (extra && extra->vtx_ready) REINDEX_TRY(cudaStreamWaitEvent(st, extra->vtx_ready, 0));
+  if (c.dedup) {  // distinct keys first (hash table), then the method on them; see k_dedup.cu
+    const uint32_t slots = dedup_table_slots(L);
+    {
+      prof::Scope s(REINDEX_K_CLEAR, -1, st);
+      REINDEX_TRY(launch_clear(p.itemsB, (size_t)slots * 4, c, st));
+    }
+    {
+      prof::Scope s(REINDEX_K_HASH_DEDUP, -1, st);
+      REINDEX_TRY(launch_hash_dedup(S, vtx, nVtx, p, slots, (uint32_t)L.Umax, c, st));
+    }
+    {
+      prof::Scope s(REINDEX_K_SORT_PLAN, -1, st);
+      REINDEX_TRY(launch_sort_plan(S, p, true, false, st));
+    }
+    const uint8_t* skip = prof::skip_buffer(p.plan, st);
+    for (int d = 0; d < S; ++d) REINDEX_TRY(sort_pass(S, d, p, c, st, skip));
+    {
+      prof::Scope s(REINDEX_K_HEAD_SCAN, -1, st);
+      REINDEX_TRY(launch_head_scan(S, p, out_vtx, out_nVtx, (uint32_t)nVtx, c, nullptr, st));
+    }
+    if (extra && extra->heads_done) REINDEX_TRY(cudaEventRecord(extra->heads_done, st));
+    {
+      prof::Scope s(REINDEX_K_RESOLVE, -1, st);
+      REINDEX_TRY(launch_resolve(nVtx, p, c, st));
+    }
+    {
+      prof::Scope s(REINDEX_K_REMAP, -1, st);
+      REINDEX_TRY(remap(ix, M, p, c, st));
+    }
+    prof::Scope s(REINDEX_K_FINALIZE, -1, st);
+    REINDEX_TRY(launch_finalize(p, out_nVtx, st));
+    return REINDEX_OK;
+  }
   if (prefix) {
     LaunchCfg cp = c;  // the passes sort 12-byte keys (8 varying bytes) with the tiles or chunk sort
     cp.sort_kernel = c.sort_kernel == kSortChunk ? kSortChunk : kSortTiles;
@@ -870,7 +910,7 @@ const char* reindex_kernel_name(int kernel) {
                                                "onesweep",  "head_scan",  "remap",        "finalize",
                                                "seg_prepare", "seg_offsets", "tile_count", "tile_offsets",
                                                "tile_scatter", "key_masks", "prefix_gate", "prefix_check",
-                                               "chunk_scatter"};
+                                               "chunk_scatter", "hash_dedup", "resolve"};
   return (kernel >= 0 && kernel < REINDEX_K_COUNT) ? names[kernel] : "unknown";
 }
 

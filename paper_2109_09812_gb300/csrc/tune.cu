@@ -7,6 +7,7 @@
 //          per tile), CTAs of the "tiles" scatter (one per tile | 1 or 4 waves striding over the
 //          tiles), tile size and threads of the chunk sort (2048 or 4096 items, 256-1024 threads)
 //          and its resident CTAs per SM (as many as fit | 1), its radix digit width (8, 7 or 6 bits),
+//          duplicate removal before the sort (hash table, with or without published item positions),
 //          key packing, prefix sort
 // Coordinate descent: each knob in turn takes the value with the lowest median time while the
 // others stay fixed.  The choice applies to every later call on the device and, if the
@@ -111,12 +112,15 @@ reindex_status reindex_autotune(const void* vtx, int64_t nVtx, int S, const int3
                             {"chunk=wide", "chunk=big", "chunk=small", "chunk=deep", nullptr},
                             {"cocc=max", "cocc=1", nullptr, nullptr, nullptr},
                             {"dbits=8", "dbits=7", "dbits=6", nullptr, nullptr},
+                            {"dedup=off", "dedup=hash", nullptr, nullptr, nullptr},
+                            {"dpub=on", "dpub=off", nullptr, nullptr, nullptr},
                             {"pack=auto", "pack=on", "pack=off", nullptr, nullptr},
                             {"prefix=auto", "prefix=on", "prefix=off", nullptr, nullptr}};
-  for (int ki = 0; ki < 10; ++ki) {
+  for (int ki = 0; ki < 12; ++ki) {
     const auto& knob = knobs[ki];
     if (rs != REINDEX_OK) break;
     if (S >= kWideMin && ki < 3) continue;  // 24- and 32-byte keys: the tiles or chunk sort, vary ranking
+    if (ki == 9 && !best.dedup) continue;   // publishing: a variant of the hash table only
     for (const char* v : knob) {
       if (!v) continue;
       LaunchCfg c = best;

@@ -267,7 +267,7 @@ def test_profile_records_every_kernel(rx, sort):
     m = synth.config_mesh(1)
     v, i = to_dev(m.vtx, m.idx)
     saved = rx.reindex_tuning_get(12)
-    rx.reindex_tuning_set(12, f"sort={sort},prefix=off")
+    rx.reindex_tuning_set(12, f"sort={sort},prefix=off,dedup=off")
     rx.profile_collect()
     rx.profile_enable(True)
     try:
@@ -282,7 +282,8 @@ def test_profile_records_every_kernel(rx, sort):
     for k in mine:
         assert names.count(k) == (1 if k == "key_masks" else 12)
     others = {k for ks in SORT_KERNELS.values() for k in ks} - set(mine)
-    assert set(names) == set(rx.KERNEL_NAMES) - {"seg_prepare", "seg_offsets", "prefix_gate", "prefix_check"} - others
+    assert set(names) == (set(rx.KERNEL_NAMES) - {"seg_prepare", "seg_offsets", "prefix_gate", "prefix_check",
+                                                   "hash_dedup", "resolve"} - others)
     # x and y are integers 0..256 as float32: their lowest byte is always zero -> skipped passes
     # (packed keys: the skipped passes are the top digit positions instead)
     sk = {r["digit"]: r["skipped"] for r in recs if r["name"] == mine[0]}
@@ -300,7 +301,9 @@ SORT_VARIANTS = ["sort=regs,rank=ballot,grid=persist,prefix=off", "sort=regs,ran
                  "sort=chunk,chunk=big,cgrid=3,pack=auto", "sort=chunk,chunk=small,cgrid=5,cocc=1,pack=off",
                  "sort=chunk,chunk=wide,cgrid=7,rank=match,pack=on", "sort=chunk,chunk=deep,cgrid=2,pack=off,prefix=off",
                  "sort=chunk,chunk=wide,cgrid=3,dbits=7,rank=ballot,prefix=off",
-                 "sort=chunk,chunk=small,dbits=6,rank=vary,prefix=auto", "sort=chunk,chunk=big,cgrid=5,dbits=6,rank=match"]
+                 "sort=chunk,chunk=small,dbits=6,rank=vary,prefix=auto", "sort=chunk,chunk=big,cgrid=5,dbits=6,rank=match",
+                 "dedup=hash,sort=auto", "dedup=hash,dpub=off,sort=tiles,rank=match",
+                 "dedup=hash,sort=chunk,chunk=big,cgrid=3", "dedup=hash,dbits=7,sort=regs"]
 
 
 @pytest.mark.parametrize("spec", SORT_VARIANTS)
@@ -323,7 +326,8 @@ def test_sort_variants_bit_exact(rx, spec, S):
 WIDE_VARIANTS = ["pack=off,swaves=tile,prefix=off", "pack=on,swaves=tile,prefix=off", "pack=auto,swaves=1",
                  "pack=on,swaves=4", "sort=chunk,chunk=big,cgrid=4,prefix=off", "sort=chunk,chunk=small,prefix=auto",
                  "sort=chunk,chunk=wide,cgrid=3,prefix=off", "sort=chunk,chunk=deep,prefix=auto",
-                 "sort=chunk,chunk=big,cgrid=4,dbits=7,prefix=auto", "sort=chunk,chunk=wide,dbits=6,prefix=off"]
+                 "sort=chunk,chunk=big,cgrid=4,dbits=7,prefix=auto", "sort=chunk,chunk=wide,dbits=6,prefix=off",
+                 "dedup=hash,sort=chunk", "dedup=hash,dpub=off,sort=tiles,cgrid=2"]
 
 
 @pytest.mark.parametrize("spec", WIDE_VARIANTS)
@@ -501,3 +505,39 @@ def test_prefix_sort_host_buffers_and_graph_capture(rx, S):
     assert int(out_n.item()) == ov.shape[0]
     np.testing.assert_array_equal(out_v[: ov.shape[0]].cpu().numpy().view(np.uint32), ov)
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+
+
+@pytest.mark.parametrize("S,kind,pub", [(12, "soup", "on"), (12, "soup", "off"), (16, "tets", "on"),
+                                        (32, "attrs", "on"), (64, "attrs", "off")])
+def test_dedup_hash_full_size(rx, S, kind, pub):
+    """Duplicate removal with the hash table before the sort, on full-size soups (about six copies of
+    every vertex in the triangle soups, twenty in the tet soup), with and without the published item
+    positions: every output element against the oracle."""
+    saved = rx.reindex_tuning_get(S)
+    rx.reindex_tuning_set(S, f"dedup=hash,dpub={pub}")
+    try:
+        if kind == "soup":
+            v, i = synth.heightfield_soup_gpu(2048, 2048, 0.05, seed=2)
+            v = v.view(torch.int32)
+        elif kind == "tets":
+            v, i = synth.tet_soup_gpu(96, 0.03, seed=3)
+            v = v.view(torch.int32)
+        else:
+            v0, i = synth.heightfield_soup_gpu(1024, 1024, 0.05, seed=2)
+            v = synth.with_attributes_gpu(v0.view(torch.int32), (S - 12) // 4, seed=2)
+        rx.profile_collect()
+        rx.profile_enable(True)
+        try:
+            out_v, out_n, out_i = rx.reindex_mesh(v, i)
+            torch.cuda.synchronize()
+        finally:
+            rx.profile_enable(False)
+        names = [r["name"] for r in rx.profile_collect()]
+        assert "hash_dedup" in names and "resolve" in names
+        D = int(out_n.item())
+        ov, oi = oracle.reindex_sort(v.cpu().numpy().view(np.uint32), i.cpu().numpy())
+        assert D == ov.shape[0]
+        np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+        np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+    finally:
+        rx.reindex_tuning_set(S, saved)

@@ -151,17 +151,17 @@ def test_autotune_keeps_results_exact_and_persists(rx, tmp_path):
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
     # explicit settings round-trip, and every variant stays exact
     for spec in ["sort=pipe,rank=match,hist=peel,grid=tile,swaves=tile,pack=on,prefix=off,chunk=wide,cocc=max,cgrid=0,"
-                 "dbits=8",
+                 "dbits=8,dedup=off,dpub=on",
                  "sort=regs,rank=ballot,hist=match,grid=persist,swaves=4,pack=off,prefix=on,chunk=big,cocc=1,cgrid=0,"
-                 "dbits=8",
+                 "dbits=8,dedup=off,dpub=off",
                  "sort=tiles,rank=ballot,hist=uniform,grid=persist,swaves=1,pack=off,prefix=auto,chunk=small,cocc=max,"
-                 "cgrid=0,dbits=8",
+                 "cgrid=0,dbits=8,dedup=off,dpub=on",
                  "sort=tiles,rank=vary,hist=uniform,grid=persist,swaves=tile,pack=on,prefix=off,chunk=deep,cocc=max,"
-                 "cgrid=0,dbits=8",
+                 "cgrid=0,dbits=8,dedup=off,dpub=on",
                  "sort=chunk,rank=match,hist=uniform,grid=persist,swaves=tile,pack=on,prefix=off,chunk=wide,cocc=1,"
-                 "cgrid=4,dbits=7",
+                 "cgrid=4,dbits=7,dedup=hash,dpub=off",
                  "sort=chunk,rank=ballot,hist=uniform,grid=persist,swaves=tile,pack=off,prefix=auto,chunk=big,cocc=max,"
-                 "cgrid=0,dbits=6"]:
+                 "cgrid=0,dbits=6,dedup=off,dpub=on"]:
         rx.reindex_tuning_set(12, spec)
         assert rx.reindex_tuning_get(12) == spec
         out_v, out_n, out_i = rx.reindex_mesh(v, i)
