@@ -334,6 +334,30 @@ def tet_measure(rx, torch, dev, local, steps, autotune=True):
             "unique_out": D, "steps": steps, "tuning": rx.reindex_tuning_get(16), "clocks": clocks.summary()}
 
 
+class BatchedTuning:
+    """Sets a tuning spec for the key sizes of batched calls (S + 4 bytes: mesh id and vertex, for
+    4- to 16-byte vertices) and restores the previous settings on exit; spec "default" leaves the
+    library's configuration.  The autotuner times single-mesh calls, so batched calls and serving
+    are configured here, explicitly; `desc` is the configuration in force for 16-byte keys (12-byte
+    vertices), reported with the records."""
+
+    def __init__(self, rx, spec):
+        self.rx, self.spec, self.saved = rx, spec, {}
+
+    def __enter__(self):
+        if self.spec and self.spec != "default":
+            for S in (8, 12, 16, 20):
+                self.saved[S] = self.rx.reindex_tuning_get(S)
+                self.rx.reindex_tuning_set(S, self.spec)
+        self.desc = self.rx.reindex_tuning_get(16)
+        return self
+
+    def __exit__(self, *exc):
+        for S, t in self.saved.items():
+            self.rx.reindex_tuning_set(S, t)
+        return False
+
+
 def batched_measure(rx, torch, dev, local, steps, warmup):
     """Batched path on the 4096-mesh workload (generated on the device, bit-identical to the host
     generator): one CUDA-graph replay of reindex_meshes over all meshes vs one reindex_mesh_ws
@@ -437,7 +461,8 @@ def run_batched_bench(args, world, rank, local):
     rxbuild.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    b = batched_measure(rx, torch, dev, local, args.steps, args.warmup)
+    with BatchedTuning(rx, args.batched_tuning) as bt:
+        b = batched_measure(rx, torch, dev, local, args.steps, args.warmup)
     line = {
         "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": b["ms_graph_replay"], "higher_is_better": True, "scaling": "weak",
@@ -446,7 +471,7 @@ def run_batched_bench(args, world, rank, local):
                    "n_elem": b["n_elem"], "unique_out": b["unique_out"], "parallelism": f"replicas x{world}",
                    "l2": b["l2"]},
         "per_mesh_loop": b["per_mesh_loop"], "batched_vs_per_mesh": b["batched_vs_per_mesh"],
-        "identical_results": b["identical_results"], "clocks": b["clocks"],
+        "identical_results": b["identical_results"], "clocks": b["clocks"], "tuning": bt.desc,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -537,7 +562,8 @@ def run_serving_bench(args, world, rank, local):
     rxbuild.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    m = serving_measure(rx, torch, dev, local, args.requests, [float(x) for x in args.loads.split(",")])
+    with BatchedTuning(rx, args.batched_tuning) as bt:
+        m = serving_measure(rx, torch, dev, local, args.requests, [float(x) for x in args.loads.split(",")])
     loads = m["loads"]
     head = loads.get("0.70") or next(iter(loads.values()))
     line = {
@@ -547,7 +573,7 @@ def run_serving_bench(args, world, rank, local):
         "config": {"workload": WORKLOADS[args.workload][0], "requests": args.requests,
                    "mean_elements": m["mean_elements"], "parallelism": f"replicas x{world}", "headline_load": 0.7},
         "latency_ms": {"p50": head["p50_ms"], "p99": head["p99_ms"], "max": head["max_ms"]},
-        "capacity_closed_loop": m["capacity_closed_loop"], "loads": loads,
+        "capacity_closed_loop": m["capacity_closed_loop"], "loads": loads, "tuning": bt.desc,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -1023,8 +1049,10 @@ def run_ours(args, world, rank, local):
     sub = {}
     if world == 1 and args.workload == "heightfield2048" and not args.no_sub:
         sub["tet128"] = tet_measure(rx, torch, dev, local, max(3, min(args.steps, 10)), not args.no_autotune)
-        sub["batched"] = batched_measure(rx, torch, dev, local, max(3, min(args.steps, 10)), 3)
-        srv = serving_measure(rx, torch, dev, local, args.serving_requests, [0.7], calib_n=args.serving_requests)
+        with BatchedTuning(rx, args.batched_tuning) as bt:
+            sub["batched"] = batched_measure(rx, torch, dev, local, max(3, min(args.steps, 10)), 3)
+            srv = serving_measure(rx, torch, dev, local, args.serving_requests, [0.7], calib_n=args.serving_requests)
+        sub["batched"]["tuning"] = bt.desc
         load = srv["loads"]["0.70"]
         sub["serving"] = {"requests": args.serving_requests, "load": 0.7, "mean_elements": srv["mean_elements"],
                           "latency_ms": {"p50": load["p50_ms"], "p99": load["p99_ms"], "max": load["max_ms"]},
@@ -1032,7 +1060,8 @@ def run_ours(args, world, rank, local):
                           "failed": load["failed"], "capacity_closed_loop": srv["capacity_closed_loop"],
                           "stream": "the first requests of the 20,000-request stream (sizes log-uniform in "
                                     "[1e3, 4e6] elements, 70% triangle / 30% tet soups), Poisson arrivals at 0.7 "
-                                    "of the closed-loop capacity measured on the same requests"}
+                                    "of the closed-loop capacity measured on the same requests",
+                          "tuning": bt.desc}
     if rank != 0:
         return
     cpu = None
@@ -1092,6 +1121,8 @@ def main():
     ap.add_argument("--requests", type=int, default=20000, help="serving workload: number of requests")
     ap.add_argument("--loads", default="0.5,0.7,0.9", help="serving workload: offered loads (fractions of capacity)")
     ap.add_argument("--no-sub", action="store_true", help="default workload: skip the batched and serving records")
+    ap.add_argument("--batched-tuning", default="dedup=hash,dpub=off",
+                    help="tuning spec of batched calls and serving (keys of 8-20 bytes), or 'default'")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="default workload: requests of the serving record")
     ap.add_argument("--record-traffic", default=None,

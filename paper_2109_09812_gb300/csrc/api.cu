@@ -482,6 +482,42 @@ static reindex_status run_batched(const void* vtx, int64_t nVtx, int S, const in
     prof::Scope sc(REINDEX_K_USED_FLAGS, -1, st);
     REINDEX_TRY(launch_seg_flags(idx, out_idx, M, seg, p, c, st));
   }
+  if (c.dedup) {  // distinct (mesh id, vertex) keys first (hash table), then the method on them
+    const uint32_t slots = dedup_table_slots(SL.L);
+    {
+      prof::Scope sc(REINDEX_K_CLEAR, -1, st);
+      REINDEX_TRY(launch_clear(p.itemsB, (size_t)slots * 4, c, st));
+    }
+    {
+      prof::Scope sc(REINDEX_K_HASH_DEDUP, -1, st);
+      REINDEX_TRY(launch_hash_dedup(S, vtx, nVtx, p, slots, (uint32_t)SL.L.Umax, c, st, &seg));
+    }
+    {
+      prof::Scope sc(REINDEX_K_SORT_PLAN, -1, st);
+      REINDEX_TRY(launch_sort_plan(S + 4, p, true, false, st));
+    }
+    const uint8_t* skip = prof::skip_buffer(p.plan, st);
+    for (int d = 0; d < S + 4; ++d) REINDEX_TRY(sort_pass(S + 4, d, p, c, st, skip));
+    {
+      prof::Scope sc(REINDEX_K_HEAD_SCAN, -1, st);
+      REINDEX_TRY(launch_head_scan(S + 4, p, out_vtx, total, (uint32_t)nVtx, c, &seg, st));
+    }
+    {
+      prof::Scope sc(REINDEX_K_SEG_OFFSETS, -1, st);
+      REINDEX_TRY(launch_seg_offsets(seg, p.ctrl, st));
+    }
+    {
+      prof::Scope sc(REINDEX_K_RESOLVE, -1, st);
+      REINDEX_TRY(launch_resolve(nVtx, p, c, st));
+    }
+    {
+      prof::Scope sc(REINDEX_K_REMAP, -1, st);
+      REINDEX_TRY(launch_seg_remap(out_idx, M, seg, p, c, st));
+    }
+    prof::Scope sc(REINDEX_K_FINALIZE, -1, st);
+    REINDEX_TRY(launch_finalize(p, total, st));
+    return REINDEX_OK;
+  }
   LaunchCfg cc = cS;  // the sort (configured for S + 4) decides whether histograms are taken
   cc.sort_kernel = c.sort_kernel;
   cc.pack_keys = c.pack_keys;

@@ -40,8 +40,8 @@ struct LaunchCfg {
                                 // longer output runs); every other sort uses 8
   int chunk_grid_cap = 0;       // "chunk" sort: at most this many chunks (0: no cap; small caps give
                                 // every CTA many tiles, e.g. to test the pipeline on small meshes)
-  int dedup = 0;                // 1: remove duplicates with a hash table before the sort (single meshes,
-                                // 8-byte keys and wider); the sort then orders the distinct keys only
+  int dedup = 0;                // 1: remove duplicates with a hash table before the sort (keys of 8
+                                // bytes and wider); the sort then orders the distinct keys only
   int dedup_pub = 1;            // 1: representatives publish their item positions in the hash table
 };
 
@@ -72,7 +72,7 @@ inline LaunchCfg resolve_cfg(LaunchCfg c, int S, int64_t Umax, bool batched = fa
     c.prefix = 0;
   else if (c.prefix < 0)  // 12-byte keys: the two passes saved do not pay for the check (GB300)
     c.prefix = S >= 16 ? 1 : 0;
-  if (batched || S < 8) c.dedup = 0;
+  if (S < 8) c.dedup = 0;
   if (c.dedup) {  // the hash table writes the plane of key byte 0 and the masks: unpacked 8-bit digits
     c.prefix = 0;
     c.pack_keys = 0;
@@ -168,8 +168,9 @@ cudaError_t launch_remap64(const int64_t* idx, int64_t* out_idx, int64_t M, WsPt
 cudaError_t launch_finalize(WsPtrs ws, int64_t* out_nVtx, cudaStream_t st);
 // Duplicate removal before the sort (k_dedup.cu): the table takes the second item buffer.
 uint32_t dedup_table_slots(const WsLayout& L);
+// seg: batched calls ((mesh id, vertex) keys of S + 4 bytes; S = 4 to 16)
 cudaError_t launch_hash_dedup(int S, const void* vtx, int64_t nVtx, WsPtrs ws, uint32_t slots, uint32_t cap,
-                              const LaunchCfg& c, cudaStream_t st);
+                              const LaunchCfg& c, cudaStream_t st, const SegArgs* seg = nullptr);
 cudaError_t launch_resolve(int64_t nVtx, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_gather_elements(const int32_t* idx, int k, int64_t nElem, const int32_t* list, int64_t nSel,
                                   int32_t* out, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);

@@ -130,8 +130,10 @@ __device__ __forceinline__ void load_item_key(const WsPtrs& ws, uint32_t pos, ui
   }
 }
 
-// CTAs per SM the register budget is set for (the grid is one wave of them)
-__host__ __device__ constexpr int dedup_ctas_per_sm(int S, bool pub) { return S <= 24 && !(pub && S == 12) ? 4 : 3; }
+// CTAs per SM the register budget is set for (the grid is one wave of them); SI = key bytes
+__host__ __device__ constexpr int dedup_ctas_per_sm(int SI, bool pub, bool seg) {
+  return SI <= 24 && !((pub || seg) && SI == 12) ? 4 : 3;
+}
 
 // Each warp keeps R rows of 32 vertices in flight (R = 4 for keys of up to 12 bytes, 2 up to 32,
 // else 1): their keys load together, their first table slots load together, and the keys they
@@ -146,11 +148,16 @@ __host__ __device__ constexpr int dedup_ctas_per_sm(int S, bool pub) { return S 
 // the vertex array.  A copy that finds a claim not yet published compares against the owner's key
 // in the vertex array.  Message passing: item stores, fence, slot store (relaxed) by the
 // representative; slot load (relaxed) or compare-and-swap, fence, item loads by the copy.
-template <int S, bool kPub>
-__global__ void __launch_bounds__(kThreads, dedup_ctas_per_sm(S, kPub))
+//
+// kSeg (batched calls): the key is (mesh id, vertex), the mesh id its most significant word, as in
+// the batched compaction; a copy compares the owner's mesh id too (looked up from its index).
+template <int S, bool kPub, bool kSeg>
+__global__ void __launch_bounds__(kThreads, dedup_ctas_per_sm(S + (kSeg ? 4 : 0), kPub, kSeg))
     k_hash_dedup(const void* __restrict__ vtx, int64_t nVtx, WsPtrs ws, uint32_t* __restrict__ table, uint32_t mask,
-                 uint32_t cap) {
-  constexpr int K = S / 4;
+                 uint32_t cap, SegArgs seg) {
+  constexpr int KV = S / 4;             // vertex words
+  constexpr int K = KV + (kSeg ? 1 : 0);  // key words
+  constexpr int SI = 4 * K;             // key bytes of an item
   constexpr int R = K <= 3 ? 4 : (K <= 8 ? 2 : 1);
   Control* ctrl = ws.ctrl;
   if (block_error(ctrl)) return;
@@ -176,7 +183,13 @@ __global__ void __launch_bounds__(kThreads, dedup_ctas_per_sm(S, kPub))
       const uint32_t used = row0 + r < rows ? __ldg(ws.bitmask + row0 + r) : 0u;
       act[r] = (used >> lane) & 1u;
       rep[r] = false;
-      if (i < nVtx) load_key<S>(vtx, i, k[r]);
+      if (i < nVtx) {
+        uint32_t kv[KV];
+        load_key<S>(vtx, i, kv);
+#pragma unroll
+        for (int q = 0; q < KV; ++q) k[r][K - KV + q] = kv[q];
+        if constexpr (kSeg) k[r][0] = seg_mesh(i, seg.vtxOff, 1, seg.blkV, seg.nMeshes);
+      }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) h[r] = act[r] ? key_hash<K>(k[r]) & mask : 0u;
@@ -227,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, dedup_ctas_per_sm(S, kPub))
               bad = true;
               act[r] = false;
             } else {
-              load_item_key<S>(ws, o[r] & ~kPosFlag, ok[r], oid[r], keep);
+              load_item_key<SI>(ws, o[r] & ~kPosFlag, ok[r], oid[r], keep);
               if ((int64_t)oid[r] >= nVtx) {
                 bad = true;
                 act[r] = false;
@@ -242,7 +255,11 @@ __global__ void __launch_bounds__(kThreads, dedup_ctas_per_sm(S, kPub))
             bad = true;
             act[r] = false;
           } else {
-            load_key_keep<S>(vtx, o[r] - 1u, ok[r], keep);
+            uint32_t kv[KV];
+            load_key_keep<S>(vtx, o[r] - 1u, kv, keep);
+#pragma unroll
+            for (int q = 0; q < KV; ++q) ok[r][K - KV + q] = kv[q];
+            if constexpr (kSeg) ok[r][0] = seg_mesh(o[r] - 1u, seg.vtxOff, 1, seg.blkV, seg.nMeshes);
             oid[r] = o[r] - 1u;
           }
         }
@@ -275,11 +292,11 @@ __global__ void __launch_bounds__(kThreads, dedup_ctas_per_sm(S, kPub))
     for (int r = 0; r < R; ++r) {
       if (rep[r]) {
         const uint32_t pos = base + __popc(b[r] & lanemask_lt());
-        Item<S> it;
+        Item<SI> it;
 #pragma unroll
         for (int q = 0; q < K; ++q) it.k[q] = k[r][q];
         it.id = (uint32_t)((row0 + r) * 32 + lane);
-        ItemIO<S>::store(ws.itemsA, ws.idoff, pos, it);
+        ItemIO<SI>::store(ws.itemsA, ws.idoff, pos, it);
         ws.digits[pos] = (uint8_t)(k[r][K - 1] & 0xFFu);  // the first pass's digit: key byte 0
 #pragma unroll
         for (int q = 0; q < K; ++q) {  // key bit masks: over the representatives, i.e. every distinct key
@@ -347,32 +364,43 @@ static int grid_rows(int64_t nVtx, const LaunchCfg& c) {
 
 template <bool kPub>
 static cudaError_t hash_dedup_s(int S, int g, const void* vtx, int64_t nVtx, WsPtrs ws, uint32_t* table,
-                                uint32_t mask, uint32_t cap, cudaStream_t st) {
+                                uint32_t mask, uint32_t cap, const SegArgs* seg, cudaStream_t st) {
+  if (seg) {  // batched: S is the vertex stride (4 to 16 bytes), keys are S + 4 bytes
+    switch (S) {
+      case 4: k_hash_dedup<4, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg); break;
+      case 8: k_hash_dedup<8, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg); break;
+      case 12: k_hash_dedup<12, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg); break;
+      case 16: k_hash_dedup<16, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  const SegArgs none{};
   switch (S) {
-    case 8: k_hash_dedup<8, kPub><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap); break;
-    case 12: k_hash_dedup<12, kPub><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap); break;
-    case 16: k_hash_dedup<16, kPub><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap); break;
-    case 20: k_hash_dedup<20, kPub><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap); break;
-    case 24: k_hash_dedup<24, kPub><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap); break;
-    case 32: k_hash_dedup<32, kPub><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap); break;
-    case 48: k_hash_dedup<48, kPub><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap); break;
-    case 64: k_hash_dedup<64, kPub><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap); break;
+    case 8: k_hash_dedup<8, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
+    case 12: k_hash_dedup<12, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
+    case 16: k_hash_dedup<16, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
+    case 20: k_hash_dedup<20, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
+    case 24: k_hash_dedup<24, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
+    case 32: k_hash_dedup<32, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
+    case 48: k_hash_dedup<48, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
+    case 64: k_hash_dedup<64, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_hash_dedup(int S, const void* vtx, int64_t nVtx, WsPtrs ws, uint32_t slots, uint32_t cap,
-                              const LaunchCfg& c, cudaStream_t st) {
+                              const LaunchCfg& c, cudaStream_t st, const SegArgs* seg) {
   if (nVtx == 0) return cudaSuccess;
   uint32_t* table = reinterpret_cast<uint32_t*>(ws.itemsB);
   const uint32_t mask = slots - 1u;
   // one wave: as many CTAs as the register cap of the kernel lets every SM hold
   int g = grid_rows(nVtx, c);
-  const int wave = c.sms * dedup_ctas_per_sm(S, c.dedup_pub != 0);
+  const int wave = c.sms * dedup_ctas_per_sm(S + (seg ? 4 : 0), c.dedup_pub != 0, seg != nullptr);
   if (g > wave) g = wave;
-  return c.dedup_pub ? hash_dedup_s<true>(S, g, vtx, nVtx, ws, table, mask, cap, st)
-                     : hash_dedup_s<false>(S, g, vtx, nVtx, ws, table, mask, cap, st);
+  return c.dedup_pub ? hash_dedup_s<true>(S, g, vtx, nVtx, ws, table, mask, cap, seg, st)
+                     : hash_dedup_s<false>(S, g, vtx, nVtx, ws, table, mask, cap, seg, st);
 }
 
 cudaError_t launch_resolve(int64_t nVtx, WsPtrs ws, const LaunchCfg& c, cudaStream_t st) {

@@ -91,6 +91,29 @@ def test_batched_sort_variants(rx, spec, S):
         rx.reindex_tuning_set(S + 4, saved)
 
 
+@pytest.mark.parametrize("pub", ["on", "off"])
+@pytest.mark.parametrize("S", [4, 8, 12, 16])
+def test_batched_dedup_hash(rx, S, pub):
+    """Duplicates removed by the hash table before the sort, with the mesh id in the key: every
+    mesh equals the oracle, and equal vertices of different meshes (a shared pool, identical meshes)
+    never merge."""
+    saved = rx.reindex_tuning_get(S + 4)
+    rx.reindex_tuning_set(S + 4, f"dedup=hash,dpub={pub}")
+    try:
+        rng = np.random.default_rng(500 + S)
+        meshes = random_meshes(rng, 31, S // 4, 3)
+        out_v, out_off, out_i = run_batched(rx, *concat(meshes))
+        check_against_oracle(meshes, out_v, out_off, out_i)
+        m = synth.heightfield_soup(20, 17, 0.1, seed=3)
+        vtx = m.vtx if S == 12 else np.ascontiguousarray(
+            np.resize(m.vtx.reshape(-1), (m.vtx.shape[0], S // 4)).astype(np.uint32))
+        same = [(vtx, m.idx)] * 5
+        out_v, out_off, out_i = run_batched(rx, *concat(same))
+        check_against_oracle(same, out_v, out_off, out_i)
+    finally:
+        rx.reindex_tuning_set(S + 4, saved)
+
+
 def test_batched_equals_single_calls(rx):
     meshes = [(m.vtx, m.idx) for m in synth.batched_heightfield(24, seed=9, min_tris=64, max_tris=20_000)]
     out_v, out_off, out_i = run_batched(rx, *concat(meshes))

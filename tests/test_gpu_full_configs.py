@@ -60,7 +60,21 @@ def _run_jobs(jobs):
     assert not bad, f"{len(bad)} mismatches, first: {bad[:3]}"
 
 
-def test_batched_4096_meshes_match_oracle_mesh_by_mesh(rx):
+@pytest.mark.parametrize("tuning", [None, "dedup=hash,dpub=off"])
+def test_batched_4096_meshes_match_oracle_mesh_by_mesh(rx, tuning):
+    """All 4,096 meshes after one graph replay, each against the oracle; with the library's
+    default configuration for 16-byte (mesh id, vertex) keys, and with duplicates removed by the
+    hash table first."""
+    saved = rx.reindex_tuning_get(16)
+    if tuning:
+        rx.reindex_tuning_set(16, tuning)
+    try:
+        _batched_4096(rx)
+    finally:
+        rx.reindex_tuning_set(16, saved)
+
+
+def _batched_4096(rx):
     specs = synth.batched_heightfield_sizes(4096, seed=4)
     parts = [synth.heightfield_soup_gpu(g, gy, uf, s) for (g, gy, uf, s) in specs]
     nv = np.array([int(v.shape[0]) for v, _ in parts], dtype=np.int64)
@@ -116,7 +130,23 @@ def _serving_sample(n_pick=256):
     return [specs[r] for r in sorted(pick)]
 
 
-def test_serving_mix_matches_oracle_request_by_request(rx):
+@pytest.mark.parametrize("tuning", [None, "dedup=hash"])
+def test_serving_mix_matches_oracle_request_by_request(rx, tuning):
+    """256 requests of the serving mix at Poisson arrivals, each against the oracle; with the default
+    configuration, and with duplicates removed by the hash table first (keys of 16 and 20 bytes:
+    triangle and tet requests with their mesh ids)."""
+    saved = {S: rx.reindex_tuning_get(S) for S in (16, 20)}
+    if tuning:
+        for S in saved:
+            rx.reindex_tuning_set(S, tuning)
+    try:
+        _serving_mix(rx)
+    finally:
+        for S, t in saved.items():
+            rx.reindex_tuning_set(S, t)
+
+
+def _serving_mix(rx):
     specs = _serving_sample()
     assert {sp["kind"] for sp in specs} == {"tri", "tet"}
     sizes = [sp["n_elem"] for sp in specs]
