@@ -3,6 +3,7 @@
 // sticky error query and the per-launch timing facility.
 #include <atomic>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <functional>
 #include <string>
@@ -240,6 +241,11 @@ struct PipeExtras {
   bool flags_done = false;
   cudaEvent_t vtx_ready = nullptr;   // the vertex array is complete once this event has fired
   cudaEvent_t heads_done = nullptr;  // recorded once the unique vertices and *out_nVtx are written
+  // hash path: the vertex array arrives in chunks of chunk_vtx vertices (a multiple of 32), chunk c
+  // complete once chunk_ready[c] has fired; each chunk is inserted as soon as it is there
+  int n_chunks = 0;
+  int64_t chunk_vtx = 0;
+  const cudaEvent_t* chunk_ready = nullptr;
 };
 
 // One radix pass (digit d) with the configured kernel variant.
@@ -319,14 +325,23 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const I
     prof::Scope s(REINDEX_K_USED_FLAGS, -1, st);
     REINDEX_TRY(used_flags(ix, M, nVtx, pp, c, st));
   }
-  if (extra && extra->vtx_ready) REINDEX_TRY(cudaStreamWaitEvent(st, extra->vtx_ready, 0));
+  const bool chunked = c.dedup && extra && extra->n_chunks > 0;
+  if (extra && extra->vtx_ready && !chunked) REINDEX_TRY(cudaStreamWaitEvent(st, extra->vtx_ready, 0));
   if (c.dedup) {  // distinct keys first (hash table), then the method on them; see k_dedup.cu
     const uint32_t slots = dedup_table_slots(L);
     {
       prof::Scope s(REINDEX_K_CLEAR, -1, st);
       REINDEX_TRY(launch_clear(p.itemsB, (size_t)slots * 4, c, st));
     }
-    {
+    if (chunked) {  // each chunk of the vertex array as it arrives
+      for (int ch = 0; ch < extra->n_chunks; ++ch) {
+        REINDEX_TRY(cudaStreamWaitEvent(st, extra->chunk_ready[ch], 0));
+        prof::Scope s(REINDEX_K_HASH_DEDUP, -1, st);
+        REINDEX_TRY(launch_hash_dedup(S, vtx, nVtx, p, slots, (uint32_t)L.Umax, c, st, nullptr,
+                                      ch * extra->chunk_vtx, (ch + 1) * extra->chunk_vtx));
+      }
+      if (extra->vtx_ready) REINDEX_TRY(cudaStreamWaitEvent(st, extra->vtx_ready, 0));
+    } else {
       prof::Scope s(REINDEX_K_HASH_DEDUP, -1, st);
       REINDEX_TRY(launch_hash_dedup(S, vtx, nVtx, p, slots, (uint32_t)L.Umax, c, st));
     }
@@ -702,6 +717,12 @@ reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int S, cons
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   WsLayout L;
   L.compute(nVtx, S, M);
+  // The hash path inserts the vertex array chunk by chunk as it arrives (indices first: the used
+  // flags must be complete before the first insertion); the other paths sort after the whole array.
+  const bool dedup = resolve_cfg(launch_cfg(S), S, L.Umax).dedup != 0;
+  constexpr int kMaxChunks = 8;
+  const int64_t chunk_vtx = align_up((size_t)((nVtx + kMaxChunks - 1) / kMaxChunks), 32);
+  const int n_chunks = dedup ? (int)((nVtx + chunk_vtx - 1) / chunk_vtx) : 0;
   const size_t b_vtx = align_up((size_t)nVtx * S, 256), b_idx = align_up((size_t)M * 4, 256);
   const size_t b_out = align_up((size_t)L.Umax * S, 256);
   const size_t total = b_vtx + 2 * b_idx + b_out + 256 + L.total;
@@ -709,10 +730,13 @@ reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int S, cons
   // A second stream carries the vertex upload (while the used flags are set from the indices) and
   // the download of the unique vertices (while the indices are remapped).
   cudaStream_t cs = nullptr;
-  cudaEvent_t ev_alloc = nullptr, ev_vtx = nullptr, ev_heads = nullptr, ev_cs = nullptr;
+  cudaEvent_t ev_alloc = nullptr, ev_vtx = nullptr, ev_heads = nullptr, ev_cs = nullptr, ev_idx = nullptr;
+  cudaEvent_t ev_chunk[kMaxChunks] = {};
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  for (cudaEvent_t* ev : {&ev_alloc, &ev_vtx, &ev_heads, &ev_cs})
+  for (cudaEvent_t* ev : {&ev_alloc, &ev_vtx, &ev_heads, &ev_cs, &ev_idx})
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  for (int ch = 0; ch < n_chunks; ++ch)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_chunk[ch], cudaEventDisableTiming);
   unsigned char* d = nullptr;
   if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d), total, st);
   int64_t D = -1, Dfinal = -1;
@@ -727,12 +751,31 @@ reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int S, cons
     PipeExtras ex;
     ex.vtx_ready = ev_vtx;
     ex.heads_done = ev_heads;
+    ex.n_chunks = n_chunks;
+    ex.chunk_vtx = chunk_vtx;
+    ex.chunk_ready = ev_chunk;
     do {
       if ((e = cudaEventRecord(ev_alloc, st)) != cudaSuccess) break;
       if ((e = cudaStreamWaitEvent(cs, ev_alloc, 0)) != cudaSuccess) break;
-      if ((e = cudaMemcpyAsync(d_vtx, host_vtx, (size_t)nVtx * S, cudaMemcpyHostToDevice, cs)) != cudaSuccess) break;
-      if ((e = cudaEventRecord(ev_vtx, cs)) != cudaSuccess) break;
-      if ((e = cudaMemcpyAsync(d_idx, host_idx, (size_t)M * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+      if (n_chunks > 0) {  // indices, then the vertex array chunk by chunk, on the copy stream
+        if ((e = cudaMemcpyAsync(d_idx, host_idx, (size_t)M * 4, cudaMemcpyHostToDevice, cs)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(ev_idx, cs)) != cudaSuccess) break;
+        for (int ch = 0; ch < n_chunks && e == cudaSuccess; ++ch) {
+          const int64_t lo = ch * chunk_vtx, hi = std::min(nVtx, lo + chunk_vtx);
+          e = cudaMemcpyAsync(static_cast<unsigned char*>(d_vtx) + (size_t)lo * S,
+                              static_cast<const unsigned char*>(host_vtx) + (size_t)lo * S, (size_t)(hi - lo) * S,
+                              cudaMemcpyHostToDevice, cs);
+          if (e == cudaSuccess) e = cudaEventRecord(ev_chunk[ch], cs);
+        }
+        if (e != cudaSuccess) break;
+        if ((e = cudaEventRecord(ev_vtx, cs)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(st, ev_idx, 0)) != cudaSuccess) break;
+      } else {
+        if ((e = cudaMemcpyAsync(d_vtx, host_vtx, (size_t)nVtx * S, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+          break;
+        if ((e = cudaEventRecord(ev_vtx, cs)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(d_idx, host_idx, (size_t)M * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+      }
       if ((e = cudaMemsetAsync(d_n, 0xFF, 8, st)) != cudaSuccess) break;  // -1 unless the head scan runs
       r = run_pipeline(d_vtx, nVtx, S, d_idx, M, d_ovtx, d_n, d_oidx, d_ws, L, st, &ex);
       if (r != REINDEX_OK) break;
@@ -755,8 +798,10 @@ reindex_status reindex_mesh_host(const void* host_vtx, int64_t nVtx, int S, cons
   cudaError_t es = cudaStreamSynchronize(st);
   cudaError_t es2 = cs ? cudaStreamSynchronize(cs) : cudaSuccess;
   D = Dfinal;
-  for (cudaEvent_t ev : {ev_alloc, ev_vtx, ev_heads, ev_cs})
+  for (cudaEvent_t ev : {ev_alloc, ev_vtx, ev_heads, ev_cs, ev_idx})
     if (ev) cudaEventDestroy(ev);
+  for (int ch = 0; ch < n_chunks; ++ch)
+    if (ev_chunk[ch]) cudaEventDestroy(ev_chunk[ch]);
   if (cs) cudaStreamDestroy(cs);
   if (r != REINDEX_OK) return r;
   if (e != cudaSuccess) return cuda_status(e);

@@ -168,9 +168,11 @@ cudaError_t launch_remap64(const int64_t* idx, int64_t* out_idx, int64_t M, WsPt
 cudaError_t launch_finalize(WsPtrs ws, int64_t* out_nVtx, cudaStream_t st);
 // Duplicate removal before the sort (k_dedup.cu): the table takes the second item buffer.
 uint32_t dedup_table_slots(const WsLayout& L);
-// seg: batched calls ((mesh id, vertex) keys of S + 4 bytes; S = 4 to 16)
+// seg: batched calls ((mesh id, vertex) keys of S + 4 bytes; S = 4 to 16).  [vlo, vhi): the vertices
+// this launch inserts (vlo a multiple of 32; vhi < 0: to the end).
 cudaError_t launch_hash_dedup(int S, const void* vtx, int64_t nVtx, WsPtrs ws, uint32_t slots, uint32_t cap,
-                              const LaunchCfg& c, cudaStream_t st, const SegArgs* seg = nullptr);
+                              const LaunchCfg& c, cudaStream_t st, const SegArgs* seg = nullptr, int64_t vlo = 0,
+                              int64_t vhi = -1);
 cudaError_t launch_resolve(int64_t nVtx, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_gather_elements(const int32_t* idx, int k, int64_t nElem, const int32_t* list, int64_t nSel,
                                   int32_t* out, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);

@@ -151,10 +151,13 @@ __host__ __device__ constexpr int dedup_ctas_per_sm(int SI, bool pub, bool seg) 
 //
 // kSeg (batched calls): the key is (mesh id, vertex), the mesh id its most significant word, as in
 // the batched compaction; a copy compares the owner's mesh id too (looked up from its index).
+// A launch inserts the used vertices of rows [row_lo, row_hi) (32 vertices a row): a call may insert
+// the vertex array chunk by chunk, as the chunks arrive, in any order -- the result does not depend
+// on which copy of a key claims its slot first.
 template <int S, bool kPub, bool kSeg>
 __global__ void __launch_bounds__(kThreads, dedup_ctas_per_sm(S + (kSeg ? 4 : 0), kPub, kSeg))
     k_hash_dedup(const void* __restrict__ vtx, int64_t nVtx, WsPtrs ws, uint32_t* __restrict__ table, uint32_t mask,
-                 uint32_t cap, SegArgs seg) {
+                 uint32_t cap, SegArgs seg, int64_t row_lo, int64_t row_hi) {
   constexpr int KV = S / 4;             // vertex words
   constexpr int K = KV + (kSeg ? 1 : 0);  // key words
   constexpr int SI = 4 * K;             // key bytes of an item
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, dedup_ctas_per_sm(S + (kSeg ? 4 : 0)
   Control* ctrl = ws.ctrl;
   if (block_error(ctrl)) return;
   const int lane = threadIdx.x & 31;
-  const int64_t rows = (nVtx + 31) >> 5;
+  const int64_t rows = row_hi;
   const int64_t warp0 = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   uint32_t kor[K], knand[K];
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, dedup_ctas_per_sm(S + (kSeg ? 4 : 0)
   uint32_t pend_h[R], pend_pos[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) pend[r] = false;
-  for (int64_t row0 = warp0 * R; row0 < rows; row0 += nwarps * R) {
+  for (int64_t row0 = row_lo + warp0 * R; row0 < rows; row0 += nwarps * R) {
     uint32_t k[R][K], h[R];
     bool act[R], rep[R];
 #pragma unroll
@@ -364,43 +367,48 @@ static int grid_rows(int64_t nVtx, const LaunchCfg& c) {
 
 template <bool kPub>
 static cudaError_t hash_dedup_s(int S, int g, const void* vtx, int64_t nVtx, WsPtrs ws, uint32_t* table,
-                                uint32_t mask, uint32_t cap, const SegArgs* seg, cudaStream_t st) {
+                                uint32_t mask, uint32_t cap, const SegArgs* seg, int64_t rlo, int64_t rhi,
+                                cudaStream_t st) {
   if (seg) {  // batched: S is the vertex stride (4 to 16 bytes), keys are S + 4 bytes
     switch (S) {
-      case 4: k_hash_dedup<4, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg); break;
-      case 8: k_hash_dedup<8, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg); break;
-      case 12: k_hash_dedup<12, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg); break;
-      case 16: k_hash_dedup<16, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg); break;
+      case 4: k_hash_dedup<4, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg, rlo, rhi); break;
+      case 8: k_hash_dedup<8, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg, rlo, rhi); break;
+      case 12: k_hash_dedup<12, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg, rlo, rhi); break;
+      case 16: k_hash_dedup<16, kPub, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, *seg, rlo, rhi); break;
       default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
   }
   const SegArgs none{};
   switch (S) {
-    case 8: k_hash_dedup<8, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
-    case 12: k_hash_dedup<12, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
-    case 16: k_hash_dedup<16, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
-    case 20: k_hash_dedup<20, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
-    case 24: k_hash_dedup<24, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
-    case 32: k_hash_dedup<32, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
-    case 48: k_hash_dedup<48, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
-    case 64: k_hash_dedup<64, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none); break;
+    case 8: k_hash_dedup<8, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 12: k_hash_dedup<12, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 16: k_hash_dedup<16, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 20: k_hash_dedup<20, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 24: k_hash_dedup<24, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 32: k_hash_dedup<32, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 48: k_hash_dedup<48, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 64: k_hash_dedup<64, kPub, false><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_hash_dedup(int S, const void* vtx, int64_t nVtx, WsPtrs ws, uint32_t slots, uint32_t cap,
-                              const LaunchCfg& c, cudaStream_t st, const SegArgs* seg) {
-  if (nVtx == 0) return cudaSuccess;
+                              const LaunchCfg& c, cudaStream_t st, const SegArgs* seg, int64_t vlo, int64_t vhi) {
+  if (vhi < 0 || vhi > nVtx) vhi = nVtx;
+  if (vlo < 0) vlo = 0;
+  if (vlo % 32 != 0) return cudaErrorInvalidValue;  // whole rows
+  if (vhi <= vlo) return cudaSuccess;
+  const int64_t rlo = vlo / 32, rhi = (vhi + 31) / 32;
   uint32_t* table = reinterpret_cast<uint32_t*>(ws.itemsB);
   const uint32_t mask = slots - 1u;
   // one wave: as many CTAs as the register cap of the kernel lets every SM hold
-  int g = grid_rows(nVtx, c);
+  int g = grid_rows(vhi - vlo, c);
   const int wave = c.sms * dedup_ctas_per_sm(S + (seg ? 4 : 0), c.dedup_pub != 0, seg != nullptr);
   if (g > wave) g = wave;
-  return c.dedup_pub ? hash_dedup_s<true>(S, g, vtx, nVtx, ws, table, mask, cap, seg, st)
-                     : hash_dedup_s<false>(S, g, vtx, nVtx, ws, table, mask, cap, seg, st);
+  return c.dedup_pub ? hash_dedup_s<true>(S, g, vtx, nVtx, ws, table, mask, cap, seg, rlo, rhi, st)
+                     : hash_dedup_s<false>(S, g, vtx, nVtx, ws, table, mask, cap, seg, rlo, rhi, st);
 }
 
 cudaError_t launch_resolve(int64_t nVtx, WsPtrs ws, const LaunchCfg& c, cudaStream_t st) {

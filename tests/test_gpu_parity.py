@@ -241,6 +241,30 @@ def test_host_buffer_variant(rx, G, pinned_in, pinned_out, tets):
         np.testing.assert_array_equal(got_i.numpy().reshape(-1), oi)
 
 
+@pytest.mark.parametrize("G,pinned,tets,pub", [(7, True, False, "off"), (1200, True, False, "off"),
+                                             (300, False, False, "on"), (24, True, True, "on")])
+def test_host_buffer_variant_hash_path(rx, G, pinned, tets, pub):
+    """The host-buffer entry point on the hash path: indices first, then the vertex array in
+    chunks, each chunk inserted into the hash table as soon as it has arrived (7^2 cells: fewer
+    vertices than chunks of 32 rows)."""
+    S = 16 if tets else 12
+    m = synth.tet_soup(G, 0.03, seed=6) if tets else synth.heightfield_soup(G, (3 * G) // 4, 0.05, seed=6)
+    ov, oi = oracle.reindex_sort(m.vtx, m.idx)
+    hv = torch.from_numpy(m.vtx.view(np.int32))
+    hi = torch.from_numpy(m.idx)
+    if pinned:
+        hv, hi = hv.pin_memory(), hi.pin_memory()
+    saved = rx.reindex_tuning_get(S)
+    rx.reindex_tuning_set(S, f"dedup=hash,dpub={pub}")
+    try:
+        for _ in range(2):
+            got_v, got_i = rx.reindex_mesh_host(hv, hi)
+            np.testing.assert_array_equal(got_v.numpy().view(np.uint32), ov)
+            np.testing.assert_array_equal(got_i.numpy().reshape(-1), oi)
+    finally:
+        rx.reindex_tuning_set(S, saved)
+
+
 def test_host_buffer_variant_reports_device_errors(rx):
     m = synth.heightfield_soup(64, 64, 0.0, seed=7)
     idx = m.idx.copy()
