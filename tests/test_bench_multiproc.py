@@ -112,3 +112,40 @@ def test_path_model_counts_the_kernels_that_ran():
     want = 2 * (4 * M + (N * S + N / 8) + (N / 8 + N * S + 16 * U + U) + 8 * (U + 2 * U * 16 + U)
                 + (16 * U + 4 * U + 2 * D * S) + (N / 8 + N * S + 4 * N + D * S) + 12 * M)
     assert gated == 2 * 5 and abs(got - want) < 1e-6
+
+
+def test_hash_path_models():
+    """The hash path: its path bytes count the table clear, the hash kernel, the sort and the head
+    scan on the D distinct keys, resolve and remap; the roofline goes to hash_dedup only while it
+    takes longer than the radix passes together, and then charges one 32-byte sector per probe and
+    per compare on top of the streamed bytes; the sort pass is charged for D items."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    N, S, M, U, D = 1000, 12, 900, 900, 150
+    W = S + 4
+    call = [_rec("clear"), _rec("used_flags"), _rec("clear"), _rec("hash_dedup"), _rec("sort_plan")]
+    for p in range(12):
+        sk = int(p in (0, 4))
+        call += [_rec("tile_count", W, sk), _rec("tile_offsets", W, sk), _rec("chunk_scatter", W, sk)]
+    call += [_rec("head_scan"), _rec("resolve"), _rec("remap"), _rec("finalize")]
+    got, gated = bench.path_model_bytes(call, N, S, M, U, D)
+    slots = bench.dedup_table_slots(N, M)
+    assert slots == 2048  # the smallest power of two >= 1.25 * 900 + 1
+    want = (4 * M + 4 * slots + (N / 8 + N * S + 4 * (U - D) + D * W + D) + 10 * (D + 2 * D * W + D)
+            + (D * W + 4 * D + D * S) + (N / 8 + 4 * U + 8 * (U - D)) + 12 * M)
+    assert gated == 0 and abs(got - want) < 1e-6
+    # the roofline: hash_dedup dominates when it outlasts the ten passes
+    for r in call:
+        r["ms"] = 1.0 if r["name"] == "hash_dedup" else 0.01
+    roof = bench.step_roofline(call, N, S, M, U, D, 1, "none", 1000.0, "test")
+    comp = N / 8 + N * S + 4 * (U - D) + D * (S + 5)
+    assert roof["kernel"] == "hash_dedup" and roof["compulsory_bytes_per_launch"] == comp
+    assert roof["algorithmic_bytes_per_launch"] == comp + 32 * (2 * U - D)
+    assert abs(roof["frac"] - (comp + 32 * (2 * U - D)) / 1e-3 / 1e9 / 1000.0) < 1e-12
+    assert roof["sort_pass"]["items_sorted"] == D
+    assert roof["sort_pass"]["algorithmic_bytes_per_launch"] == 2 * D * W
+    for r in call:
+        r["ms"] = 0.5 if r["name"] == "chunk_scatter" else 0.01
+    roof = bench.step_roofline(call, N, S, M, U, D, 1, "none", 1000.0, "test")
+    assert roof["kernel"] == "chunk_scatter" and roof["items_sorted"] == D
