@@ -116,6 +116,47 @@ def test_merge_and_submesh_with_prefix_sort(rx, S):
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
 
 
+@pytest.mark.parametrize("S,pub", [(8, "on"), (12, "off"), (16, "on"), (32, "off")])
+def test_merge_and_submesh_hash_path(rx, S, pub):
+    """Merging (indices offset into the concatenated vertex array, then the single-mesh hash path)
+    and subset extraction with duplicates removed by the hash table first: two identical patches
+    merge into one, and a subset equals the oracle on the selected elements."""
+    saved = {k: rx.reindex_tuning_get(k) for k in (S, S + 4)}
+    for k in saved:
+        rx.reindex_tuning_set(k, f"dedup=hash,dpub={pub}")
+    try:
+        m0 = synth.heightfield_soup_attrs(40, 30, 0.05, seed=4, stride=S) if S >= 12 else None
+        if m0 is None:  # 8-byte vertices: x, y of the heightfield soup
+            h = synth.heightfield_soup(40, 30, 0.05, seed=4)
+            vtx1, idx1 = np.ascontiguousarray(h.vtx[:, :2]), h.idx
+        else:
+            vtx1, idx1 = m0.vtx, m0.idx
+        vtx = np.concatenate([vtx1, vtx1])
+        n1, e1 = vtx1.shape[0], idx1.shape[0]
+        voff = np.array([0, n1, 2 * n1], np.int64)
+        eoff = np.array([0, e1, 2 * e1], np.int64)
+        idx = np.concatenate([idx1, idx1])
+        ov, oi = oracle.reindex_sort(vtx, np.concatenate([idx1, idx1 + n1]))
+        out_v, out_n, out_i = rx.reindex_merge_meshes(dev(vtx.view(np.int32)), dev(voff), dev(idx), dev(eoff))
+        torch.cuda.synchronize()
+        D = int(out_n.item())
+        assert D == ov.shape[0]
+        np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+        np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+        rng = np.random.default_rng(40 + S)
+        sel = np.flatnonzero(rng.random(e1) < 0.3).astype(np.int32)
+        ov, oi = oracle.reindex_sort(vtx1, idx1[sel])
+        out_v, out_n, out_i = rx.reindex_submesh(dev(vtx1.view(np.int32)), dev(idx1), dev(sel))
+        torch.cuda.synchronize()
+        D = int(out_n.item())
+        assert D == ov.shape[0]
+        np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+        np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+    finally:
+        for k, t in saved.items():
+            rx.reindex_tuning_set(k, t)
+
+
 def test_submesh_bad_element_id(rx):
     m = synth.heightfield_soup(10, 10, 0.0, seed=2)
     sel = np.array([0, 5, m.n_elem], np.int32)

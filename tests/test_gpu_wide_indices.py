@@ -52,6 +52,32 @@ def test_int64_indices_match_oracle(rx, S):
         np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi.astype(np.int64))
 
 
+@pytest.mark.parametrize("S,pub", [(8, "off"), (12, "on"), (16, "off"), (32, "on")])
+def test_int64_indices_hash_path(rx, S, pub):
+    """int64 indices with duplicates removed by the hash table before the sort."""
+    saved = rx.reindex_tuning_get(S)
+    rx.reindex_tuning_set(S, f"dedup=hash,dpub={pub}")
+    try:
+        _int64_cases(rx, S)
+    finally:
+        rx.reindex_tuning_set(S, saved)
+
+
+def _int64_cases(rx, S):
+    rng = np.random.default_rng(700 + S)
+    for n, m in SIZES:
+        vtx, idx = _mesh(rng, n, m * 3 if n > 1 else 3, S // 4)
+        v = torch.from_numpy(vtx.view(np.int32)).cuda()
+        i = torch.from_numpy(idx.reshape(-1, 3)).cuda()
+        out_v, out_n, out_i = rx.reindex_mesh(v, i)
+        torch.cuda.synchronize()
+        D = int(out_n.item())
+        ov, oi = oracle.reindex_sort(vtx, idx.astype(np.int32))
+        assert D == ov.shape[0]
+        np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+        np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi.astype(np.int64))
+
+
 def test_int64_workspace_variant_in_place(rx):
     rng = np.random.default_rng(7)
     vtx, idx = _mesh(rng, 50_000, 60_000, 3)
@@ -94,8 +120,8 @@ def _vertex_value(i):
     return ((np.asarray(i, dtype=np.int64) * 0x9E3779B1) >> 7) & 0xFFF
 
 
-@pytest.mark.parametrize("wide", [False, True])
-def test_more_than_2_30_vertices(rx, wide):
+@pytest.mark.parametrize("wide,words", [(False, 1), (True, 1), (True, 2)])
+def test_more_than_2_30_vertices(rx, wide, words):
     """nVtx = 2^30 + 5,000 four-byte vertices (filled on the device), 300,000 indices spread over
     the whole range including both sides of 2^30 and the last vertex.  Only the used vertices
     matter to the result, so the oracle runs on them alone: the referenced vertices' values and the
@@ -108,12 +134,23 @@ def test_more_than_2_30_vertices(rx, wide):
     ar = torch.arange(n, device="cuda", dtype=torch.int64)
     v = (((ar * 0x9E3779B1) >> 7) & 0xFFF).to(torch.int32).reshape(n, 1)
     del ar
+    if words == 2:  # 8-byte vertices (value, 0) on the hash path: owner indices beyond 2^30 in the table
+        v = torch.cat([v, torch.zeros_like(v)], dim=1)
     i = torch.from_numpy(idx.reshape(-1, 3) if wide else idx.astype(np.int32).reshape(-1, 3)).cuda()
-    out_v, out_n, out_i = rx.reindex_mesh(v, i)
-    torch.cuda.synchronize()
+    saved = rx.reindex_tuning_get(4 * words)
+    if words == 2:
+        rx.reindex_tuning_set(8, "dedup=hash")
+    try:
+        out_v, out_n, out_i = rx.reindex_mesh(v, i)
+        torch.cuda.synchronize()
+    finally:
+        rx.reindex_tuning_set(4 * words, saved)
     D = int(out_n.item())
     used, pos = np.unique(idx, return_inverse=True)
-    ov, oi = oracle.reindex_sort(_vertex_value(used).astype(np.uint32).reshape(-1, 1), pos.astype(np.int32))
+    uv = _vertex_value(used).astype(np.uint32).reshape(-1, 1)
+    if words == 2:
+        uv = np.concatenate([uv, np.zeros_like(uv)], axis=1)
+    ov, oi = oracle.reindex_sort(uv, pos.astype(np.int32))
     assert D == ov.shape[0]
     np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)

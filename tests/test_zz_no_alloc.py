@@ -101,6 +101,21 @@ def test_noalloc_wide_vertices_at_the_limit(rx, words):
     _check(rx, *_mesh(4, MAX_VTX, 87_381, 3, words))
 
 
+@pytest.mark.parametrize("pub", ["on", "off"])
+def test_noalloc_hash_path(rx, pub):
+    """With duplicates removed by the hash table before the sort (its table in the same scratch
+    array): calls in a row, small, large and small again, each against the oracle."""
+    saved = rx.reindex_tuning_get(12)
+    rx.reindex_tuning_set(12, f"dedup=hash,dpub={pub}")
+    try:
+        small = _mesh(11, 30_001, 12_000, 3, 3)
+        large = _mesh(12, 200_000, 150_000, 3, 3)
+        for vtx, idx in (small, large, small):
+            _check(rx, vtx, idx)
+    finally:
+        rx.reindex_tuning_set(12, saved)
+
+
 def _cudart():
     """The CUDA runtime library as a separate handle, for the memory-pool queries."""
     cands = ["libcudart.so", "libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so"]
