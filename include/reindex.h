@@ -55,7 +55,8 @@
  *     128-bit vector loads and stores).
  *   - nVtx <= 2^31 - 1 (INT32_MAX; the look-back status words carry 31-bit counts and the old
  *     vertex index travels as 32 bits) and nElem * idxPerElem <= 2^31 - 1 for int32 indices; the
- *     int64-index entry points (reindex_mesh64*) take up to 2^40 index entries.
+ *     int64-index entry points (reindex_mesh64*) take up to 2^40 index entries, and
+ *     reindex_mesh64 also meshes of up to 2^40 vertices (below).
  *   - out_idx may alias idx (the remap reads and writes the same slot in one thread).  No
  *     other output may overlap an input.
  *   - Thread safety: calls may be issued concurrently from several host threads on different
@@ -125,10 +126,17 @@ reindex_status reindex_mesh_ws(const void* vtx, int64_t nVtx, int vtxStrideBytes
  * nElem * idxPerElem entries (8-byte aligned; 16-byte alignment enables vector loads), which may
  * alias.  Everything else -- vertices, result, workspace layout, errors -- is as for the int32
  * entry points; the index arrays no longer cap the element count at 2^31 - 1 indices (up to 2^40
- * here), while nVtx <= 2^31 - 1 still holds (indices beyond nVtx, however large, and negative
- * indices are REINDEX_ERR_INDEX_RANGE; none is truncated to 32 bits).  Section 3.5 of the paper
- * expects other formats to carry over; int64 index buffers are the common one besides int32.
- * reindex_workspace_size64 gives the workspace of reindex_mesh64_ws (0 for unsupported sizes). */
+ * here); indices beyond nVtx, however large, and negative indices are REINDEX_ERR_INDEX_RANGE
+ * (none is truncated to 32 bits).  Section 3.5 of the paper expects other formats to carry over;
+ * int64 index buffers are the common one besides int32.
+ * reindex_mesh64 takes meshes of more than 2^31 - 1 vertices too (up to 2^40): the vertex array is
+ * re-indexed in ranges of 2^30 vertices, each range's unique vertices are concatenated and re-indexed
+ * once more, and the two maps are composed for every index -- the same result as a single pass.
+ * Such a call BLOCKS: it synchronises `stream` once per range, and allocates about 4 * nVtx bytes
+ * besides a range's workspace.  The distinct used vertices must number at most 2^31 - 1, else
+ * REINDEX_ERR_UNSUPPORTED; an index-range error is returned (and written into *out_nVtx as usual).
+ * reindex_mesh64_ws keeps nVtx <= 2^31 - 1; reindex_workspace_size64 gives its workspace (0 for
+ * unsupported sizes). */
 size_t reindex_workspace_size64(int64_t nVtx, int vtxStrideBytes, int64_t nElem, int idxPerElem);
 reindex_status reindex_mesh64(const void* vtx, int64_t nVtx, int vtxStrideBytes,
                               const int64_t* idx, int64_t nElem, int idxPerElem,

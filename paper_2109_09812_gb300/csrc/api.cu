@@ -213,10 +213,14 @@ static reindex_status check_args(int64_t nVtx, int S, int64_t nElem, int k, int6
 }
 
 // int64 indices: the same vertex limit; up to 2^40 index entries (nElem * idxPerElem).
-static reindex_status check_args64(int64_t nVtx, int S, int64_t nElem, int k, int64_t* M) {
+// Vertex ranges of meshes beyond kMaxCount vertices (reindex_mesh64 only)
+constexpr int kRangeShift = 30;
+constexpr int64_t kMaxLargeVtx = int64_t(1) << 40;
+
+static reindex_status check_args64(int64_t nVtx, int S, int64_t nElem, int k, int64_t* M, bool large_ok = false) {
   if (!stride_supported(S)) return REINDEX_ERR_UNSUPPORTED;
   if (nVtx < 0 || nElem < 0 || k < 1) return REINDEX_ERR_INVALID_ARG;
-  if (nVtx > kMaxCount) return REINDEX_ERR_UNSUPPORTED;
+  if (nVtx > (large_ok ? kMaxLargeVtx : kMaxCount)) return REINDEX_ERR_UNSUPPORTED;
   if (nElem > (int64_t(1) << 40) / k) return REINDEX_ERR_UNSUPPORTED;
   *M = nElem * (int64_t)k;
   return REINDEX_OK;
@@ -246,6 +250,7 @@ struct PipeExtras {
   int n_chunks = 0;
   int64_t chunk_vtx = 0;
   const cudaEvent_t* chunk_ready = nullptr;
+  bool no_prefix = false;  // the caller's indices are not available for the prefix sort's fallback
 };
 
 // One radix pass (digit d) with the configured kernel variant.
@@ -307,6 +312,7 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const I
                                    void* out_vtx, int64_t* out_nVtx, void* ws, const WsLayout& L, cudaStream_t st,
                                    const PipeExtras* extra = nullptr) {
   LaunchCfg c = resolve_cfg(launch_cfg(S), S, L.Umax);  // one configuration for the whole call
+  if (extra && extra->no_prefix) c.prefix = 0;
   const WsPtrs p = ws_ptrs(ws, L);
   // Prefix sort first: items keep the 64 most significant varying key bits; the full-key sort
   // below then runs only if two different keys shared a prefix (else every kernel of it returns
@@ -680,15 +686,106 @@ reindex_status reindex_mesh64_ws(const void* vtx, int64_t nVtx, int S, const int
   return run_pipeline(vtx, nVtx, S, Indices{idx, out_idx, true}, M, out_vtx, out_nVtx, ws, L, st);
 }
 
+// Meshes of more than kMaxCount vertices (int64 indices): the look-back counts, the 32-bit old-index
+// payload and oldToNew cover at most kMaxCount vertices, so the vertex array is re-indexed in ranges
+// of 2^30 vertices.  Range p takes the used vertices in [p * 2^30, (p + 1) * 2^30) -- its used bits
+// set from all the indices -- through the single-mesh path (no remap), which leaves each of them its
+// rank among the range's unique vertices and writes those unique vertices, sorted, after the previous
+// ranges'.  The concatenated unique vertices (fewer than 2^31, or REINDEX_ERR_UNSUPPORTED) are then
+// re-indexed once more with identity indices, which merges keys that occur in several ranges and
+// gives each range-unique vertex its final index; a last kernel composes the two maps for every
+// index.  The result is the single-level one: the unique vertices are the distinct used keys in key
+// order, and every index resolves to its key's rank.  Synchronises the stream once per range.
+static reindex_status run_large64(const void* vtx, int64_t N, int S, const int64_t* idx, int64_t M, void* out_vtx,
+                                  int64_t* out_nVtx, int64_t* out_idx, cudaStream_t st) {
+  const int64_t part = int64_t(1) << kRangeShift;
+  const int P = (int)((N + part - 1) / part);
+  const int64_t cap = std::min(N, M);  // unique vertices of all ranges together, at most
+  WsLayout Lp;
+  Lp.compute(part, S, std::min(part, M));
+  const size_t b_rank = align_up((size_t)N * 4, 256), b_cat = align_up((size_t)cap * S, 256),
+               b_off = align_up((size_t)(P + 1) * 8, 256);
+  set_pool_threshold();
+  unsigned char* d = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), b_rank + b_cat + b_off + 256 + Lp.total, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  uint32_t* rank = reinterpret_cast<uint32_t*>(d);
+  unsigned char* cat = d + b_rank;
+  int64_t* part_off = reinterpret_cast<int64_t*>(d + b_rank + b_cat);
+  int64_t* cnt = reinterpret_cast<int64_t*>(d + b_rank + b_cat + b_off);
+  void* ws = d + b_rank + b_cat + b_off + 256;
+  std::vector<int64_t> off(P + 1, 0);
+  reindex_status r = REINDEX_OK;
+  const LaunchCfg c0 = launch_cfg(S);
+  for (int pi = 0; pi < P && r == REINDEX_OK && e == cudaSuccess; ++pi) {
+    const int64_t lo = pi * part, n = std::min(part, N - lo);
+    WsLayout L;
+    L.compute(n, S, std::min(n, M));
+    PipeExtras ex;
+    ex.flags_done = true;
+    ex.no_prefix = true;
+    ex.pre = [&](const WsPtrs& w, const LaunchCfg& c) {
+      return launch_used_flags_range64(idx, M, lo, n, N, w, pi == 0, c, st);
+    };
+    r = run_pipeline(static_cast<const unsigned char*>(vtx) + (size_t)lo * S, n, S, Indices{nullptr, nullptr, true},
+                     0, cat + (size_t)off[pi] * S, cnt, ws, L, st, &ex);
+    if (r != REINDEX_OK) break;
+    if ((e = cudaMemcpyAsync(rank + lo, static_cast<unsigned char*>(ws) + L.off_old2new, (size_t)n * 4,
+                             cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      break;
+    int64_t Dp = 0;
+    if ((e = cudaMemcpyAsync(&Dp, cnt, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+    if (Dp < 0) {  // a device-detected error (an index out of range, found with range 0)
+      e = launch_set_count(out_nVtx, Dp, st);
+      r = (reindex_status)(-Dp);
+      break;
+    }
+    off[pi + 1] = off[pi] + Dp;
+  }
+  const int64_t N2 = off[P];
+  if (r == REINDEX_OK && e == cudaSuccess && N2 > kMaxCount) r = REINDEX_ERR_UNSUPPORTED;
+  if (r == REINDEX_OK && e == cudaSuccess) {
+    WsLayout L2;
+    L2.compute(N2, S, N2);
+    const size_t b_map = align_up((size_t)N2 * 4, 256);
+    unsigned char* d2 = nullptr;
+    e = cudaMallocAsync(reinterpret_cast<void**>(&d2), 2 * b_map + L2.total, st);
+    if (e == cudaSuccess) {
+      int32_t* iota = reinterpret_cast<int32_t*>(d2);
+      int32_t* map2 = reinterpret_cast<int32_t*>(d2 + b_map);
+      do {
+        if ((e = cudaMemcpyAsync(part_off, off.data(), (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+          break;
+        if ((e = launch_iota(iota, N2, c0, st)) != cudaSuccess) break;
+        r = run_pipeline(cat, N2, S, Indices{iota, map2, false}, N2, out_vtx, out_nVtx, d2 + 2 * b_map, L2, st);
+        if (r != REINDEX_OK) break;
+        e = launch_remap_two_level(idx, out_idx, M, rank, part_off, map2, kRangeShift, c0, st);
+      } while (0);
+      // the host copy of the offsets must outlive the transfer above
+      cudaError_t es = cudaStreamSynchronize(st);
+      if (e == cudaSuccess) e = es;
+      cudaError_t ef = cudaFreeAsync(d2, st);
+      if (e == cudaSuccess) e = ef;
+    }
+  }
+  cudaError_t ef = cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = ef;
+  if (r != REINDEX_OK) return r;
+  return e == cudaSuccess ? REINDEX_OK : cuda_status(e);
+}
+
 reindex_status reindex_mesh64(const void* vtx, int64_t nVtx, int S, const int64_t* idx, int64_t nElem, int k,
                               void* out_vtx, int64_t* out_nVtx, int64_t* out_idx, reindex_stream_t stream) {
   int64_t M = 0;
-  reindex_status r = check_args64(nVtx, S, nElem, k, &M);
+  reindex_status r = check_args64(nVtx, S, nElem, k, &M, true);
   if (r != REINDEX_OK) return r;
   if ((r = check_ptrs(vtx, nVtx, S, idx, M, out_vtx, out_nVtx, out_idx, 8)) != REINDEX_OK) return r;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (M == 0) return cuda_status(launch_set_count(out_nVtx, 0, st));
   if (nVtx == 0) return REINDEX_ERR_INDEX_RANGE;
+  if (nVtx > kMaxCount) return run_large64(vtx, nVtx, S, idx, M, out_vtx, out_nVtx, out_idx, st);
   WsLayout L;
   L.compute(nVtx, S, M);
   set_pool_threshold();

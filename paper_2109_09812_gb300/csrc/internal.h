@@ -174,6 +174,13 @@ cudaError_t launch_hash_dedup(int S, const void* vtx, int64_t nVtx, WsPtrs ws, u
                               const LaunchCfg& c, cudaStream_t st, const SegArgs* seg = nullptr, int64_t vlo = 0,
                               int64_t vhi = -1);
 cudaError_t launch_resolve(int64_t nVtx, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
+// Meshes of more than 2^31 - 1 vertices, re-indexed in vertex ranges (k_simple.cu)
+cudaError_t launch_used_flags_range64(const int64_t* idx, int64_t M, int64_t lo, int64_t n, int64_t N, WsPtrs ws,
+                                      bool check, const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_iota(int32_t* out, int64_t n, const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_remap_two_level(const int64_t* idx, int64_t* out, int64_t M, const uint32_t* rank,
+                                   const int64_t* part_off, const int32_t* map2, int shift, const LaunchCfg& c,
+                                   cudaStream_t st);
 cudaError_t launch_gather_elements(const int32_t* idx, int k, int64_t nElem, const int32_t* list, int64_t nSel,
                                   int32_t* out, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_set_count(int64_t* out_nVtx, int64_t value, cudaStream_t st);

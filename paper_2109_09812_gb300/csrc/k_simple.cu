@@ -107,6 +107,46 @@ __global__ void __launch_bounds__(kThreads) k_used_flags64(const int64_t* idx, i
   if (bad) record_error(ctrl, kErrIndexRange);
 }
 
+// Meshes of more than 2^31 - 1 vertices (int64 indices) are re-indexed in vertex ranges (see api.cu):
+// k_used_flags_range64 sets the used bits of range [lo, lo + n) only, from all the indices (relative
+// to lo); with `check` it also records indices outside [0, N) as an index-range error.
+__global__ void __launch_bounds__(kThreads) k_used_flags_range64(const int64_t* __restrict__ idx, int64_t M,
+                                                                  int64_t lo, int64_t n, int64_t N,
+                                                                  uint32_t* bitmask, Control* ctrl, int check) {
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < M; i += stride) {
+    const int64_t v = __ldcs(idx + i);
+    if ((uint64_t)v >= (uint64_t)N) {
+      bad = true;
+    } else if (v >= lo && v < lo + n) {
+      const uint32_t r = (uint32_t)(v - lo);
+      atomicOr(bitmask + (r >> 5), 1u << (r & 31u));
+    }
+  }
+  if (bad && check) record_error(ctrl, kErrIndexRange);
+}
+
+// out[j] = j (the identity indices of the second level).
+__global__ void __launch_bounds__(kThreads) k_iota(int32_t* out, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += stride) out[i] = (int32_t)i;
+}
+
+// out[j] = map2[part_off[v >> shift] + rank[v]] for v = idx[j]: the vertex's rank among its range's
+// unique vertices, then that range's unique vertex's final index (indices already range-checked).
+__global__ void __launch_bounds__(kThreads) k_remap_two_level(const int64_t* __restrict__ idx,
+                                                               int64_t* __restrict__ out, int64_t M,
+                                                               const uint32_t* __restrict__ rank,
+                                                               const int64_t* __restrict__ part_off,
+                                                               const int32_t* __restrict__ map2, int shift) {
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < M; i += stride) {
+    const int64_t v = __ldcs(idx + i);
+    __stcs(out + i, (int64_t)__ldg(map2 + __ldg(part_off + (v >> shift)) + __ldg(rank + v)));
+  }
+}
+
 // Digit offsets and pass plan (one CTA of 256 threads; thread t owns digit value t).
 // The radix-sort plan for the P byte positions of a P-byte key.  With upfront histograms
 // (onesweep sort): a byte is trivial if one value holds all U items; exclusive digit offsets from
@@ -460,6 +500,27 @@ cudaError_t launch_used_flags64(const int64_t* idx, int64_t M, int64_t nVtx, WsP
     k_used_flags64<true><<<g, kThreads, 0, st>>>(idx, M, (uint32_t)nVtx, ws.bitmask, ws.ctrl);
   else
     k_used_flags64<false><<<g, kThreads, 0, st>>>(idx, M, (uint32_t)nVtx, ws.bitmask, ws.ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_used_flags_range64(const int64_t* idx, int64_t M, int64_t lo, int64_t n, int64_t N, WsPtrs ws,
+                                      bool check, const LaunchCfg& c, cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  k_used_flags_range64<<<grid_for(M, c, 8), kThreads, 0, st>>>(idx, M, lo, n, N, ws.bitmask, ws.ctrl, check ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iota(int32_t* out, int64_t n, const LaunchCfg& c, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_iota<<<grid_for(n, c, 8), kThreads, 0, st>>>(out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_remap_two_level(const int64_t* idx, int64_t* out, int64_t M, const uint32_t* rank,
+                                   const int64_t* part_off, const int32_t* map2, int shift, const LaunchCfg& c,
+                                   cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  k_remap_two_level<<<grid_for(M, c, 8), kThreads, 0, st>>>(idx, out, M, rank, part_off, map2, shift);
   return cudaGetLastError();
 }
 

@@ -289,11 +289,15 @@ def test_noalloc_scratch_holds_the_largest_accepted_mesh(L):
 
 
 def test_int64_entry_points_host_checks(L):
-    """The int64-index entry points: same vertex limit, 8-byte aligned index arrays, no 2^31 cap on
-    the index count (the workspace grows with min(nVtx, indices) only)."""
+    """The int64-index entry points: 8-byte aligned index arrays, no 2^31 cap on the index count (the
+    workspace grows with min(nVtx, indices) only); reindex_mesh64 takes up to 2^40 vertices (in
+    vertex ranges), its workspace variant up to 2^31 - 1."""
     z = ctypes.c_void_p(0)
     fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails its host checks
-    assert L.reindex_mesh64(fake, 1 << 31, 12, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
+    assert L.reindex_mesh64(fake, (1 << 40) + 1, 12, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
+    assert L.reindex_mesh64_ws(fake, 1 << 31, 12, fake, 3, 3, fake, fake, fake, fake, ctypes.c_size_t(1 << 40), z) \
+        == rx.REINDEX_ERR_UNSUPPORTED
+    assert rx.lib().reindex_workspace_size64(1 << 31, 12, 3, 3) == 0
     assert L.reindex_mesh64(fake, 10, 6, fake, 3, 3, fake, fake, fake, z) == rx.REINDEX_ERR_UNSUPPORTED
     assert L.reindex_mesh64(fake, 10, 12, ctypes.c_void_p((1 << 20) + 4), 3, 3, fake, fake, fake, z) \
         == rx.REINDEX_ERR_INVALID_ARG  # int64 indices must be 8-byte aligned

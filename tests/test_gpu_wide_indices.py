@@ -154,3 +154,47 @@ def test_more_than_2_30_vertices(rx, wide, words):
     assert D == ov.shape[0]
     np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
     np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+
+
+@pytest.mark.parametrize("words,tuning", [(1, None), (2, "dedup=hash")])
+def test_more_than_2_31_vertices(rx, words, tuning):
+    """nVtx = 2^31 + 5,000 vertices (beyond INT32_MAX: re-indexed in vertex ranges of 2^30, then the
+    ranges' unique vertices once more), 300,000 int64 indices reaching both sides of every range
+    boundary and the last vertex; only 4,096 distinct values, so every range shares keys with the
+    others.  The oracle runs on the used vertices alone, relabelled (as for 2^30 + 5,000).  Then one
+    index past the end: REINDEX_ERR_INDEX_RANGE."""
+    n = (1 << 31) + 5000
+    rng = np.random.default_rng(37)
+    idx = rng.integers(0, n, size=300_000).astype(np.int64)
+    edges = [0, (1 << 30) - 1, 1 << 30, (1 << 30) + 1, (1 << 31) - 1, 1 << 31, (1 << 31) + 1, n - 1, n - 2]
+    idx[: len(edges)] = edges
+    ar = torch.arange(n, device="cuda", dtype=torch.int64)
+    v = (((ar * 0x9E3779B1) >> 7) & 0xFFF).to(torch.int32).reshape(n, 1)
+    del ar
+    if words == 2:
+        v = torch.cat([v, torch.zeros_like(v)], dim=1)
+    i = torch.from_numpy(idx.reshape(-1, 3)).cuda()
+    S = 4 * words
+    saved = rx.reindex_tuning_get(S)
+    if tuning:
+        rx.reindex_tuning_set(S, tuning)
+    try:
+        out_v, out_n, out_i = rx.reindex_mesh(v, i)
+        torch.cuda.synchronize()
+        D = int(out_n.item())
+        used, pos = np.unique(idx, return_inverse=True)
+        uv = _vertex_value(used).astype(np.uint32).reshape(-1, 1)
+        if words == 2:
+            uv = np.concatenate([uv, np.zeros_like(uv)], axis=1)
+        ov, oi = oracle.reindex_sort(uv, pos.astype(np.int32))
+        assert D == ov.shape[0]
+        np.testing.assert_array_equal(out_v[:D].cpu().numpy().view(np.uint32), ov)
+        np.testing.assert_array_equal(out_i.cpu().numpy().reshape(-1), oi)
+        bad = idx.copy()
+        bad[4321] = n
+        with pytest.raises(rx.ReindexError) as ei:
+            rx.reindex_mesh(v, torch.from_numpy(bad.reshape(-1, 3)).cuda())
+        assert ei.value.code == rx.REINDEX_ERR_INDEX_RANGE
+        rx.reindex_stream_status()  # clear the sticky word
+    finally:
+        rx.reindex_tuning_set(S, saved)
