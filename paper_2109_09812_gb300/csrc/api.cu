@@ -311,8 +311,9 @@ static cudaError_t remap(const Indices& ix, int64_t M, const WsPtrs& p, const La
 static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const Indices& ix, int64_t M,
                                    void* out_vtx, int64_t* out_nVtx, void* ws, const WsLayout& L, cudaStream_t st,
                                    const PipeExtras* extra = nullptr) {
-  LaunchCfg c = resolve_cfg(launch_cfg(S), S, L.Umax);  // one configuration for the whole call
-  if (extra && extra->no_prefix) c.prefix = 0;
+  LaunchCfg c0 = launch_cfg(S);
+  if (extra && extra->no_prefix) c0.prefix = 0;
+  LaunchCfg c = resolve_cfg(c0, S, L.Umax);  // one configuration for the whole call
   const WsPtrs p = ws_ptrs(ws, L);
   // Prefix sort first: items keep the 64 most significant varying key bits; the full-key sort
   // below then runs only if two different keys shared a prefix (else every kernel of it returns
@@ -333,24 +334,29 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const I
   }
   const bool chunked = c.dedup && extra && extra->n_chunks > 0;
   if (extra && extra->vtx_ready && !chunked) REINDEX_TRY(cudaStreamWaitEvent(st, extra->vtx_ready, 0));
-  if (c.dedup) {  // distinct keys first (hash table), then the method on them; see k_dedup.cu
+  // the hash table's insertion: each chunk of the vertex array as it arrives, or all at once
+  auto hash_insert = [&](const WsPtrs& w, uint32_t slots, bool repmask) -> cudaError_t {
+    if (chunked) {
+      for (int ch = 0; ch < extra->n_chunks; ++ch) {
+        cudaError_t e = cudaStreamWaitEvent(st, extra->chunk_ready[ch], 0);
+        if (e != cudaSuccess) return e;
+        prof::Scope s(REINDEX_K_HASH_DEDUP, -1, st);
+        e = launch_hash_dedup(S, vtx, nVtx, w, slots, (uint32_t)L.Umax, c, st, nullptr, ch * extra->chunk_vtx,
+                              (ch + 1) * extra->chunk_vtx, repmask);
+        if (e != cudaSuccess) return e;
+      }
+      return extra->vtx_ready ? cudaStreamWaitEvent(st, extra->vtx_ready, 0) : cudaSuccess;
+    }
+    prof::Scope s(REINDEX_K_HASH_DEDUP, -1, st);
+    return launch_hash_dedup(S, vtx, nVtx, w, slots, (uint32_t)L.Umax, c, st, nullptr, 0, -1, repmask);
+  };
+  if (c.dedup && !prefix) {  // distinct keys first (hash table), then the method on them; see k_dedup.cu
     const uint32_t slots = dedup_table_slots(L);
     {
       prof::Scope s(REINDEX_K_CLEAR, -1, st);
       REINDEX_TRY(launch_clear(p.itemsB, (size_t)slots * 4, c, st));
     }
-    if (chunked) {  // each chunk of the vertex array as it arrives
-      for (int ch = 0; ch < extra->n_chunks; ++ch) {
-        REINDEX_TRY(cudaStreamWaitEvent(st, extra->chunk_ready[ch], 0));
-        prof::Scope s(REINDEX_K_HASH_DEDUP, -1, st);
-        REINDEX_TRY(launch_hash_dedup(S, vtx, nVtx, p, slots, (uint32_t)L.Umax, c, st, nullptr,
-                                      ch * extra->chunk_vtx, (ch + 1) * extra->chunk_vtx));
-      }
-      if (extra->vtx_ready) REINDEX_TRY(cudaStreamWaitEvent(st, extra->vtx_ready, 0));
-    } else {
-      prof::Scope s(REINDEX_K_HASH_DEDUP, -1, st);
-      REINDEX_TRY(launch_hash_dedup(S, vtx, nVtx, p, slots, (uint32_t)L.Umax, c, st));
-    }
+    REINDEX_TRY(hash_insert(p, slots, false));
     {
       prof::Scope s(REINDEX_K_SORT_PLAN, -1, st);
       REINDEX_TRY(launch_sort_plan(S, p, true, false, st));
@@ -380,7 +386,14 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const I
     const LaunchCfg c12 = launch_cfg(kPrefixItem);
     cp.occ_tiles = c12.occ_tiles;
     for (int k = 0; k < 4; ++k) cp.occ_chunk[k] = c12.occ_chunk[k];
-    {
+    if (c.dedup) {  // the representatives become the used vertices; the key masks come with them
+      const uint32_t slots = dedup_table_slots(L);
+      {
+        prof::Scope s(REINDEX_K_CLEAR, -1, st);
+        REINDEX_TRY(launch_clear(p.itemsB, (size_t)slots * 4, c, st));
+      }
+      REINDEX_TRY(hash_insert(pp, slots, true));
+    } else {
       prof::Scope s(REINDEX_K_KEY_MASKS, -1, st);
       REINDEX_TRY(launch_key_masks(S, vtx, nVtx, pp, c, nullptr, st));
     }
@@ -442,7 +455,10 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const I
   if (extra && extra->heads_done) REINDEX_TRY(cudaEventRecord(extra->heads_done, st));
   {
     prof::Scope s(REINDEX_K_REMAP, -1, st);
-    REINDEX_TRY(remap(ix, M, p, c, st));
+    if (c.dedup)  // the prefix path sorted the representatives: copies go through theirs
+      REINDEX_TRY(launch_remap_rep(ix.idx, ix.out, ix.wide, M, p, c, st));
+    else
+      REINDEX_TRY(remap(ix, M, p, c, st));
   }
   {
     prof::Scope s(REINDEX_K_FINALIZE, -1, st);

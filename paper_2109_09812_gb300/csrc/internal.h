@@ -73,10 +73,9 @@ inline LaunchCfg resolve_cfg(LaunchCfg c, int S, int64_t Umax, bool batched = fa
   else if (c.prefix < 0)  // 12-byte keys: the two passes saved do not pay for the check (GB300)
     c.prefix = S >= 16 ? 1 : 0;
   if (S < 8) c.dedup = 0;
-  if (c.dedup) {  // the hash table writes the plane of key byte 0 and the masks: unpacked 8-bit digits
-    c.prefix = 0;
-    c.pack_keys = 0;
-    c.digit_bits = 8;
+  if (c.dedup && !c.prefix) {  // the hash table writes the plane of key byte 0 and the masks: unpacked
+    c.pack_keys = 0;           // 8-bit digits (with the prefix sort, it marks the representatives and
+    c.digit_bits = 8;          // the prefix path sorts them instead)
     if (!uses_plane(c.sort_kernel)) c.sort_kernel = kSortChunk;
   }
   return c;
@@ -170,9 +169,14 @@ cudaError_t launch_finalize(WsPtrs ws, int64_t* out_nVtx, cudaStream_t st);
 uint32_t dedup_table_slots(const WsLayout& L);
 // seg: batched calls ((mesh id, vertex) keys of S + 4 bytes; S = 4 to 16).  [vlo, vhi): the vertices
 // this launch inserts (vlo a multiple of 32; vhi < 0: to the end).
+// repmask: representatives replace the used bits instead of appending items (single meshes whose
+// sort runs on key prefixes: 12-byte keys and wider; the prefix path then sorts them).
 cudaError_t launch_hash_dedup(int S, const void* vtx, int64_t nVtx, WsPtrs ws, uint32_t slots, uint32_t cap,
                               const LaunchCfg& c, cudaStream_t st, const SegArgs* seg = nullptr, int64_t vlo = 0,
-                              int64_t vhi = -1);
+                              int64_t vhi = -1, bool repmask = false);
+// out = oldToNew[idx], a tagged entry through its representative (int32 or, with wide, int64 indices)
+cudaError_t launch_remap_rep(const void* idx, void* out, bool wide, int64_t M, WsPtrs ws, const LaunchCfg& c,
+                             cudaStream_t st);
 cudaError_t launch_resolve(int64_t nVtx, WsPtrs ws, const LaunchCfg& c, cudaStream_t st);
 // Meshes of more than 2^31 - 1 vertices, re-indexed in vertex ranges (k_simple.cu)
 cudaError_t launch_used_flags_range64(const int64_t* idx, int64_t M, int64_t lo, int64_t n, int64_t N, WsPtrs ws,

@@ -151,10 +151,15 @@ __host__ __device__ constexpr int dedup_ctas_per_sm(int SI, bool pub, bool seg) 
 //
 // kSeg (batched calls): the key is (mesh id, vertex), the mesh id its most significant word, as in
 // the batched compaction; a copy compares the owner's mesh id too (looked up from its index).
+// kRepMask (single meshes of 12-byte vertices and wider whose sort runs on key prefixes):
+// representatives append nothing;
+// each row's used-bit word is replaced by the bits of its representatives (the warp that reads a
+// row's word is the only one that touches it), so that the prefix path's compaction, sort, check
+// and fallback take the representatives as the used vertices; copies still record theirs.
 // A launch inserts the used vertices of rows [row_lo, row_hi) (32 vertices a row): a call may insert
 // the vertex array chunk by chunk, as the chunks arrive, in any order -- the result does not depend
 // on which copy of a key claims its slot first.
-template <int S, bool kPub, bool kSeg>
+template <int S, bool kPub, bool kSeg, bool kRepMask = false>
 __global__ void __launch_bounds__(kThreads, dedup_ctas_per_sm(S + (kSeg ? 4 : 0), kPub, kSeg))
     k_hash_dedup(const void* __restrict__ vtx, int64_t nVtx, WsPtrs ws, uint32_t* __restrict__ table, uint32_t mask,
                  uint32_t cap, SegArgs seg, int64_t row_lo, int64_t row_hi) {
@@ -287,6 +292,20 @@ __global__ void __launch_bounds__(kThreads, dedup_ctas_per_sm(S + (kSeg ? 4 : 0)
       b[r] = __ballot_sync(0xffffffffu, rep[r]);
       tot += __popc(b[r]);
     }
+    if constexpr (kRepMask) {  // the rows' used bits become their representatives' bits
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (lane == 0 && row0 + r < rows) ws.bitmask[row0 + r] = b[r];
+        if (rep[r]) {
+#pragma unroll
+          for (int q = 0; q < K; ++q) {
+            kor[q] |= k[r][q];
+            knand[q] |= ~k[r][q];
+          }
+        }
+      }
+      continue;
+    }
     if (tot == 0) continue;  // warp-uniform
     uint32_t base = 0;
     if (lane == 0) base = atomicAdd(&ctrl->U, tot);
@@ -365,6 +384,22 @@ static int grid_rows(int64_t nVtx, const LaunchCfg& c) {
   return g < 1 ? 1 : (int)g;
 }
 
+static cudaError_t hash_repmask_s(int S, int g, const void* vtx, int64_t nVtx, WsPtrs ws, uint32_t* table,
+                                  uint32_t mask, uint32_t cap, int64_t rlo, int64_t rhi, cudaStream_t st) {
+  const SegArgs none{};
+  switch (S) {
+    case 12: k_hash_dedup<12, false, false, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 16: k_hash_dedup<16, false, false, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 20: k_hash_dedup<20, false, false, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 24: k_hash_dedup<24, false, false, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 32: k_hash_dedup<32, false, false, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 48: k_hash_dedup<48, false, false, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    case 64: k_hash_dedup<64, false, false, true><<<g, kThreads, 0, st>>>(vtx, nVtx, ws, table, mask, cap, none, rlo, rhi); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 template <bool kPub>
 static cudaError_t hash_dedup_s(int S, int g, const void* vtx, int64_t nVtx, WsPtrs ws, uint32_t* table,
                                 uint32_t mask, uint32_t cap, const SegArgs* seg, int64_t rlo, int64_t rhi,
@@ -395,7 +430,8 @@ static cudaError_t hash_dedup_s(int S, int g, const void* vtx, int64_t nVtx, WsP
 }
 
 cudaError_t launch_hash_dedup(int S, const void* vtx, int64_t nVtx, WsPtrs ws, uint32_t slots, uint32_t cap,
-                              const LaunchCfg& c, cudaStream_t st, const SegArgs* seg, int64_t vlo, int64_t vhi) {
+                              const LaunchCfg& c, cudaStream_t st, const SegArgs* seg, int64_t vlo, int64_t vhi,
+                              bool repmask) {
   if (vhi < 0 || vhi > nVtx) vhi = nVtx;
   if (vlo < 0) vlo = 0;
   if (vlo % 32 != 0) return cudaErrorInvalidValue;  // whole rows
@@ -405,10 +441,54 @@ cudaError_t launch_hash_dedup(int S, const void* vtx, int64_t nVtx, WsPtrs ws, u
   const uint32_t mask = slots - 1u;
   // one wave: as many CTAs as the register cap of the kernel lets every SM hold
   int g = grid_rows(vhi - vlo, c);
-  const int wave = c.sms * dedup_ctas_per_sm(S + (seg ? 4 : 0), c.dedup_pub != 0, seg != nullptr);
+  const bool pub = c.dedup_pub != 0 && !repmask;  // (no items to publish with repmask)
+  const int wave = c.sms * dedup_ctas_per_sm(S + (seg ? 4 : 0), pub, seg != nullptr);
   if (g > wave) g = wave;
+  if (repmask) return seg ? cudaErrorInvalidValue : hash_repmask_s(S, g, vtx, nVtx, ws, table, mask, cap, rlo, rhi, st);
   return c.dedup_pub ? hash_dedup_s<true>(S, g, vtx, nVtx, ws, table, mask, cap, seg, rlo, rhi, st)
                      : hash_dedup_s<false>(S, g, vtx, nVtx, ws, table, mask, cap, seg, rlo, rhi, st);
+}
+
+// out[j] = oldToNew[idx[j]], through the representative for a copy (tagged entry): the remap of a
+// call whose representatives were sorted by the prefix path (no resolve pass).  After a full-key
+// fallback every used vertex holds its new index and the second look-up never happens.
+template <typename I>
+__global__ void __launch_bounds__(kThreads) k_remap_rep(const I* idx, I* out, int64_t M, const uint32_t* o2n,
+                                                        const Control* ctrl) {
+  const uint32_t err = ctrl->err;
+  if (err && err != kErrSkip) return;
+  constexpr int kB = 4;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < M; i += stride * kB) {
+    I q[kB];
+    uint32_t v[kB];
+#pragma unroll
+    for (int b = 0; b < kB; ++b)
+      if (i + b * stride < M) q[b] = __ldcs(idx + i + b * stride);
+#pragma unroll
+    for (int b = 0; b < kB; ++b)
+      if (i + b * stride < M) v[b] = __ldg(o2n + q[b]);
+#pragma unroll
+    for (int b = 0; b < kB; ++b)
+      if (i + b * stride < M && (v[b] & kRepTag)) v[b] = __ldg(o2n + (v[b] & ~kRepTag));
+#pragma unroll
+    for (int b = 0; b < kB; ++b)
+      if (i + b * stride < M) __stcs(out + i + b * stride, (I)v[b]);
+  }
+}
+
+cudaError_t launch_remap_rep(const void* idx, void* out, bool wide, int64_t M, WsPtrs ws, const LaunchCfg& c,
+                             cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  int64_t g = (M + kThreads - 1) / kThreads;
+  if (g > (int64_t)c.sms * 8) g = (int64_t)c.sms * 8;
+  if (wide)
+    k_remap_rep<int64_t><<<(int)g, kThreads, 0, st>>>(static_cast<const int64_t*>(idx), static_cast<int64_t*>(out),
+                                                      M, ws.old2new, ws.ctrl);
+  else
+    k_remap_rep<int32_t><<<(int)g, kThreads, 0, st>>>(static_cast<const int32_t*>(idx), static_cast<int32_t*>(out),
+                                                      M, ws.old2new, ws.ctrl);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_resolve(int64_t nVtx, WsPtrs ws, const LaunchCfg& c, cudaStream_t st) {

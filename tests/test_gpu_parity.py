@@ -327,7 +327,8 @@ SORT_VARIANTS = ["sort=regs,rank=ballot,grid=persist,prefix=off", "sort=regs,ran
                  "sort=chunk,chunk=wide,cgrid=3,dbits=7,rank=ballot,prefix=off",
                  "sort=chunk,chunk=small,dbits=6,rank=vary,prefix=auto", "sort=chunk,chunk=big,cgrid=5,dbits=6,rank=match",
                  "dedup=hash,sort=auto", "dedup=hash,dpub=off,sort=tiles,rank=match",
-                 "dedup=hash,sort=chunk,chunk=big,cgrid=3", "dedup=hash,dbits=7,sort=regs"]
+                 "dedup=hash,sort=chunk,chunk=big,cgrid=3", "dedup=hash,dbits=7,sort=regs",
+                 "dedup=hash,prefix=off,sort=chunk", "dedup=hash,prefix=on,dpub=on,sort=tiles"]
 
 
 @pytest.mark.parametrize("spec", SORT_VARIANTS)
@@ -351,7 +352,8 @@ WIDE_VARIANTS = ["pack=off,swaves=tile,prefix=off", "pack=on,swaves=tile,prefix=
                  "pack=on,swaves=4", "sort=chunk,chunk=big,cgrid=4,prefix=off", "sort=chunk,chunk=small,prefix=auto",
                  "sort=chunk,chunk=wide,cgrid=3,prefix=off", "sort=chunk,chunk=deep,prefix=auto",
                  "sort=chunk,chunk=big,cgrid=4,dbits=7,prefix=auto", "sort=chunk,chunk=wide,dbits=6,prefix=off",
-                 "dedup=hash,sort=chunk", "dedup=hash,dpub=off,sort=tiles,cgrid=2"]
+                 "dedup=hash,sort=chunk", "dedup=hash,dpub=off,sort=tiles,cgrid=2",
+                 "dedup=hash,prefix=off,sort=chunk,cgrid=3", "dedup=hash,prefix=off,dpub=on"]
 
 
 @pytest.mark.parametrize("spec", WIDE_VARIANTS)
@@ -532,11 +534,13 @@ def test_prefix_sort_host_buffers_and_graph_capture(rx, S):
 
 
 @pytest.mark.parametrize("S,kind,pub", [(12, "soup", "on"), (12, "soup", "off"), (16, "tets", "on"),
-                                        (32, "attrs", "on"), (64, "attrs", "off")])
+                                        (16, "tets", "on,prefix=off"), (32, "attrs", "on"),
+                                        (32, "attrs", "off,prefix=off"), (64, "attrs", "off")])
 def test_dedup_hash_full_size(rx, S, kind, pub):
     """Duplicate removal with the hash table before the sort, on full-size soups (about six copies of
     every vertex in the triangle soups, twenty in the tet soup), with and without the published item
-    positions: every output element against the oracle."""
+    positions, and for 16-byte keys and wider with the prefix sort of the representatives (the
+    default) or the full-key sort of them: every output element against the oracle."""
     saved = rx.reindex_tuning_get(S)
     rx.reindex_tuning_set(S, f"dedup=hash,dpub={pub}")
     try:
@@ -557,7 +561,11 @@ def test_dedup_hash_full_size(rx, S, kind, pub):
         finally:
             rx.profile_enable(False)
         names = [r["name"] for r in rx.profile_collect()]
-        assert "hash_dedup" in names and "resolve" in names
+        assert "hash_dedup" in names
+        if S == 12 or "prefix=off" in pub:  # hash path: the sort of the representatives' full keys
+            assert "resolve" in names and "prefix_check" not in names
+        else:  # the prefix path sorts the representatives; copies resolve in the remap
+            assert "prefix_check" in names and "resolve" not in names
         D = int(out_n.item())
         ov, oi = oracle.reindex_sort(v.cpu().numpy().view(np.uint32), i.cpu().numpy())
         assert D == ov.shape[0]
