@@ -632,16 +632,18 @@ def dedup_table_slots(N, M):
     return p
 
 
-def hash_dedup_bytes(N, S, U, D):
+def hash_dedup_bytes(N, S, U, D, repmask=False):
     """Compulsory bytes of one hash_dedup launch: the bitmask N/8 and the vertex array N*S read;
-    oldToNew of every copy 4(U-D), the representatives' items D(S+4) and their digit plane D written."""
-    return N / 8 + N * S + 4 * (U - D) + D * (S + 4) + D
+    oldToNew of every copy 4(U-D) written, then either the representatives' items D(S+4) and their
+    digit plane D, or (when the prefix path sorts them) the representatives' bitmask N/8."""
+    return N / 8 + N * S + 4 * (U - D) + (N / 8 if repmask else D * (S + 4) + D)
 
 
 def step_roofline(recs, N, S, M, U, D, steps, workload, peak, peak_kind):
     """The dominant kernel's roofline: the radix scatter, or hash_dedup when duplicates are removed
     before the sort and it takes longer than all the radix passes together."""
     dedup = any(r["name"] == "hash_dedup" for r in recs)
+    repmask = dedup and any(r["name"] == "prefix_check" for r in recs)  # the prefix path sorts the representatives
     items = D if dedup else U
     kname, alg_bytes, avg_ms, item_bytes, n_sweeps = sort_pass_roofline(recs, items)
     per_pass, count_pass = {}, {}
@@ -663,7 +665,7 @@ def step_roofline(recs, N, S, M, U, D, steps, workload, peak, peak_kind):
     if not hd or sum(r["ms"] for r in hd) <= sort_ms:
         return sort
     h_ms = sum(r["ms"] for r in hd) / len(hd)
-    comp = hash_dedup_bytes(N, S, U, D)
+    comp = hash_dedup_bytes(N, S, U, D, repmask)
     rand = 32 * (2 * U - D)
     h_bytes = comp + rand
     h_ach = h_bytes / (h_ms / 1e3) / 1e9
@@ -673,9 +675,10 @@ def step_roofline(recs, N, S, M, U, D, steps, workload, peak, peak_kind):
             "avg_launch_ms": h_ms, "launches_per_step": len(hd) / steps,
             "compulsory_bytes_per_launch": comp, "random_sector_bytes_per_launch": rand,
             "compulsory_frac": comp / (h_ms / 1e3) / 1e9 / peak,
-            "basis": "streamed bytes (bitmask and vertex array read; copies' oldToNew, representatives' items "
-                     "and digit plane written) plus one random 32-byte sector per table probe (one per used "
-                     "vertex) and per key compare (one per copy): N/8 + N*S + 4(U-D) + D(S+5) + 32(2U-D)",
+            "basis": "streamed bytes (bitmask and vertex array read; copies' oldToNew, and the representatives' "
+                     "items and digit plane D(S+5) -- or their bitmask N/8 when the prefix path sorts them -- "
+                     "written) plus one random 32-byte sector per table probe (one per used vertex) and per "
+                     "key compare (one per copy): N/8 + N*S + 4(U-D) + [D(S+5) | N/8] + 32(2U-D)",
             "sort_pass": sort}
 
 
@@ -708,11 +711,17 @@ def path_model_bytes(recs, N, S, M, U, D):
     for call in calls:
         prefix = any(r["name"] == "prefix_check" for r in call)
         if any(r["name"] == "hash_dedup" for r in call):
-            clears = 0
+            clears, gated = 0, False
             for r in call:
-                table = r["name"] == "clear" and clears > 0  # the first clear zeroes the counters
+                if r["name"] == "prefix_gate":
+                    gated = True
+                    continue
+                if gated and r["name"] not in ("remap", "finalize"):
+                    gated_all += 1
+                    continue
+                table = r["name"] == "clear" and clears == 1  # the first clear zeroes the counters
                 clears += r["name"] == "clear"
-                total += _dedup_launch_bytes(r, table, N, S, W, M, U, D)
+                total += _dedup_launch_bytes(r, table, N, S, W, M, U, D, prefix)
             continue
         gated = False
         for r in call:
@@ -727,21 +736,25 @@ def path_model_bytes(recs, N, S, M, U, D):
     return total, gated_all
 
 
-def _dedup_launch_bytes(r, table, N, S, W, M, U, D):
+def _dedup_launch_bytes(r, table, N, S, W, M, U, D, prefix=False):
     """Algorithmic bytes of one launch of a call that removed duplicates before the sort: the table
     clear 4*slots (written), hash_dedup (compulsory bytes, hash_dedup_bytes), the sort and the head
-    scan on the D distinct keys, resolve N/8 + 4U + 8(U-D) (bitmask, used oldToNew entries, each
-    copy's representative read and its entry rewritten), remap 12M."""
+    scan on the D distinct keys (with the prefix path: its compaction, 16-byte records, head scan and
+    check on the D representatives; the gated full-key sort counts 0), resolve N/8 + 4U + 8(U-D)
+    (bitmask, used oldToNew entries, each copy's representative read and its entry rewritten), remap
+    12M (+ 4(U-D) for the copies' second look-up when the prefix path ran)."""
     n = r["name"]
     if r["skipped"]:
         return 0.0
     if n == "clear":
         return 4 * dedup_table_slots(N, M) if table else 0.0
     if n == "hash_dedup":
-        return hash_dedup_bytes(N, S, U, D)
+        return hash_dedup_bytes(N, S, U, D, prefix)
     if n == "resolve":
         return N / 8 + 4 * U + 8 * (U - D)
-    return _launch_bytes(r, n, False, N, S, W, M, D, D)
+    if n == "remap":
+        return 12 * M + (4 * (U - D) if prefix else 0)
+    return _launch_bytes(r, n, prefix, N, S, W, M, D, D)
 
 
 def _launch_bytes(r, n, prefix, N, S, W, M, U, D):

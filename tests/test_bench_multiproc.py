@@ -149,3 +149,30 @@ def test_hash_path_models():
         r["ms"] = 0.5 if r["name"] == "chunk_scatter" else 0.01
     roof = bench.step_roofline(call, N, S, M, U, D, 1, "none", 1000.0, "test")
     assert roof["kernel"] == "chunk_scatter" and roof["items_sorted"] == D
+
+
+def test_hash_and_prefix_path_model():
+    """Hash table plus prefix sort (keys of 12 bytes and wider): the hash kernel writes the
+    representatives' bitmask instead of items, the prefix path's kernels count on the D
+    representatives, the gated full-key sort counts 0, and the remap adds the copies' second look-up."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    N, S, M, U, D = 1000, 32, 900, 900, 150
+    call = [_rec("clear"), _rec("used_flags"), _rec("clear"), _rec("hash_dedup"), _rec("sort_plan"),
+            _rec("compact_hist")]
+    call += [_rec("tile_count", 16), _rec("tile_offsets", 16), _rec("chunk_scatter", 16)] * 8
+    call += [_rec("head_scan"), _rec("prefix_check"), _rec("clear"), _rec("prefix_gate"), _rec("used_flags"),
+             _rec("compact_hist"), _rec("sort_plan"), _rec("chunk_scatter", 36, 1), _rec("head_scan"),
+             _rec("remap"), _rec("finalize")]  # (a gated pass is recorded as skipped)
+    got, gated = bench.path_model_bytes(call, N, S, M, U, D)
+    want = (4 * M + 4 * bench.dedup_table_slots(N, M) + (N / 8 + N * S + 4 * (U - D) + N / 8)
+            + (N / 8 + N * S + 16 * D + D) + 8 * (D + 2 * D * 16 + D) + (16 * D + 4 * D + 2 * D * S)
+            + (N / 8 + N * S + 4 * N + D * S) + 12 * M + 4 * (U - D))
+    assert gated == 5 and abs(got - want) < 1e-6
+    for r in call:
+        r["ms"] = 1.0 if r["name"] == "hash_dedup" else 0.01
+    roof = bench.step_roofline(call, N, S, M, U, D, 1, "none", 1000.0, "test")
+    assert roof["kernel"] == "hash_dedup"
+    assert roof["compulsory_bytes_per_launch"] == N / 8 + N * S + 4 * (U - D) + N / 8
+    assert roof["sort_pass"]["items_sorted"] == D and roof["sort_pass"]["item_bytes"] == 16
