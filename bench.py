@@ -721,7 +721,8 @@ def path_model_bytes(recs, N, S, M, U, D):
                     continue
                 table = r["name"] == "clear" and clears == 1  # the first clear zeroes the counters
                 clears += r["name"] == "clear"
-                total += _dedup_launch_bytes(r, table, N, S, W, M, U, D, prefix)
+                total += _dedup_launch_bytes(r, table, N, S, W, M, U, D, prefix,
+                                             hop2=not any(x["name"] == "resolve" for x in call))
             continue
         gated = False
         for r in call:
@@ -736,13 +737,13 @@ def path_model_bytes(recs, N, S, M, U, D):
     return total, gated_all
 
 
-def _dedup_launch_bytes(r, table, N, S, W, M, U, D, prefix=False):
+def _dedup_launch_bytes(r, table, N, S, W, M, U, D, prefix=False, hop2=True):
     """Algorithmic bytes of one launch of a call that removed duplicates before the sort: the table
     clear 4*slots (written), hash_dedup (compulsory bytes, hash_dedup_bytes), the sort and the head
     scan on the D distinct keys (with the prefix path: its compaction, 16-byte records, head scan and
     check on the D representatives; the gated full-key sort counts 0), resolve N/8 + 4U + 8(U-D)
     (bitmask, used oldToNew entries, each copy's representative read and its entry rewritten), remap
-    12M (+ 4(U-D) for the copies' second look-up when the prefix path ran)."""
+    12M (+ 4(U-D) for the copies' second look-up when no resolve pass ran)."""
     n = r["name"]
     if r["skipped"]:
         return 0.0
@@ -753,7 +754,7 @@ def _dedup_launch_bytes(r, table, N, S, W, M, U, D, prefix=False):
     if n == "resolve":
         return N / 8 + 4 * U + 8 * (U - D)
     if n == "remap":
-        return 12 * M + (4 * (U - D) if prefix else 0)
+        return 12 * M + (4 * (U - D) if hop2 else 0)
     return _launch_bytes(r, n, prefix, N, S, W, M, D, D)
 
 

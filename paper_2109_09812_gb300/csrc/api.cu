@@ -251,6 +251,7 @@ struct PipeExtras {
   int64_t chunk_vtx = 0;
   const cudaEvent_t* chunk_ready = nullptr;
   bool no_prefix = false;  // the caller's indices are not available for the prefix sort's fallback
+  bool o2n_out = false;    // the caller reads oldToNew after the call (every entry a new index)
 };
 
 // One radix pass (digit d) with the configured kernel variant.
@@ -368,13 +369,13 @@ static reindex_status run_pipeline(const void* vtx, int64_t nVtx, int S, const I
       REINDEX_TRY(launch_head_scan(S, p, out_vtx, out_nVtx, (uint32_t)nVtx, c, nullptr, st));
     }
     if (extra && extra->heads_done) REINDEX_TRY(cudaEventRecord(extra->heads_done, st));
-    {
+    if (extra && extra->o2n_out) {  // oldToNew is itself a product: every copy takes its new index
       prof::Scope s(REINDEX_K_RESOLVE, -1, st);
       REINDEX_TRY(launch_resolve(nVtx, p, c, st));
     }
-    {
+    {  // copies go through their representative (a second look-up: cheaper than a resolve pass)
       prof::Scope s(REINDEX_K_REMAP, -1, st);
-      REINDEX_TRY(remap(ix, M, p, c, st));
+      REINDEX_TRY(launch_remap_rep(ix.idx, ix.out, ix.wide, M, p, c, st));
     }
     prof::Scope s(REINDEX_K_FINALIZE, -1, st);
     REINDEX_TRY(launch_finalize(p, out_nVtx, st));
@@ -740,6 +741,7 @@ static reindex_status run_large64(const void* vtx, int64_t N, int S, const int64
     PipeExtras ex;
     ex.flags_done = true;
     ex.no_prefix = true;
+    ex.o2n_out = true;
     ex.pre = [&](const WsPtrs& w, const LaunchCfg& c) {
       return launch_used_flags_range64(idx, M, lo, n, N, w, pi == 0, c, st);
     };

@@ -11,7 +11,9 @@
 //                 equals its own (raw bits) and records that representative in oldToNew, tagged;
 //   (sort, run heads, scan, oldToNew scatter, gather: unchanged, on the D distinct keys -- every
 //    item is a run head, and oldToNew[rep] = its new index)
-//   k_resolve     every tagged oldToNew entry takes its representative's new index.
+//   k_remap_rep   out = oldToNew[idx], a tagged entry through its representative's (single meshes);
+//   k_resolve     every tagged oldToNew entry takes its representative's new index (batched calls,
+//                 and callers that read oldToNew itself), before the ordinary remap.
 // Keys compare by raw bits, so the set of representatives' keys is exactly the set of distinct
 // used keys, and the sorted result (unique vertices in ascending key order, each index's rank) is
 // the paper's, bit for bit, whichever copy became a representative.  The table lives in the sort's

@@ -128,7 +128,7 @@ def test_hash_path_models():
     for p in range(12):
         sk = int(p in (0, 4))
         call += [_rec("tile_count", W, sk), _rec("tile_offsets", W, sk), _rec("chunk_scatter", W, sk)]
-    call += [_rec("head_scan"), _rec("resolve"), _rec("remap"), _rec("finalize")]
+    call += [_rec("head_scan"), _rec("resolve"), _rec("remap"), _rec("finalize")]  # (batched-style: a resolve pass)
     got, gated = bench.path_model_bytes(call, N, S, M, U, D)
     slots = bench.dedup_table_slots(N, M)
     assert slots == 2048  # the smallest power of two >= 1.25 * 900 + 1
