@@ -545,10 +545,6 @@ static reindex_status run_batched(const void* vtx, int64_t nVtx, int S, const in
       REINDEX_TRY(launch_seg_offsets(seg, p.ctrl, st));
     }
     {
-      prof::Scope sc(REINDEX_K_RESOLVE, -1, st);
-      REINDEX_TRY(launch_resolve(nVtx, p, c, st));
-    }
-    {
       prof::Scope sc(REINDEX_K_REMAP, -1, st);
       REINDEX_TRY(launch_seg_remap(out_idx, M, seg, p, c, st));
     }

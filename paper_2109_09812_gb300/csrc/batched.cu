@@ -11,7 +11,8 @@
 //    vertices of different meshes stay distinct, and each mesh's unique vertices come out
 //    contiguous and ascending; the head scan records each mesh's first output vertex)
 //   k_seg_offsets  meshes without used vertices take the next mesh's offset; last = D
-//   k_seg_remap    out_idx[j] = oldToNew[global index] - first output vertex of j's mesh
+//   k_seg_remap    out_idx[j] = oldToNew[global index] - first output vertex of j's mesh (a copy's
+//                  entry on the hash path through its representative's)
 // Every mesh's result is therefore identical to re-indexing it alone.
 #include "internal.h"
 
@@ -102,7 +103,9 @@ __global__ void __launch_bounds__(kThreads) k_seg_remap(int32_t* io, int64_t M, 
   const int64_t t0 = blockIdx.x * (int64_t)kThreads + threadIdx.x, stride = (int64_t)gridDim.x * kThreads;
   for (int64_t j = t0; j < M; j += stride) {
     const uint32_t m = seg_mesh(j, seg.elemOff, seg.k, seg.blkI, seg.nMeshes);
-    io[j] = (int32_t)((int64_t)__ldg(o2n + (uint32_t)io[j]) - seg.outOff[m]);
+    uint32_t v = __ldg(o2n + (uint32_t)io[j]);
+    if (v & kRepTag) v = __ldg(o2n + (v & ~kRepTag));  // a copy (hash path): its representative's
+    io[j] = (int32_t)((int64_t)v - seg.outOff[m]);
   }
 }
 

@@ -165,7 +165,10 @@ cudaError_t launch_used_flags64(const int64_t* idx, int64_t M, int64_t nVtx, WsP
 cudaError_t launch_remap64(const int64_t* idx, int64_t* out_idx, int64_t M, WsPtrs ws, const LaunchCfg& c,
                            cudaStream_t st);
 cudaError_t launch_finalize(WsPtrs ws, int64_t* out_nVtx, cudaStream_t st);
-// Duplicate removal before the sort (k_dedup.cu): the table takes the second item buffer.
+// Duplicate removal before the sort (k_dedup.cu): the table takes the second item buffer.  A copy's
+// oldToNew entry holds kRepTag | its representative's index until the remap looks that up (new
+// indices stay below 2^31, so an untagged entry is a new index).
+constexpr uint32_t kRepTag = 0x80000000u;
 uint32_t dedup_table_slots(const WsLayout& L);
 // seg: batched calls ((mesh id, vertex) keys of S + 4 bytes; S = 4 to 16).  [vlo, vhi): the vertices
 // this launch inserts (vlo a multiple of 32; vhi < 0: to the end).

@@ -11,9 +11,10 @@
 //                 equals its own (raw bits) and records that representative in oldToNew, tagged;
 //   (sort, run heads, scan, oldToNew scatter, gather: unchanged, on the D distinct keys -- every
 //    item is a run head, and oldToNew[rep] = its new index)
-//   k_remap_rep   out = oldToNew[idx], a tagged entry through its representative's (single meshes);
-//   k_resolve     every tagged oldToNew entry takes its representative's new index (batched calls,
-//                 and callers that read oldToNew itself), before the ordinary remap.
+//   k_remap_rep   out = oldToNew[idx], a tagged entry through its representative's (single meshes;
+//                 batched calls: k_seg_remap does the same);
+//   k_resolve     every tagged oldToNew entry takes its representative's new index (callers that
+//                 read oldToNew itself).
 // Keys compare by raw bits, so the set of representatives' keys is exactly the set of distinct
 // used keys, and the sorted result (unique vertices in ascending key order, each index's rank) is
 // the paper's, bit for bit, whichever copy became a representative.  The table lives in the sort's
@@ -21,8 +22,6 @@
 #include "internal.h"
 
 namespace reindex {
-
-constexpr uint32_t kRepTag = 0x80000000u;  // oldToNew entry: "representative is the low 31 bits"
 
 // Table slot values: 0 (empty); owner index + 1 (claimed by a representative whose item is not
 // published: below 2^31); kPosFlag | item position (published, in the publishing variant).
