@@ -995,6 +995,22 @@ def run_ours(args, world, rank, local):
     D = int(out_n.item())
     if D != mesh.expected_unique:
         raise SystemExit(f"unexpected unique count {D} (expected {mesh.expected_unique})")
+    # one call captured into a CUDA graph (the library's workspace variant allocates nothing and
+    # never synchronises): a replay issues the whole launch sequence at once, as a caller that
+    # re-indexes meshes of one size in a loop would
+    graph = None
+    if not args.no_graph:
+        gs = torch.cuda.Stream(dev)
+        gs.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            rx.reindex_mesh_ws(vtx, idx, ws, out_v, out_n, out_i, stream=gs)
+        stream.wait_stream(gs)
+        out_n.fill_(-1)
+        graph.replay()
+        torch.cuda.synchronize(dev)
+        if int(out_n.item()) != D:
+            raise SystemExit("graph replay: unexpected unique count")
 
     # ---- timed region: device-resident inputs (inputs larger than L2)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1004,12 +1020,24 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize(dev)
         e0.record(stream)
         for _ in range(args.steps):
-            rx.reindex_mesh_ws(vtx, idx, ws, out_v, out_n, out_i)
+            if graph is not None:
+                graph.replay()
+            else:
+                rx.reindex_mesh_ws(vtx, idx, ws, out_v, out_n, out_i)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         if world > 1:
             torch.distributed.barrier()
         ms = e0.elapsed_time(e1) / args.steps
+        ms_stream = None
+        if graph is not None:  # the same steps launched call by call, for reference
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(args.steps):
+                rx.reindex_mesh_ws(vtx, idx, ws, out_v, out_n, out_i)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_stream = e0.elapsed_time(e1) / args.steps
         # the same steps again with a pair of events around every kernel launch: per-kernel
         # durations for the breakdown and the roofline (the events add a little time per launch,
         # so the step time above is taken without them)
@@ -1092,7 +1120,10 @@ def run_ours(args, world, rank, local):
         "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][0], "n_vtx": n_vtx, "n_elem": n_elem, "stride_bytes": S,
                    "idx_per_elem": k, "unique_out": D, "parallelism": f"replicas x{world}",
-                   "l2": f"inputs larger than L2 ({(n_vtx * S + M * 4) / 1e6:.0f} MB read per step)"},
+                   "l2": f"inputs larger than L2 ({(n_vtx * S + M * 4) / 1e6:.0f} MB read per step)",
+                   "launch": ("one CUDA graph replay per step (one reindex_mesh_ws call, captured once)"
+                              if graph is not None else "one reindex_mesh_ws call per step")},
+        "ms_per_step_stream_launched": ms_stream,
         "roofline": roofline, "step_model": step_model, "cpu_baseline": cpu, "e2e": e2e, "tuning": tuning,
         **sub,
         "gpu_launches": len(recs),
@@ -1135,6 +1166,8 @@ def main():
     ap.add_argument("--requests", type=int, default=20000, help="serving workload: number of requests")
     ap.add_argument("--loads", default="0.5,0.7,0.9", help="serving workload: offered loads (fractions of capacity)")
     ap.add_argument("--no-sub", action="store_true", help="default workload: skip the batched and serving records")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time the call launched on the stream each step instead of a captured CUDA graph's replay")
     ap.add_argument("--batched-tuning", default="dedup=hash,dpub=off",
                     help="tuning spec of batched calls and serving (keys of 8-20 bytes), or 'default'")
     ap.add_argument("--serving-requests", type=int, default=2000,
