@@ -101,19 +101,21 @@ def test_noalloc_wide_vertices_at_the_limit(rx, words):
     _check(rx, *_mesh(4, MAX_VTX, 87_381, 3, words))
 
 
-@pytest.mark.parametrize("pub", ["on", "off"])
-def test_noalloc_hash_path(rx, pub):
+@pytest.mark.parametrize("words,pub", [(3, "on"), (3, "off"), (8, "off")])
+def test_noalloc_hash_path(rx, words, pub):
     """With duplicates removed by the hash table before the sort (its table in the same scratch
-    array): calls in a row, small, large and small again, each against the oracle."""
-    saved = rx.reindex_tuning_get(12)
-    rx.reindex_tuning_set(12, f"dedup=hash,dpub={pub}")
+    array; 32-byte vertices: the prefix sort of the representatives): calls in a row, small, large
+    and small again, each against the oracle."""
+    S = 4 * words
+    saved = rx.reindex_tuning_get(S)
+    rx.reindex_tuning_set(S, f"dedup=hash,dpub={pub}")
     try:
-        small = _mesh(11, 30_001, 12_000, 3, 3)
-        large = _mesh(12, 200_000, 150_000, 3, 3)
+        small = _mesh(11, 30_001, 12_000, 3, words)
+        large = _mesh(12, 200_000, 150_000, 3, words)
         for vtx, idx in (small, large, small):
             _check(rx, vtx, idx)
     finally:
-        rx.reindex_tuning_set(12, saved)
+        rx.reindex_tuning_set(S, saved)
 
 
 def _cudart():
