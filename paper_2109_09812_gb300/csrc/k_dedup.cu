@@ -7,8 +7,10 @@
 //                 a slot is claimed by compare-and-swap for the first vertex that reaches it empty).
 //                 A vertex that claims an empty slot is its key's representative and appends its
 //                 (key, index) item for the sort, with the item's first-pass digit and the key bit
-//                 masks (as the compaction does); any other vertex finds the slot whose owner's key
-//                 equals its own (raw bits) and records that representative in oldToNew, tagged;
+//                 masks (as the compaction does) -- or, when the prefix path sorts the
+//                 representatives, marks itself in the used bits instead; any other vertex finds
+//                 the slot whose owner's key equals its own (raw bits) and records that
+//                 representative in oldToNew, tagged;
 //   (sort, run heads, scan, oldToNew scatter, gather: unchanged, on the D distinct keys -- every
 //    item is a run head, and oldToNew[rep] = its new index)
 //   k_remap_rep   out = oldToNew[idx], a tagged entry through its representative's (single meshes;
@@ -153,10 +155,10 @@ __host__ __device__ constexpr int dedup_ctas_per_sm(int SI, bool pub, bool seg) 
 // kSeg (batched calls): the key is (mesh id, vertex), the mesh id its most significant word, as in
 // the batched compaction; a copy compares the owner's mesh id too (looked up from its index).
 // kRepMask (single meshes of 12-byte vertices and wider whose sort runs on key prefixes):
-// representatives append nothing;
-// each row's used-bit word is replaced by the bits of its representatives (the warp that reads a
-// row's word is the only one that touches it), so that the prefix path's compaction, sort, check
-// and fallback take the representatives as the used vertices; copies still record theirs.
+// representatives append nothing; each row's used-bit word is replaced by the bits of its
+// representatives (the warp that reads a row's word is the only one that touches it), so that the
+// prefix path's compaction, sort, check and fallback take the representatives as the used
+// vertices; copies still record theirs.
 // A launch inserts the used vertices of rows [row_lo, row_hi) (32 vertices a row): a call may insert
 // the vertex array chunk by chunk, as the chunks arrive, in any order -- the result does not depend
 // on which copy of a key claims its slot first.
