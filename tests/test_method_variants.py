@@ -77,3 +77,62 @@ def test_vertex_ranges_compose_to_the_single_level_result(K, values, width):
         got_i = map2[np.array(off)[idx // width] + rank[idx]]
         np.testing.assert_array_equal(fv, want_v)
         np.testing.assert_array_equal(got_i, want_i)
+
+
+def _prefix64(keys):
+    """The 64 most significant varying bits of each key (K uint32 words, word 0 most significant),
+    in order, as one uint64 per key: an order-preserving prefix of the key (the bits left out are
+    constant over the keys or less significant than every bit kept)."""
+    K = keys.shape[1]
+    bits = np.unpackbits(keys.astype(">u4").view(np.uint8).reshape(keys.shape[0], 4 * K), axis=1)  # MSB first
+    varying = np.flatnonzero(bits.max(axis=0) != bits.min(axis=0))[:64]
+    p = np.zeros(keys.shape[0], dtype=np.uint64)
+    for b in varying:
+        p = (p << np.uint64(1)) | bits[:, b].astype(np.uint64)
+    return p << np.uint64(64 - len(varying)) if len(varying) < 64 else p
+
+
+def _prefix_path(vtx, idx):
+    """Sort the used vertices by prefix (stable); each run of equal prefixes gives one unique
+    vertex (its first key); the check: every used vertex equals its run's key.  Returns the result,
+    or None when the check fails (two keys share a prefix: the full-key sort must run)."""
+    used = np.unique(idx)
+    keys = vtx[used]
+    pre = _prefix64(keys)
+    order = np.argsort(pre, kind="stable")
+    sp = pre[order]
+    head = np.ones(sp.size, dtype=bool)
+    head[1:] = sp[1:] != sp[:-1]
+    run = np.cumsum(head) - 1  # run rank of each sorted used vertex
+    heads = keys[order][head]
+    if not np.array_equal(keys[order], heads[run]):
+        return None
+    rank = np.empty(used.size, dtype=np.int64)
+    rank[order] = run
+    new = np.full(vtx.shape[0], -1, dtype=np.int64)
+    new[used] = rank
+    return heads, new[idx].astype(np.int32)
+
+
+@pytest.mark.parametrize("K,values,collide", [(4, 5000, False), (8, 3000, False), (4, 7, True), (8, 5, True)])
+def test_prefix_sort_with_check_and_fallback(K, values, collide):
+    """The prefix sort: when the check passes its result is the plain definition's; keys built to
+    share their 64-bit prefixes fail the check (the full-key sort then runs)."""
+    rng = np.random.default_rng(31 * K + values)
+    fallbacks = 0
+    for n, m in [(1, 1), (60, 150), (4000, 6000)]:
+        if collide:  # few values per word, all words varying: more than 64 varying bits
+            pool = rng.integers(0, 2**32, size=(values,), dtype=np.uint64).astype(np.uint32)
+            vtx = pool[rng.integers(0, values, size=(n, K))]
+        else:
+            vtx = _mesh(rng, n, 1, K, values)[0]
+        idx = rng.integers(0, n, size=m).astype(np.int32)
+        want_v, want_i = oracle.reindex_sort(vtx, idx)
+        got = _prefix_path(vtx, idx)
+        if got is None:
+            fallbacks += 1
+            got = oracle.reindex_sort(vtx, idx)  # the full-key sort
+        np.testing.assert_array_equal(got[0], want_v)
+        np.testing.assert_array_equal(got[1], want_i)
+    if collide:
+        assert fallbacks >= 1
